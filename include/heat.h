@@ -1,0 +1,145 @@
+/*
+ * heat.h -- C ABI of libheat: stochastic heating and emissivity of dust grains
+ * on one NVIDIA GB300 (sm_103a).
+ *
+ * The method is Porter & Vladimirov, "Calculation of Stochastic Heating and
+ * Emissivity of Cosmic Dust Grains ..." (HEATCODE), Sec. 2:
+ *   - enthalpy bins i = 0..M with centres E_i = H(T_i)            (Sec. 2.1)
+ *   - heating elements T_ul, u > l, from Omega = u_lambda C_abs with
+ *     log-log interpolation between wavelength nodes                (Eq. heating, Eq. interpolation)
+ *   - thermal-continuous cooling T_{f-1,f}                           (Eq. adjacent, Eq. cooling)
+ *   - B_fj = sum_{k>=f} T_kj and the X recursion, then P = X / sum X (Eq. bmatrix, Eq. xf, Eq. renormalization)
+ *   - emissivity j_lambda = C_abs(lambda) sum_i P_i B_lambda(T_i) [E_i >= hc/lambda]
+ *                                                                    (Eq. emission, Eq. emission-lambda)
+ *   - optional size integration J = sum_g w_g j_g                    (Eq. convolution)
+ * The heating element is the wavelength integral over the target bin's edges,
+ *   T_ul = (1/h) int Omega(lambda) lambda dlambda over [hc/(Ehi_u - E_l), hc/(Elo_u - E_l)],
+ * with Elo_0 = 0, Elo_i = (E_{i-1}+E_i)/2, Ehi_i = Elo_{i+1}, Ehi_M = infinity, plus the
+ * power of photons too soft to leave bin l carried by T_{l+1,l}.  Cooling integrates the
+ * cross-section continued as a power law beyond the wavelength grid.
+ *
+ * Units are CGS: wavelengths in cm, u_lambda in erg cm^-3 cm^-1, C_abs in cm^2,
+ * temperatures in K, enthalpies in erg, P dimensionless, j in erg s^-1 sr^-1 cm^-1.
+ *
+ * Conventions for every call:
+ *   - A heat_ctx is bound to one CUDA device; calls on one ctx must not run
+ *     concurrently from several host threads (distinct ctxs are independent).
+ *   - Host arrays are read during the call only.  Device pointers are borrowed:
+ *     they must stay valid until the work queued on the given stream completes.
+ *   - Argument errors return HEAT_EINVAL synchronously and queue no work.
+ *   - Errors detected on the device (non-finite input, a zero cooling rate with
+ *     non-zero inflow) are recorded in a device status word and reported by
+ *     heat_sync (and by the next call that synchronises).
+ *   - heat_last_error returns a message for the last failed call on the ctx.
+ */
+#ifndef LIBHEAT_HEAT_H
+#define LIBHEAT_HEAT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct heat_ctx heat_ctx;
+
+typedef enum {
+    HEAT_OK = 0,
+    HEAT_EINVAL = 1,   /* bad argument; nothing queued */
+    HEAT_ENOMEM = 2,   /* device or host allocation failed */
+    HEAT_ECUDA = 3,    /* a CUDA call failed (message in heat_last_error) */
+    HEAT_ENUMERIC = 4, /* a cooling rate is zero while the bin receives inflow (no steady state) */
+    HEAT_ETIMEOUT = 5, /* a bounded device-side wait gave up */
+    HEAT_ESTATE = 6    /* call out of order (e.g. solve before grains/fields are set) */
+} heat_status;
+
+/* element types for field input and emissivity output */
+enum { HEAT_F64 = 0, HEAT_F32 = 1 };
+
+/* precision of the matrix build (B elements and the per-cell wavelength tables);
+ * the recursion (Eq. xf) always accumulates in FP64 */
+enum { HEAT_BUILD_F64 = 0, HEAT_BUILD_F32 = 1 };
+
+/* emissivity contraction (Eq. emission) */
+enum {
+    HEAT_EMIS_NONE = -1, /* no emissivity */
+    HEAT_EMIS_F64 = 0    /* FP64 FMA contraction (exact path) */
+};
+
+typedef struct heat_opts {
+    int build;          /* HEAT_BUILD_F64 (exact) or HEAT_BUILD_F32 (mixed)                      */
+    int emis;           /* HEAT_EMIS_*                                                             */
+    int j_dtype;        /* HEAT_F64 or HEAT_F32 element type of j_out                              */
+    int size_integrate; /* 0: j_out is [cells][grains][n_lambda]; 1: [cells][n_lambda], sum_g w_g j_g */
+    int cell_begin;     /* first cell solved (0-based)                                             */
+    int cell_count;     /* cells solved; <= 0 means all cells from cell_begin                      */
+    int chunk_cells;    /* cells per internal chunk (multiple of 32; 0 = library default)         */
+    int host_io;        /* 1: P_out and j_out are host pointers; the library stages through device
+                           memory and the call returns after the results are on the host          */
+} heat_opts;
+
+/* Fill *opts with defaults: exact FP64 build, FP64 emissivity, FP64 j, per-grain j,
+ * all cells, device outputs. */
+void heat_default_opts(heat_opts* opts);
+
+/* Create a context on CUDA device `device` for the wavelength grid lambda_cm[n_lambda]
+ * (host, strictly ascending, > 0, n_lambda >= 2).  The grid is copied.
+ * Errors: HEAT_EINVAL (bad grid), HEAT_ECUDA, HEAT_ENOMEM. */
+heat_status heat_create_grid(heat_ctx** out, int device, int n_lambda, const double* lambda_cm);
+
+/* Set the grain sizes (Sec. 2; paper's GrainModel + temperature grid).  All arrays are host:
+ *   radius_cm[n_grains]              grain radius (kept for size bookkeeping; > 0)
+ *   c_abs_cm2[n_grains][n_lambda]    absorption cross-section on the grid (>= 0, finite)
+ *   bin_offset[n_grains+1]           bins of grain g are bin_offset[g] .. bin_offset[g+1]-1,
+ *                                    at least 2 and at most 4096 bins per grain
+ *   T_bins_K[bin_offset[n_grains]]   bin temperatures, strictly ascending per grain, > 0
+ *   H_bins_erg[bin_offset[n_grains]] bin enthalpies E_i = H(T_i), strictly ascending per grain, > 0
+ *   size_weight[n_grains] or NULL    weights w_g for size integration (Eq. convolution)
+ * Computes on the device, once: cooling rates (Eq. cooling, FP64 Gauss-Legendre),
+ * the Planck kernels C_abs B_lambda(T_i) [E_i >= hc/lambda], and the field-independent
+ * band tables of each grain (which (f, j) can be reached by a photon on the grid, and
+ * where each transition wavelength hc/(Elo_f - E_j) falls on the grid).
+ * Synchronous.  Errors: HEAT_EINVAL, HEAT_ENOMEM, HEAT_ECUDA. */
+heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm, const double* c_abs_cm2,
+                            const int* bin_offset, const double* T_bins_K, const double* H_bins_erg,
+                            const double* size_weight);
+
+/* Set the radiation fields u_lambda[n_cells][n_lambda] (erg cm^-3 cm^-1, >= 0, finite),
+ * element type `dtype` (HEAT_F64 or HEAT_F32).  on_device = 1: `u_lambda` is a device
+ * pointer, borrowed until the solves that use it complete; on_device = 0: host memory
+ * (pinned or pageable), copied asynchronously on `stream` into library-owned device memory.
+ * Negative or non-finite values are flagged on the device during heat_solve
+ * (HEAT_EINVAL from heat_sync).  Errors: HEAT_EINVAL, HEAT_ENOMEM, HEAT_ECUDA, HEAT_ESTATE. */
+heat_status heat_set_fields(heat_ctx* ctx, int n_cells, const void* u_lambda, int dtype, int on_device,
+                            void* cuda_stream);
+
+/* Solve cells [cell_begin, cell_begin + cell_count) on `cuda_stream` (a cudaStream_t, NULL = legacy):
+ *   P_out  FP64 [cell_count][bin_offset[n_grains]] or NULL: the steady-state distributions
+ *          P of every grain (Eq. renormalization), row c holds all grains' bins back to back;
+ *   j_out  j_dtype, [cell_count][n_grains][n_lambda] (or [cell_count][n_lambda] with
+ *          size_integrate) or NULL: the emissivity (Eq. emission).
+ * Device pointers unless opts->host_io.  Asynchronous with respect to the host unless
+ * host_io; device-side errors surface at heat_sync.  Non-interacting grains give
+ * P = delta_{i0} (no error).  Errors: HEAT_EINVAL, HEAT_ESTATE, HEAT_ENOMEM, HEAT_ECUDA. */
+heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void* j_out, void* cuda_stream);
+
+/* Wait for all work of the ctx's last calls and return the device status:
+ * HEAT_OK, HEAT_ENUMERIC, HEAT_EINVAL (bad field values) or HEAT_ECUDA.  Clears the status. */
+heat_status heat_sync(heat_ctx* ctx);
+
+/* Message of the last failure on ctx (never NULL; "" when none). */
+const char* heat_last_error(const heat_ctx* ctx);
+
+/* Copy the cooling rates T_{f-1,f} (Eq. cooling) of all grains to host Cf[bin_offset[n_grains]]
+ * (Cf[bin_offset[g]] = 0 for every grain).  Errors: HEAT_ESTATE, HEAT_ECUDA. */
+heat_status heat_get_cooling(heat_ctx* ctx, double* Cf_host);
+
+/* Number of band elements (f, j), j < f, that a photon on the grid can reach, summed over
+ * grains: the FP64 FMAs of one spectrum set's recursion.  Errors: HEAT_ESTATE. */
+heat_status heat_band_elements(const heat_ctx* ctx, long long* per_cell);
+
+/* Release the ctx and all device memory it owns (no-op on NULL). */
+void heat_destroy(heat_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

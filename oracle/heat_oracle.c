@@ -104,7 +104,8 @@ double orc_range_integral(int N, const double* lam, const double* om, int p, dou
     if (b > lam[N - 1]) b = lam[N - 1];
     if (!(b > a)) return 0.0;
     double sum = 0.0;
-    for (int n = 0; n < N - 1; ++n) {
+    int n_first = find_segment(N, lam, a), n_last = find_segment(N, lam, b);
+    for (int n = n_first; n <= n_last; ++n) {
         double x = a > lam[n] ? a : lam[n];
         double y = b < lam[n + 1] ? b : lam[n + 1];
         if (y > x) sum += seg_integral(lam, om, n, p, x, y);
@@ -337,7 +338,11 @@ double orc_emitted_power(int N, const double* lam, const double* cabs, double T,
 int orc_cooling(int N, const double* lam, const double* cabs, int nb, const double* T, const double* E, double* Cf)
 {
     if (N < 2 || nb < 2) return ORC_EINVAL;
+    gl_init();
     Cf[0] = 0.0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
     for (int f = 1; f < nb; ++f)
         Cf[f] = orc_emitted_power(N, lam, cabs, T[f], E[f]) / (E[f] - E[f - 1]);
     return ORC_OK;

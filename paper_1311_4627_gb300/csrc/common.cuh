@@ -1,0 +1,83 @@
+// Shared device-side definitions for the libheat CUDA kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace heat {
+
+// CODATA 2018 exact values (CGS).
+constexpr double kH = 6.62607015e-27;   // erg s
+constexpr double kC = 2.99792458e10;    // cm s^-1
+constexpr double kK = 1.380649e-16;     // erg K^-1
+constexpr double kHC = kH * kC;         // erg cm (rounded product of the two)
+
+// Device status bits (OR-ed into the context's status word).
+constexpr int kStatNumeric = 1;   // zero cooling rate with non-zero inflow
+constexpr int kStatBadInput = 2;  // non-finite or negative field value
+constexpr int kStatTimeout = 4;   // bounded wait gave up
+
+constexpr double kRescaleBig = 0x1p800;     // exact power of two
+constexpr double kRescaleSmall = 0x1p-800;
+
+// Band element of the exact (FP64) build: wavelength segment and log offset.
+struct ElemF64 {
+    int n;       // segment index; N-1 means the abscissa is past the last node
+    int pad;
+    double t;    // ln(lambda_fj / lambda_n) (0 for n = N-1)
+};
+
+// Band element of the FP32 build.  With a_n = u_n * ca_n and z = (su_n + s2_n) t:
+//   B_fj = Phi_n + u_n * cat * E1(fma(su_n, t, zt)),   cat = ca_n t,  zt = s2_n t,
+// where ca_n = C_n lambda_n^2 / h (0 on an inactive C segment), s2_n = sC_n + 2.
+struct ElemF32 {
+    int n;
+    float t;
+    float cat;
+    float zt;
+};
+
+// Soft-photon abscissa for the intra-bin term of row j+1:
+// lambda_s = hc / (Elo_{j+1} - E_j) in segment n with offset t; n = -1 below the
+// grid (all absorbed power counts), n = N-1 at or above the last node (none).
+struct SoftF64 {
+    int j;
+    int n;
+    double t;
+};
+
+// E1(z) = (e^z - 1)/z in FP32: Taylor series for |z| < 0.5 (truncation below
+// 2^-24 relative), library expm1f otherwise.
+__device__ __forceinline__ float e1f(float z) {
+    if (fabsf(z) < 0.5f) {
+        float p = 1.0f / 40320.0f;
+        p = fmaf(p, z, 1.0f / 5040.0f);
+        p = fmaf(p, z, 1.0f / 720.0f);
+        p = fmaf(p, z, 1.0f / 120.0f);
+        p = fmaf(p, z, 1.0f / 24.0f);
+        p = fmaf(p, z, 1.0f / 6.0f);
+        p = fmaf(p, z, 0.5f);
+        p = fmaf(p, z, 1.0f);
+        return p;
+    }
+    return expm1f(z) / z;
+}
+
+// E1(z) in FP64 (library expm1; exact at z = 0).
+__device__ __forceinline__ double e1d(double z) {
+    return z == 0.0 ? 1.0 : expm1(z) / z;
+}
+
+// Widen a non-negative finite float to double with integer operations only
+// (rebias the exponent, shift the mantissa); zero and subnormals map to 0.
+// Keeps the conversion off the FP64 pipe, which is the bound of the recursion.
+__device__ __forceinline__ double widen_pos(float x) {
+    unsigned b = __float_as_uint(x);
+    unsigned hi = (b >> 3) + 0x38000000u;
+    unsigned lo = b << 29;
+    bool tiny = b < 0x00800000u;
+    hi = tiny ? 0u : hi;
+    lo = tiny ? 0u : lo;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+}  // namespace heat

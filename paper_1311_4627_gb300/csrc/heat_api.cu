@@ -1,0 +1,587 @@
+// Host side of libheat: context, grain set-up (band and pattern tables), field
+// staging, chunked solve and the C ABI declared in include/heat.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/heat.h"
+#include "common.cuh"
+#include "internal.h"
+
+using namespace heat;
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t bytes) {
+        if (bytes <= cap) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e == cudaSuccess) cap = bytes;
+        return e;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+    template <typename T>
+    T* as() const { return (T*)p; }
+};
+
+}  // namespace
+
+struct heat_ctx {
+    int device = 0;
+    int N = 0;
+    std::vector<double> lam;
+    std::string err;
+
+    // grid
+    DevBuf d_lam, d_dln, d_lam32, d_dln32;
+    // grains
+    int G = 0, nbt = 0;
+    std::vector<int> bin_off;
+    std::vector<double> w;
+    bool has_w = false;
+    long long band_per_cell = 0;
+    std::vector<int> grain_order;
+    DevBuf d_bin_off, d_cabs, d_T, d_E, d_Cf, d_invC, d_invdE, d_invdE32, d_Cact, d_sC, d_ca32, d_ce32, d_sC32,
+        d_rowptr, d_el64, d_el32, d_soft, d_soft_off, d_K, d_Kw, d_w, d_koff_all;
+    // fields
+    int n_cells = 0;
+    const void* u_dev = nullptr;
+    int u_dtype = 0;
+    DevBuf d_u_own;
+    // chunk scratch
+    DevBuf s_tasks, s_ua64, s_su64, s_ua32, s_su32, s_phi64, s_aq64, s_q64, s_phi32, s_intra64, s_intra32, s_xs,
+        s_pabs, s_P, s_j;
+    int tasks_NG = -1;
+    DevBuf d_status;
+
+    heat_status fail(heat_status s, const std::string& m) {
+        err = m;
+        return s;
+    }
+    heat_status cuda_fail(cudaError_t e, const char* where) {
+        err = std::string(where) + ": " + cudaGetErrorString(e);
+        return HEAT_ECUDA;
+    }
+};
+
+#define CKR(call)                                         \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return ctx->cuda_fail(e_, #call); \
+    } while (0)
+
+namespace {
+
+const double kHChost = 6.62607015e-27 * 2.99792458e10;
+const double kHhost = 6.62607015e-27;
+const double kChost = 2.99792458e10;
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n.
+void gauss_legendre(int n, double* x, double* w) {
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+            double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// largest n in [0, N-2] with lam[n] <= x (x inside the grid)
+int segment_of(const std::vector<double>& lam, double x) {
+    int lo = 0, hi = (int)lam.size() - 2;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) / 2;
+        if (lam[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T>
+cudaError_t upload(DevBuf& b, const std::vector<T>& v) {
+    size_t bytes = std::max<size_t>(v.size() * sizeof(T), 16);
+    cudaError_t e = b.ensure(bytes);
+    if (e != cudaSuccess) return e;
+    if (v.empty()) return cudaSuccess;
+    return cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+}  // namespace
+
+extern "C" {
+
+void heat_default_opts(heat_opts* o) {
+    if (!o) return;
+    o->build = HEAT_BUILD_F64;
+    o->emis = HEAT_EMIS_F64;
+    o->j_dtype = HEAT_F64;
+    o->size_integrate = 0;
+    o->cell_begin = 0;
+    o->cell_count = 0;
+    o->chunk_cells = 0;
+    o->host_io = 0;
+}
+
+heat_status heat_create_grid(heat_ctx** out, int device, int n_lambda, const double* lambda_cm) {
+    if (!out) return HEAT_EINVAL;
+    *out = nullptr;
+    if (n_lambda < 2 || !lambda_cm) return HEAT_EINVAL;
+    for (int n = 0; n < n_lambda; ++n) {
+        if (!(lambda_cm[n] > 0.0) || !std::isfinite(lambda_cm[n])) return HEAT_EINVAL;
+        if (n > 0 && !(lambda_cm[n] > lambda_cm[n - 1])) return HEAT_EINVAL;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return HEAT_ECUDA;
+    heat_ctx* ctx = new (std::nothrow) heat_ctx();
+    if (!ctx) return HEAT_ENOMEM;
+    ctx->device = device;
+    ctx->N = n_lambda;
+    ctx->lam.assign(lambda_cm, lambda_cm + n_lambda);
+    auto cleanup = [&](heat_status s) { heat_destroy(ctx); return s; };
+    if (cudaSetDevice(device) != cudaSuccess) return cleanup(HEAT_ECUDA);
+    std::vector<double> dln(n_lambda - 1);
+    std::vector<float> lam32(n_lambda), dln32(n_lambda - 1);
+    for (int n = 0; n < n_lambda - 1; ++n) {
+        dln[n] = std::log(lambda_cm[n + 1] / lambda_cm[n]);
+        dln32[n] = (float)dln[n];
+    }
+    for (int n = 0; n < n_lambda; ++n) lam32[n] = (float)lambda_cm[n];
+    if (upload(ctx->d_lam, ctx->lam) != cudaSuccess || upload(ctx->d_dln, dln) != cudaSuccess ||
+        upload(ctx->d_lam32, lam32) != cudaSuccess || upload(ctx->d_dln32, dln32) != cudaSuccess)
+        return cleanup(HEAT_ENOMEM);
+    if (ctx->d_status.ensure(sizeof(int)) != cudaSuccess) return cleanup(HEAT_ENOMEM);
+    if (cudaMemset(ctx->d_status.p, 0, sizeof(int)) != cudaSuccess) return cleanup(HEAT_ECUDA);
+    double glx[kGLPoints], glw[kGLPoints];
+    gauss_legendre(kGLPoints, glx, glw);
+    if (set_gauss_legendre(glx, glw) != cudaSuccess) return cleanup(HEAT_ECUDA);
+    *out = ctx;
+    return HEAT_OK;
+}
+
+heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm, const double* c_abs_cm2,
+                            const int* bin_offset, const double* T_bins_K, const double* H_bins_erg,
+                            const double* size_weight) {
+    if (!ctx) return HEAT_EINVAL;
+    if (n_grains < 1 || !radius_cm || !c_abs_cm2 || !bin_offset || !T_bins_K || !H_bins_erg)
+        return ctx->fail(HEAT_EINVAL, "heat_set_grains: null argument or n_grains < 1");
+    const int N = ctx->N, G = n_grains;
+    if (bin_offset[0] != 0) return ctx->fail(HEAT_EINVAL, "heat_set_grains: bin_offset[0] must be 0");
+    for (int g = 0; g < G; ++g) {
+        int nb = bin_offset[g + 1] - bin_offset[g];
+        if (nb < 2 || nb > 4096) return ctx->fail(HEAT_EINVAL, "heat_set_grains: each grain needs 2..4096 bins");
+        if (!(radius_cm[g] > 0.0)) return ctx->fail(HEAT_EINVAL, "heat_set_grains: radius must be > 0");
+        for (int n = 0; n < N; ++n) {
+            double c = c_abs_cm2[(size_t)g * N + n];
+            if (!(c >= 0.0) || !std::isfinite(c)) return ctx->fail(HEAT_EINVAL, "heat_set_grains: bad C_abs");
+        }
+        for (int i = bin_offset[g]; i < bin_offset[g + 1]; ++i) {
+            if (!(T_bins_K[i] > 0.0) || !(H_bins_erg[i] > 0.0) || !std::isfinite(T_bins_K[i]) ||
+                !std::isfinite(H_bins_erg[i]))
+                return ctx->fail(HEAT_EINVAL, "heat_set_grains: T and H must be positive and finite");
+            if (i > bin_offset[g] && !(T_bins_K[i] > T_bins_K[i - 1] && H_bins_erg[i] > H_bins_erg[i - 1]))
+                return ctx->fail(HEAT_EINVAL, "heat_set_grains: T and H must ascend within a grain");
+        }
+    }
+    if (size_weight)
+        for (int g = 0; g < G; ++g)
+            if (!std::isfinite(size_weight[g])) return ctx->fail(HEAT_EINVAL, "heat_set_grains: bad size weight");
+    CKR(cudaSetDevice(ctx->device));
+    const int nbt = bin_offset[G];
+    const std::vector<double>& lam = ctx->lam;
+    ctx->G = G;
+    ctx->nbt = nbt;
+    ctx->bin_off.assign(bin_offset, bin_offset + G + 1);
+    ctx->has_w = size_weight != nullptr;
+    ctx->w.assign(G, 0.0);
+    if (size_weight) std::copy(size_weight, size_weight + G, ctx->w.begin());
+    ctx->tasks_NG = -1;
+
+    // per-grain cross-section tables
+    std::vector<double> Cact((size_t)G * N, 0.0), sC((size_t)G * N, 0.0);
+    std::vector<float> ca32((size_t)G * N, 0.0f), ce32((size_t)G * N, 0.0f), sC32((size_t)G * N, 0.0f);
+    for (int g = 0; g < G; ++g) {
+        const double* C = c_abs_cm2 + (size_t)g * N;
+        for (int n = 0; n < N - 1; ++n) {
+            if (C[n] > 0.0 && C[n + 1] > 0.0) {
+                size_t k = (size_t)g * N + n;
+                Cact[k] = C[n];
+                sC[k] = std::log(C[n + 1] / C[n]) / std::log(lam[n + 1] / lam[n]);
+                ca32[k] = (float)(C[n] * lam[n] * lam[n] / kHhost);
+                ce32[k] = (float)(kChost * C[n] * lam[n]);
+                sC32[k] = (float)sC[k];
+            }
+        }
+    }
+    // bins, band and soft-photon tables
+    std::vector<double> invdE(nbt, 0.0);
+    std::vector<float> invdE32(nbt, 0.0f);
+    std::vector<int> rowptr;
+    rowptr.reserve(nbt + G);
+    std::vector<ElemF64> el64;
+    std::vector<ElemF32> el32;
+    std::vector<SoftF64> soft;
+    std::vector<int> soft_off(G + 1, 0);
+    std::vector<int> bin_grain(nbt);
+    std::vector<long long> cost(G, 0);
+    long long band_total = 0;
+    for (int g = 0; g < G; ++g) {
+        const int off = bin_offset[g], nb = bin_offset[g + 1] - off, M = nb - 1;
+        const double* E = H_bins_erg + off;
+        std::vector<double> Elo(nb);
+        Elo[0] = 0.0;
+        for (int i = 1; i < nb; ++i) Elo[i] = 0.5 * (E[i - 1] + E[i]);
+        for (int i = 0; i < nb; ++i) bin_grain[off + i] = g;
+        for (int j = 0; j < M; ++j) {
+            invdE[off + j] = 1.0 / (E[j + 1] - E[j]);
+            invdE32[off + j] = (float)invdE[off + j];
+        }
+        long long band = 0;
+        // row 0 has no elements
+        rowptr.push_back((int)el64.size());
+        for (int f = 1; f <= M; ++f) {
+            rowptr.push_back((int)el64.size());
+            int jlo = f;
+            for (int j = f - 1; j >= 0; --j) {
+                if (kHChost / (Elo[f] - E[j]) < lam[0]) break;
+                jlo = j;
+            }
+            for (int j = jlo; j < f; ++j) {
+                double lf = kHChost / (Elo[f] - E[j]);
+                ElemF64 a;
+                ElemF32 b;
+                a.pad = 0;
+                if (lf >= lam[N - 1]) {
+                    a.n = N - 1;
+                    a.t = 0.0;
+                } else {
+                    a.n = segment_of(lam, lf);
+                    a.t = std::log(lf / lam[a.n]);
+                }
+                size_t k = (size_t)g * N + a.n;
+                double ca = (a.n < N - 1) ? Cact[k] * lam[a.n] * lam[a.n] / kHhost : 0.0;
+                double s2 = (a.n < N - 1) ? sC[k] + 2.0 : 0.0;
+                b.n = a.n;
+                b.t = (float)a.t;
+                b.cat = (float)(ca * a.t);
+                b.zt = (float)(s2 * a.t);
+                el64.push_back(a);
+                el32.push_back(b);
+                ++band;
+            }
+        }
+        rowptr.push_back((int)el64.size());
+        // soft-photon abscissae, sorted by segment, descending
+        soft_off[g] = (int)soft.size();
+        std::vector<SoftF64> sg;
+        for (int j = 0; j < M; ++j) {
+            double ls = kHChost / (Elo[j + 1] - E[j]);
+            SoftF64 s;
+            s.j = j;
+            if (ls < lam[0]) {
+                s.n = -1;
+                s.t = 0.0;
+            } else if (ls >= lam[N - 1]) {
+                s.n = N - 1;
+                s.t = 0.0;
+            } else {
+                s.n = segment_of(lam, ls);
+                s.t = std::log(ls / lam[s.n]);
+            }
+            sg.push_back(s);
+        }
+        std::stable_sort(sg.begin(), sg.end(), [](const SoftF64& a, const SoftF64& b) { return a.n > b.n; });
+        soft.insert(soft.end(), sg.begin(), sg.end());
+        band_total += band;
+        cost[g] = band + 4LL * nb + N;
+    }
+    soft_off[G] = (int)soft.size();
+    if (el64.size() > (size_t)0x7fffffff) return ctx->fail(HEAT_EINVAL, "heat_set_grains: band tables too large");
+    ctx->band_per_cell = band_total;
+    ctx->grain_order.resize(G);
+    for (int g = 0; g < G; ++g) ctx->grain_order[g] = g;
+    std::stable_sort(ctx->grain_order.begin(), ctx->grain_order.end(),
+                     [&](int a, int b) { return cost[a] > cost[b]; });
+
+    std::vector<double> cabs(c_abs_cm2, c_abs_cm2 + (size_t)G * N), T(T_bins_K, T_bins_K + nbt),
+        E(H_bins_erg, H_bins_erg + nbt);
+    std::vector<int> boff(bin_offset, bin_offset + G + 1);
+    if (upload(ctx->d_bin_off, boff) || upload(ctx->d_cabs, cabs) || upload(ctx->d_T, T) || upload(ctx->d_E, E) ||
+        upload(ctx->d_invdE, invdE) || upload(ctx->d_invdE32, invdE32) || upload(ctx->d_Cact, Cact) ||
+        upload(ctx->d_sC, sC) || upload(ctx->d_ca32, ca32) || upload(ctx->d_ce32, ce32) ||
+        upload(ctx->d_sC32, sC32) || upload(ctx->d_rowptr, rowptr) || upload(ctx->d_el64, el64) ||
+        upload(ctx->d_el32, el32) || upload(ctx->d_soft, soft) || upload(ctx->d_soft_off, soft_off) ||
+        upload(ctx->d_w, ctx->w))
+        return ctx->fail(HEAT_ENOMEM, "heat_set_grains: device allocation failed");
+    std::vector<int> koff_all = {0, nbt};
+    if (upload(ctx->d_koff_all, koff_all)) return ctx->fail(HEAT_ENOMEM, "heat_set_grains: device allocation failed");
+
+    // cooling rates on the device
+    std::vector<int2> work;
+    for (int g = 0; g < G; ++g)
+        for (int f = 1; f < bin_offset[g + 1] - bin_offset[g]; ++f) work.push_back(make_int2(g, f));
+    DevBuf d_work, d_bg;
+    if (upload(d_work, work) || upload(d_bg, bin_grain))
+        return ctx->fail(HEAT_ENOMEM, "heat_set_grains: device allocation failed");
+    if (ctx->d_Cf.ensure(sizeof(double) * nbt)) return ctx->fail(HEAT_ENOMEM, "heat_set_grains: allocation");
+    CKR(cudaMemset(ctx->d_Cf.p, 0, sizeof(double) * nbt));
+    CKR(launch_cooling(N, ctx->d_lam.as<double>(), ctx->d_cabs.as<double>(), ctx->d_bin_off.as<int>(), G,
+                       ctx->d_T.as<double>(), ctx->d_E.as<double>(), ctx->d_Cf.as<double>(), d_work.as<int2>(),
+                       (int)work.size(), 0));
+    size_t kbytes = sizeof(double) * (size_t)nbt * N;
+    if (ctx->d_K.ensure(kbytes)) return ctx->fail(HEAT_ENOMEM, "heat_set_grains: allocation of Planck kernels");
+    if (ctx->has_w && ctx->d_Kw.ensure(kbytes))
+        return ctx->fail(HEAT_ENOMEM, "heat_set_grains: allocation of Planck kernels");
+    CKR(launch_planck(N, nbt, ctx->d_lam.as<double>(), ctx->d_cabs.as<double>(), d_bg.as<int>(), ctx->d_T.as<double>(),
+                      ctx->d_E.as<double>(), ctx->d_w.as<double>(), ctx->d_K.as<double>(),
+                      ctx->has_w ? ctx->d_Kw.as<double>() : nullptr, 0));
+    CKR(cudaDeviceSynchronize());
+    std::vector<double> Cf(nbt), invC(nbt, 0.0);
+    CKR(cudaMemcpy(Cf.data(), ctx->d_Cf.p, sizeof(double) * nbt, cudaMemcpyDeviceToHost));
+    for (int g = 0; g < G; ++g)
+        for (int i = bin_offset[g] + 1; i < bin_offset[g + 1]; ++i) invC[i] = Cf[i] > 0.0 ? 1.0 / Cf[i] : 0.0;
+    if (upload(ctx->d_invC, invC)) return ctx->fail(HEAT_ENOMEM, "heat_set_grains: allocation");
+    d_work.release();
+    d_bg.release();
+    return HEAT_OK;
+}
+
+heat_status heat_set_fields(heat_ctx* ctx, int n_cells, const void* u, int dtype, int on_device, void* stream) {
+    if (!ctx) return HEAT_EINVAL;
+    if (n_cells < 0 || (n_cells > 0 && !u) || (dtype != HEAT_F64 && dtype != HEAT_F32))
+        return ctx->fail(HEAT_EINVAL, "heat_set_fields: bad argument");
+    CKR(cudaSetDevice(ctx->device));
+    ctx->n_cells = n_cells;
+    ctx->u_dtype = dtype;
+    if (on_device) {
+        ctx->u_dev = u;
+        return HEAT_OK;
+    }
+    size_t bytes = (size_t)n_cells * ctx->N * (dtype == HEAT_F64 ? 8 : 4);
+    if (ctx->d_u_own.ensure(std::max<size_t>(bytes, 16)))
+        return ctx->fail(HEAT_ENOMEM, "heat_set_fields: device allocation failed");
+    if (bytes) CKR(cudaMemcpyAsync(ctx->d_u_own.p, u, bytes, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    ctx->u_dev = ctx->d_u_own.p;
+    return HEAT_OK;
+}
+
+heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void* j_out, void* stream) {
+    if (!ctx || !opts) return HEAT_EINVAL;
+    if (ctx->G == 0) return ctx->fail(HEAT_ESTATE, "heat_solve: grains not set");
+    if (!ctx->u_dev && ctx->n_cells > 0) return ctx->fail(HEAT_ESTATE, "heat_solve: fields not set");
+    const heat_opts& o = *opts;
+    if ((o.build != HEAT_BUILD_F64 && o.build != HEAT_BUILD_F32) || (o.emis != HEAT_EMIS_NONE && o.emis != HEAT_EMIS_F64) ||
+        (o.j_dtype != HEAT_F64 && o.j_dtype != HEAT_F32))
+        return ctx->fail(HEAT_EINVAL, "heat_solve: bad precision option");
+    if (o.size_integrate && !ctx->has_w) return ctx->fail(HEAT_EINVAL, "heat_solve: size integration needs weights");
+    if (o.chunk_cells < 0 || (o.chunk_cells % 32) != 0)
+        return ctx->fail(HEAT_EINVAL, "heat_solve: chunk_cells must be a non-negative multiple of 32");
+    int c_begin = o.cell_begin, count = o.cell_count > 0 ? o.cell_count : ctx->n_cells - o.cell_begin;
+    if (c_begin < 0 || count < 0 || c_begin + count > ctx->n_cells)
+        return ctx->fail(HEAT_EINVAL, "heat_solve: cell range outside the fields");
+    bool want_j = (j_out != nullptr) && o.emis != HEAT_EMIS_NONE;
+    if (j_out && o.emis == HEAT_EMIS_NONE) return ctx->fail(HEAT_EINVAL, "heat_solve: j_out given with HEAT_EMIS_NONE");
+    if (count == 0) return HEAT_OK;
+    CKR(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = ctx->N, G = ctx->G, nbt = ctx->nbt;
+    const int build = o.build;
+    const size_t jel = o.j_dtype == HEAT_F64 ? 8 : 4;
+    const size_t jrow = (size_t)(o.size_integrate ? 1 : G) * N;
+
+    // chunk size: bound the per-task wavelength tables to ~2 GiB
+    int chunk = o.chunk_cells;
+    if (chunk == 0) {
+        size_t per_group = (size_t)G * N * 32 * (build == 0 ? 24 : 4) + (size_t)nbt * 32 * 16;
+        size_t groups = std::max<size_t>(1, (size_t(2) << 30) / per_group);
+        chunk = (int)std::min<size_t>(groups * 32, 16384);
+    }
+    int span = std::min(count, chunk);
+    int Cc = (span + 31) / 32 * 32, NG = Cc / 32;
+
+    // scratch
+    size_t tasks_n = (size_t)G * NG;
+    bool ok = true;
+    ok &= !ctx->s_tasks.ensure(sizeof(int2) * tasks_n);
+    if (build == 0) {
+        ok &= !ctx->s_ua64.ensure(sizeof(double) * (size_t)N * Cc);
+        ok &= !ctx->s_su64.ensure(sizeof(double) * (size_t)N * Cc);
+        ok &= !ctx->s_phi64.ensure(sizeof(double) * tasks_n * N * 32);
+        ok &= !ctx->s_aq64.ensure(sizeof(double) * tasks_n * N * 32);
+        ok &= !ctx->s_q64.ensure(sizeof(double) * tasks_n * N * 32);
+        ok &= !ctx->s_intra64.ensure(sizeof(double) * (size_t)NG * nbt * 32);
+    } else {
+        ok &= !ctx->s_ua32.ensure(sizeof(float) * (size_t)N * Cc);
+        ok &= !ctx->s_su32.ensure(sizeof(float) * (size_t)N * Cc);
+        ok &= !ctx->s_phi32.ensure(sizeof(float) * tasks_n * N * 32);
+        ok &= !ctx->s_intra32.ensure(sizeof(float) * (size_t)NG * nbt * 32);
+    }
+    ok &= !ctx->s_xs.ensure(sizeof(double) * (size_t)NG * nbt * 32);
+    ok &= !ctx->s_pabs.ensure(sizeof(double) * (size_t)Cc * G);
+    bool internal_P = (P_out == nullptr) || o.host_io;
+    if (internal_P) ok &= !ctx->s_P.ensure(sizeof(double) * (size_t)Cc * nbt);
+    if (want_j && o.host_io) ok &= !ctx->s_j.ensure(jel * (size_t)Cc * jrow);
+    if (!ok) return ctx->fail(HEAT_ENOMEM, "heat_solve: scratch allocation failed");
+    if (ctx->tasks_NG != NG) {
+        std::vector<int2> tasks;
+        tasks.reserve(tasks_n);
+        for (int gi = 0; gi < G; ++gi)
+            for (int grp = 0; grp < NG; ++grp) tasks.push_back(make_int2(ctx->grain_order[gi], grp));
+        CKR(cudaMemcpy(ctx->s_tasks.p, tasks.data(), sizeof(int2) * tasks_n, cudaMemcpyHostToDevice));
+        ctx->tasks_NG = NG;
+    }
+
+    GrainDev gd;
+    gd.N = N;
+    gd.G = G;
+    gd.nbt = nbt;
+    gd.lam = ctx->d_lam.as<double>();
+    gd.dln = ctx->d_dln.as<double>();
+    gd.bin_off = ctx->d_bin_off.as<int>();
+    gd.Cact = ctx->d_Cact.as<double>();
+    gd.sC = ctx->d_sC.as<double>();
+    gd.lam32 = ctx->d_lam32.as<float>();
+    gd.dln32 = ctx->d_dln32.as<float>();
+    gd.ca32 = ctx->d_ca32.as<float>();
+    gd.ce32 = ctx->d_ce32.as<float>();
+    gd.sC32 = ctx->d_sC32.as<float>();
+    gd.invdE32 = ctx->d_invdE32.as<float>();
+    gd.invC = ctx->d_invC.as<double>();
+    gd.invdE = ctx->d_invdE.as<double>();
+    gd.rowptr = ctx->d_rowptr.as<int>();
+    gd.el64 = ctx->d_el64.as<ElemF64>();
+    gd.el32 = ctx->d_el32.as<ElemF32>();
+    gd.soft = ctx->d_soft.as<SoftF64>();
+    gd.soft_off = ctx->d_soft_off.as<int>();
+
+    for (int c0 = 0; c0 < count; c0 += chunk) {
+        int cells = std::min(chunk, count - c0);
+        int cc_pad = (cells + 31) / 32 * 32;
+        ChunkDev ch;
+        ch.cells = cells;
+        ch.Cc = cc_pad;
+        ch.NG = cc_pad / 32;
+        ch.tasks = ctx->s_tasks.as<int2>();
+        ch.n_tasks = G * ch.NG;
+        if (ch.NG != NG) {
+            // last, shorter chunk: tasks list must only hold its groups
+            std::vector<int2> tasks;
+            for (int gi = 0; gi < G; ++gi)
+                for (int grp = 0; grp < ch.NG; ++grp) tasks.push_back(make_int2(ctx->grain_order[gi], grp));
+            CKR(cudaMemcpyAsync(ctx->s_tasks.p, tasks.data(), sizeof(int2) * tasks.size(), cudaMemcpyHostToDevice, st));
+            CKR(cudaStreamSynchronize(st));
+            ctx->tasks_NG = ch.NG;
+        }
+        ch.ua64 = ctx->s_ua64.as<double>();
+        ch.su64 = ctx->s_su64.as<double>();
+        ch.ua32 = ctx->s_ua32.as<float>();
+        ch.su32 = ctx->s_su32.as<float>();
+        ch.phi64 = ctx->s_phi64.as<double>();
+        ch.aq64 = ctx->s_aq64.as<double>();
+        ch.q64 = ctx->s_q64.as<double>();
+        ch.phi32 = ctx->s_phi32.as<float>();
+        ch.intra64 = ctx->s_intra64.as<double>();
+        ch.intra32 = ctx->s_intra32.as<float>();
+        ch.xs = ctx->s_xs.as<double>();
+        ch.pabs = ctx->s_pabs.as<double>();
+        ch.status = ctx->d_status.as<int>();
+        ch.ldP = nbt;
+        ch.P = internal_P ? ctx->s_P.as<double>() : P_out + (size_t)c0 * nbt;
+        long long cell0 = (long long)c_begin + c0;
+        CKR(launch_field(gd, ctx->u_dev, ctx->u_dtype, cell0, ch, build, st));
+        CKR(launch_prep(gd, ch, build, st));
+        CKR(launch_recur(gd, ch, build, st));
+        if (want_j) {
+            char* jdst = o.host_io ? ctx->s_j.as<char>() : (char*)j_out + (size_t)c0 * jrow * jel;
+            if (o.size_integrate)
+                CKR(launch_gemm_f64(cells, N, 1, ctx->d_koff_all.as<int>(), ch.P, nbt, ctx->d_Kw.as<double>(), N, jdst,
+                                    N, 0, o.j_dtype == HEAT_F32, st));
+            else
+                CKR(launch_gemm_f64(cells, N, G, ctx->d_bin_off.as<int>(), ch.P, nbt, ctx->d_K.as<double>(), N, jdst,
+                                    (long long)G * N, N, o.j_dtype == HEAT_F32, st));
+            if (o.host_io)
+                CKR(cudaMemcpyAsync((char*)j_out + (size_t)c0 * jrow * jel, jdst, (size_t)cells * jrow * jel,
+                                    cudaMemcpyDeviceToHost, st));
+        }
+        if (P_out && o.host_io)
+            CKR(cudaMemcpyAsync(P_out + (size_t)c0 * nbt, ch.P, sizeof(double) * (size_t)cells * nbt,
+                                cudaMemcpyDeviceToHost, st));
+        if (o.host_io) CKR(cudaStreamSynchronize(st));
+    }
+    return HEAT_OK;
+}
+
+heat_status heat_sync(heat_ctx* ctx) {
+    if (!ctx) return HEAT_EINVAL;
+    CKR(cudaSetDevice(ctx->device));
+    CKR(cudaDeviceSynchronize());
+    int st = 0;
+    CKR(cudaMemcpy(&st, ctx->d_status.p, sizeof(int), cudaMemcpyDeviceToHost));
+    CKR(cudaMemset(ctx->d_status.p, 0, sizeof(int)));
+    if (st & kStatBadInput) return ctx->fail(HEAT_EINVAL, "device: negative or non-finite field value");
+    if (st & kStatNumeric) return ctx->fail(HEAT_ENUMERIC, "device: zero cooling rate with non-zero inflow");
+    if (st & kStatTimeout) return ctx->fail(HEAT_ETIMEOUT, "device: bounded wait gave up");
+    return HEAT_OK;
+}
+
+const char* heat_last_error(const heat_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+heat_status heat_get_cooling(heat_ctx* ctx, double* Cf) {
+    if (!ctx || !Cf) return HEAT_EINVAL;
+    if (ctx->G == 0) return ctx->fail(HEAT_ESTATE, "heat_get_cooling: grains not set");
+    CKR(cudaSetDevice(ctx->device));
+    CKR(cudaMemcpy(Cf, ctx->d_Cf.p, sizeof(double) * ctx->nbt, cudaMemcpyDeviceToHost));
+    return HEAT_OK;
+}
+
+heat_status heat_band_elements(const heat_ctx* ctx, long long* per_cell) {
+    if (!ctx || !per_cell) return HEAT_EINVAL;
+    if (ctx->G == 0) return HEAT_ESTATE;
+    *per_cell = ctx->band_per_cell;
+    return HEAT_OK;
+}
+
+void heat_destroy(heat_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    DevBuf* bufs[] = {&ctx->d_lam, &ctx->d_dln, &ctx->d_lam32, &ctx->d_dln32, &ctx->d_bin_off, &ctx->d_cabs,
+                      &ctx->d_T, &ctx->d_E, &ctx->d_Cf, &ctx->d_invC, &ctx->d_invdE, &ctx->d_invdE32, &ctx->d_Cact,
+                      &ctx->d_sC, &ctx->d_ca32, &ctx->d_ce32, &ctx->d_sC32, &ctx->d_rowptr, &ctx->d_el64,
+                      &ctx->d_el32, &ctx->d_soft, &ctx->d_soft_off, &ctx->d_K, &ctx->d_Kw, &ctx->d_w,
+                      &ctx->d_koff_all, &ctx->d_u_own, &ctx->s_tasks, &ctx->s_ua64, &ctx->s_su64, &ctx->s_ua32,
+                      &ctx->s_su32, &ctx->s_phi64, &ctx->s_aq64, &ctx->s_q64, &ctx->s_phi32, &ctx->s_intra64,
+                      &ctx->s_intra32, &ctx->s_xs, &ctx->s_pabs, &ctx->s_P, &ctx->s_j, &ctx->d_status};
+    for (DevBuf* b : bufs) b->release();
+    delete ctx;
+}
+
+}  // extern "C"

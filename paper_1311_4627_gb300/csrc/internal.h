@@ -1,0 +1,82 @@
+// Launchers shared between the host API and the kernel translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace heat {
+
+constexpr int kGLPoints = 16;
+
+struct ElemF64;
+struct ElemF32;
+struct SoftF64;
+
+// ---- grain set-up (k_setup.cu)
+cudaError_t set_gauss_legendre(const double* x, const double* w);
+cudaError_t launch_cooling(int N, const double* lam, const double* cabs, const int* bin_off, int G, const double* T,
+                           const double* E, double* Cf, const int2* work, int n_work, cudaStream_t st);
+cudaError_t launch_planck(int N, int nbt, const double* lam, const double* cabs, const int* bin_grain, const double* T,
+                          const double* E, const double* w, double* K, double* Kw, cudaStream_t st);
+
+// ---- per-solve kernels (k_solve.cu)
+
+// Per-grain device tables consumed by the solve kernels.
+struct GrainDev {
+    int N;              // wavelengths
+    int G;              // grains
+    int nbt;            // total bins over grains
+    const double* lam;  // [N]
+    const double* dln;  // [N-1] ln(lambda_{n+1}/lambda_n)
+    const int* bin_off; // [G+1]
+    const double* Cact;     // [G][N] C_n if the C segment n is active (both ends > 0), else 0
+    const double* sC;       // [G][N] log-log slope of C on segment n (0 if inactive)
+    const float* lam32;     // [N]   FP32 copies for the FP32 build
+    const float* dln32;     // [N-1]
+    const float* ca32;      // [G][N] C_n lambda_n^2 / h on active C segments, else 0
+    const float* ce32;      // [G][N] c C_n lambda_n on active C segments, else 0
+    const float* sC32;      // [G][N]
+    const float* invdE32;   // [nbt]
+    const double* invC;     // [nbt] 1/T_{f-1,f} (0 where the cooling rate is 0 and for f = 0)
+    const double* invdE;    // [nbt] 1/(E_{j+1}-E_j) (0 for the last bin)
+    const int* rowptr;      // [nbt + G] per grain, rows f = 0..M: band elements of row f at
+                            //   rowptr[off_g + g + f] .. rowptr[off_g + g + f + 1]
+    const ElemF64* el64;    // band elements (FP64 build)
+    const ElemF32* el32;    // band elements (FP32 build)
+    const SoftF64* soft;    // [nbt - G] per grain, sorted by segment (descending)
+    const int* soft_off;    // [G+1] start of each grain's soft list
+};
+
+// Per-chunk scratch.
+struct ChunkDev {
+    int cells;          // valid cells in the chunk
+    int Cc;             // padded cells (multiple of 32)
+    int NG;             // Cc / 32 cell groups
+    const int2* tasks;  // [G * NG] (grain, group), largest work first
+    int n_tasks;
+    // field tables, transposed [N][Cc]
+    double* ua64; double* su64;
+    float* ua32; float* su32;
+    // per-task wavelength tables [task][N][32]
+    double* phi64; double* aq64; double* q64;
+    float* phi32;
+    // per-group bin arrays [NG][nbt][32]
+    double* intra64; float* intra32;
+    double* xs;         // X history of the recursion
+    double* pabs;       // [Cc][G] absorbed power c int Omega dlambda (erg/s)
+    double* P;          // [Cc][nbt] output distributions (row stride ldP)
+    long long ldP;
+    int* status;
+};
+
+cudaError_t launch_field(const GrainDev& g, const void* u, int dtype, long long cell0, const ChunkDev& ch, int build,
+                         cudaStream_t st);
+cudaError_t launch_prep(const GrainDev& g, const ChunkDev& ch, int build, cudaStream_t st);
+cudaError_t launch_recur(const GrainDev& g, const ChunkDev& ch, int build, cudaStream_t st);
+
+// ---- emissivity (k_emis.cu)
+// C[z][m][n] = sum_{k in [koff[z], koff[z+1])} A[m][k] B[k][n] for z < nz, m < M, n < N;
+// koff is a device array of nz+1 offsets; C[z] starts at C + z * zstride_c.
+cudaError_t launch_gemm_f64(int M, int N, int nz, const int* koff, const double* A, long long lda,
+                            const double* B, long long ldb, void* C, long long ldc, long long zstride_c, int c_is_f32,
+                            cudaStream_t st);
+
+}  // namespace heat

@@ -1,0 +1,165 @@
+"""ctypes binding of libheat (include/heat.h): the same entry points, argument marshalling only.
+
+Pointers may be given as torch tensors (their data_ptr), numpy arrays (host memory),
+plain integers (raw addresses) or None.  Streams are cudaStream_t handles as integers
+(e.g. ``torch.cuda.current_stream().cuda_stream``) or None for the legacy stream.
+The library must have been built (``paper_1311_4627_gb300.build.build_lib``); there is
+no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libheat.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "heat.h")
+
+HEAT_OK, HEAT_EINVAL, HEAT_ENOMEM, HEAT_ECUDA, HEAT_ENUMERIC, HEAT_ETIMEOUT, HEAT_ESTATE = range(7)
+HEAT_F64, HEAT_F32 = 0, 1
+HEAT_BUILD_F64, HEAT_BUILD_F32 = 0, 1
+HEAT_EMIS_NONE, HEAT_EMIS_F64 = -1, 0
+
+_STATUS = {0: "HEAT_OK", 1: "HEAT_EINVAL", 2: "HEAT_ENOMEM", 3: "HEAT_ECUDA", 4: "HEAT_ENUMERIC",
+           5: "HEAT_ETIMEOUT", 6: "HEAT_ESTATE"}
+
+
+class HeatError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class heat_opts(ctypes.Structure):
+    _fields_ = [("build", ctypes.c_int), ("emis", ctypes.c_int), ("j_dtype", ctypes.c_int),
+                ("size_integrate", ctypes.c_int), ("cell_begin", ctypes.c_int), ("cell_count", ctypes.c_int),
+                ("chunk_cells", ctypes.c_int), ("host_io", ctypes.c_int)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+
+
+def declared_symbols():
+    """Names of the functions include/heat.h declares."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*[a-z_ ]+\*?\s*\*?(heat_[a-z0-9_]+)\s*\(", text, flags=re.M)))
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1311_4627_gb300.build.build_lib()")
+        L = ctypes.CDLL(LIB_PATH)
+        L.heat_default_opts.restype = None
+        L.heat_default_opts.argtypes = [ctypes.POINTER(heat_opts)]
+        L.heat_create_grid.restype = ctypes.c_int
+        L.heat_create_grid.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, _vp]
+        L.heat_set_grains.restype = ctypes.c_int
+        L.heat_set_grains.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.heat_set_fields.restype = ctypes.c_int
+        L.heat_set_fields.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int, _vp]
+        L.heat_solve.restype = ctypes.c_int
+        L.heat_solve.argtypes = [_vp, ctypes.POINTER(heat_opts), _vp, _vp, _vp]
+        L.heat_sync.restype = ctypes.c_int
+        L.heat_sync.argtypes = [_vp]
+        L.heat_last_error.restype = ctypes.c_char_p
+        L.heat_last_error.argtypes = [_vp]
+        L.heat_get_cooling.restype = ctypes.c_int
+        L.heat_get_cooling.argtypes = [_vp, _vp]
+        L.heat_band_elements.restype = ctypes.c_int
+        L.heat_band_elements.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong)]
+        L.heat_destroy.restype = None
+        L.heat_destroy.argtypes = [_vp]
+        _lib = L
+    return _lib
+
+
+def _ptr(x):
+    """Raw address of a torch tensor, numpy array, integer or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy arrays passed to libheat must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors passed to libheat must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _check(ctx, st):
+    if st != HEAT_OK:
+        msg = heat_last_error(ctx) if ctx else ""
+        raise HeatError(st, msg)
+
+
+def heat_default_opts(**kw) -> heat_opts:
+    o = heat_opts()
+    lib().heat_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, int(v))
+    return o
+
+
+def heat_create_grid(device: int, lam_cm) -> int:
+    lam = np.ascontiguousarray(lam_cm, dtype=np.float64)
+    h = _vp()
+    st = lib().heat_create_grid(ctypes.byref(h), int(device), lam.size, lam.ctypes.data)
+    if st != HEAT_OK:
+        raise HeatError(st, "heat_create_grid failed")
+    return h.value
+
+
+def heat_set_grains(ctx, radius_cm, c_abs_cm2, bin_offset, T_bins_K, H_bins_erg, size_weight=None):
+    r = np.ascontiguousarray(radius_cm, dtype=np.float64)
+    c = np.ascontiguousarray(c_abs_cm2, dtype=np.float64)
+    o = np.ascontiguousarray(bin_offset, dtype=np.int32)
+    t = np.ascontiguousarray(T_bins_K, dtype=np.float64)
+    e = np.ascontiguousarray(H_bins_erg, dtype=np.float64)
+    w = None if size_weight is None else np.ascontiguousarray(size_weight, dtype=np.float64)
+    st = lib().heat_set_grains(ctx, r.size, r.ctypes.data, c.ctypes.data, o.ctypes.data, t.ctypes.data,
+                               e.ctypes.data, None if w is None else w.ctypes.data)
+    _check(ctx, st)
+
+
+def heat_set_fields(ctx, n_cells, u, dtype, on_device, stream=None):
+    _check(ctx, lib().heat_set_fields(ctx, int(n_cells), _ptr(u), int(dtype), int(on_device), stream))
+
+
+def heat_solve(ctx, opts: heat_opts, P_out=None, j_out=None, stream=None):
+    _check(ctx, lib().heat_solve(ctx, ctypes.byref(opts), _ptr(P_out), _ptr(j_out), stream))
+
+
+def heat_sync(ctx):
+    _check(ctx, lib().heat_sync(ctx))
+
+
+def heat_last_error(ctx) -> str:
+    m = lib().heat_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def heat_get_cooling(ctx, nbt: int) -> np.ndarray:
+    out = np.zeros(int(nbt))
+    _check(ctx, lib().heat_get_cooling(ctx, out.ctypes.data))
+    return out
+
+
+def heat_band_elements(ctx) -> int:
+    v = ctypes.c_longlong()
+    _check(ctx, lib().heat_band_elements(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def heat_destroy(ctx):
+    if ctx:
+        lib().heat_destroy(ctx)

@@ -230,3 +230,15 @@ def field_subset(wl: Workload, cells) -> Workload:
 def custom(lam, radii, comps, nbins, u) -> Workload:
     radii, comps, cabs, off, T, E, sw = make_grains(lam, radii, comps, nbins)
     return Workload("custom", lam, radii, comps, cabs, off, T, E, sw, u=np.atleast_2d(np.asarray(u, np.float64)))
+
+
+def grain_subset(wl: Workload, grains) -> Workload:
+    """Same grid and fields, only the listed grains (in the given order)."""
+    grains = [int(g) for g in grains]
+    nb = [wl.bins(g) for g in grains]
+    off = np.zeros(len(grains) + 1, dtype=np.int32)
+    off[1:] = np.cumsum(nb)
+    T = np.concatenate([wl.T[wl.grain_slice(g)] for g in grains])
+    E = np.concatenate([wl.E[wl.grain_slice(g)] for g in grains])
+    return Workload(wl.name + f" [grains {grains}]", wl.lam, wl.radius[grains], [wl.composition[g] for g in grains],
+                    wl.cabs[grains], off, T, E, wl.size_weight[grains], u=wl.u, chi=wl.chi, hardness=wl.hardness)

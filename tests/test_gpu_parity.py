@@ -1,0 +1,169 @@
+"""GPU parity: libheat through its C ABI against the FP64 oracle (element by element)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1311_4627_gb300 import heat
+from paper_1311_4627_gb300 import workloads as W
+
+from .gpu_helpers import Lib, masked_relerr, relerr
+
+pytestmark = pytest.mark.gpu
+
+EXACT_TOL = 1e-10   # exact path: relative, over entries > 1e-280
+MIXED_TOL = 1e-3    # FP32 build: relative on j where j > 1e-6 of its peak
+
+
+@pytest.fixture(scope="module")
+def single():
+    wl = W.single_cell()
+    Cf = oracle.grain_cooling(wl)
+    P, j, led, st = oracle.solve_batch(wl, Cf, want_ledger=True)
+    assert st == oracle.OK
+    lib = Lib(wl)
+    lib.set_fields(wl.u)
+    yield wl, Cf, P, j, lib
+    lib.close()
+
+
+@pytest.fixture(scope="module")
+def batched_sub():
+    """Batched workload: 7 grains spanning 128..1024 bins, 45 cells (ragged vs 32)."""
+    full = W.batched(cells=45)
+    wl = W.grain_subset(full, [0, 5, 17, 30, 41, 52, 63])
+    Cf = oracle.grain_cooling(wl)
+    P, j, _, st = oracle.solve_batch(wl, Cf)
+    assert st == oracle.OK
+    lib = Lib(wl)
+    lib.set_fields(wl.u)
+    yield wl, Cf, P, j, lib
+    lib.close()
+
+
+def test_cooling_rates_match_oracle(single):
+    wl, Cf, _, _, lib = single
+    got = lib.cooling()
+    r, _ = relerr(got, Cf)
+    assert r < 1e-12, r
+
+
+def test_exact_path_single_cell(single):
+    wl, _, P, j, lib = single
+    Pg, jg = lib.solve(build=heat.HEAT_BUILD_F64)
+    rP, okP = relerr(Pg, P)
+    rj, okj = relerr(jg, j)
+    assert okP and okj
+    assert rP <= EXACT_TOL, rP
+    assert rj <= EXACT_TOL, rj
+    for g in range(wl.n_grains):
+        assert abs(Pg[0, wl.grain_slice(g)].sum() - 1.0) < 1e-13
+
+
+def test_mixed_build_single_cell(single):
+    wl, _, P, j, lib = single
+    Pg, jg = lib.solve(build=heat.HEAT_BUILD_F32)
+    assert masked_relerr(jg, j) <= MIXED_TOL
+
+
+def test_exact_path_batched_subset_ragged_chunks(batched_sub):
+    wl, _, P, j, lib = batched_sub
+    Pg, jg = lib.solve(build=heat.HEAT_BUILD_F64, chunk_cells=32)
+    rP, okP = relerr(Pg, P)
+    rj, okj = relerr(jg, j)
+    assert okP and okj
+    assert rP <= EXACT_TOL, rP
+    assert rj <= EXACT_TOL, rj
+
+
+def test_cooling_rates_batched_subset(batched_sub):
+    wl, Cf, _, _, lib = batched_sub
+    r, _ = relerr(lib.cooling(), Cf)
+    assert r < 1e-12, r
+
+
+def test_mixed_build_batched_subset(batched_sub):
+    wl, _, P, j, lib = batched_sub
+    _, jg = lib.solve(build=heat.HEAT_BUILD_F32)
+    assert masked_relerr(jg, j) <= MIXED_TOL
+
+
+def test_size_integration_and_f32_output(batched_sub):
+    wl, _, _, j, lib = batched_sub
+    _, J = lib.solve(want_P=False, build=heat.HEAT_BUILD_F64, size_integrate=1)
+    Jref = oracle.size_integrate(wl.size_weight, j)
+    r, ok = relerr(J, Jref)
+    assert ok and r <= EXACT_TOL, r
+    _, j32 = lib.solve(want_P=False, build=heat.HEAT_BUILD_F64, j_dtype=heat.HEAT_F32)
+    m = np.abs(j) > 1e-30
+    assert np.max(np.abs(j32[m] - j[m]) / np.abs(j[m])) < 1e-6
+
+
+def test_cell_ranges_compose_bitwise(batched_sub):
+    """Solving [0, k) and [k, n) separately equals one solve (independent spectra)."""
+    wl, _, _, _, lib = batched_sub
+    Pa, ja = lib.solve(build=heat.HEAT_BUILD_F32)
+    n = wl.n_cells
+    P1, j1 = lib.solve(build=heat.HEAT_BUILD_F32, cell_begin=0, cell_count=13)
+    P2, j2 = lib.solve(build=heat.HEAT_BUILD_F32, cell_begin=13, cell_count=n - 13)
+    assert np.array_equal(np.concatenate([P1, P2]), Pa)
+    assert np.array_equal(np.concatenate([j1, j2]), ja)
+
+
+def test_deterministic(batched_sub):
+    wl, _, _, _, lib = batched_sub
+    a = lib.solve(build=heat.HEAT_BUILD_F32)
+    b = lib.solve(build=heat.HEAT_BUILD_F32)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_zero_field_is_ground_state(single):
+    wl, Cf, _, _, lib = single
+    lib.set_fields(np.zeros((3, wl.n_lambda)))
+    try:
+        Pg, jg = lib.solve(build=heat.HEAT_BUILD_F64)
+        Pr, jr, _, _ = oracle.solve_batch(wl, Cf, u=np.zeros((3, wl.n_lambda)))
+        for g in range(wl.n_grains):
+            s = wl.grain_slice(g)
+            assert np.all(Pg[:, s][:, 0] == 1.0) and np.all(Pg[:, s][:, 1:] == 0.0)
+        r, ok = relerr(jg, jr)
+        assert ok and r <= EXACT_TOL
+    finally:
+        lib.set_fields(wl.u)
+
+
+def test_host_io_matches_device_path(single):
+    wl, _, _, _, lib = single
+    import torch
+
+    Pd, jd = lib.solve(build=heat.HEAT_BUILD_F64)
+    P = np.zeros((1, wl.total_bins))
+    j = np.zeros((1, wl.n_grains, wl.n_lambda))
+    u = np.ascontiguousarray(wl.u)
+    heat.heat_set_fields(lib.ctx, 1, u, heat.HEAT_F64, 0, torch.cuda.current_stream().cuda_stream)
+    heat.heat_solve(lib.ctx, heat.heat_default_opts(host_io=1), P, j, torch.cuda.current_stream().cuda_stream)
+    heat.heat_sync(lib.ctx)
+    assert np.array_equal(P, Pd) and np.array_equal(j, jd)
+    lib.set_fields(wl.u)
+
+
+def test_bad_field_is_reported_not_faulted(single):
+    wl, _, _, _, lib = single
+    u = wl.u.copy()
+    u[0, 17] = np.nan
+    lib.set_fields(u)
+    try:
+        with pytest.raises(heat.HeatError) as ei:
+            lib.solve(build=heat.HEAT_BUILD_F64)
+        assert ei.value.status == heat.HEAT_EINVAL
+    finally:
+        lib.set_fields(wl.u)
+    lib.solve(build=heat.HEAT_BUILD_F64)  # the context stays usable
+
+
+def test_argument_errors_are_synchronous(single):
+    wl, _, _, _, lib = single
+    with pytest.raises(heat.HeatError) as ei:
+        lib.solve(build=7)
+    assert ei.value.status == heat.HEAT_EINVAL
+    with pytest.raises(heat.HeatError):
+        lib.solve(cell_begin=0, cell_count=5)
