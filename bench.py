@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Benchmark: cell x grain emissivity spectra/s on one GB300.
+
+Workload (the batched configuration): 4096 cells x 64 grain radii (3.5 A - 1 um,
+alternating carbonaceous / silicate), 128-1024 enthalpy bins per grain, 1024
+wavelengths, three-blackbody fields with chi log-uniform in [1e-2, 1e4] and hardness
+in [-1, 1] (seeded, synthetic).  One step = one heat_solve over all cells: field
+tables, B-matrix build, FP64 recursion, renormalisation and the emissivity of every
+(cell, grain) pair, with inputs resident in HBM.
+
+Paths (``--path``): ``batched`` = FP32 matrix build, FP64 recursion, FP64 emissivity
+(the batched configuration's stated precisions); ``exact`` = FP64 everywhere.
+The JSON line adds the roofline of the dominant kernel, an end-to-end number
+through the C ABI with host buffers, the oracle timed on the host cores, and the
+SM clocks sampled during the timed region.
+
+``--impl reference`` times the FP64 oracle (plain C, OpenMP over spectra) on the
+host cores on a bounded sample of the same workload and prints the same JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell×grain emissivity spectra/s on 1 GB300: plain vs mixed vs surrogate @ rel err"
+UNIT = "spectra/s"
+FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of a GB300 (no measured figure in the peaks file)
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--path", default="batched", choices=["batched", "exact"])
+    ap.add_argument("--cells", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-exact", action="store_true", help="skip the extra exact-path measurement")
+    ap.add_argument("--oracle-cells", type=int, default=24, help="cells in the oracle sample")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------- utils
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------- oracle leg
+def oracle_sample(wl, n_cells, Cf=None):
+    """Time the FP64 oracle on the first n_cells cells x all grains (cooling untimed)."""
+    import oracle
+
+    from paper_1311_4627_gb300 import workloads as W
+
+    if Cf is None:
+        Cf = oracle.grain_cooling(wl)
+    sub = W.field_subset(wl, np.arange(n_cells))
+    threads = oracle.max_threads()
+    t0 = time.perf_counter()
+    P, j, _, st = oracle.solve_batch(sub, Cf)
+    dt = time.perf_counter() - t0
+    spectra = n_cells * wl.n_grains
+    return {"value": spectra / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n_cells} cells x {wl.n_grains} grains of the workload ({spectra} spectra, "
+                      f"{dt:.1f} s, OpenMP over spectra; cooling set-up untimed)",
+            "status": st}, P, j, Cf
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    from paper_1311_4627_gb300 import workloads as W
+
+    wl = W.batched(cells=args.cells)
+    Cf = oracle.grain_cooling(wl)
+    per_step = 2  # cells per step: a bounded sample of the workload (~1 s of CPU work)
+    times = []
+    for s in range(args.warmup + args.steps):
+        cells = np.arange(s * per_step, (s + 1) * per_step) % wl.n_cells
+        sub = W.field_subset(wl, cells)
+        t0 = time.perf_counter()
+        oracle.solve_batch(sub, Cf)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    spectra = per_step * wl.n_grains
+    ms = 1e3 * float(np.mean(times))
+    value = spectra / (ms / 1e3)
+    cores = oracle.max_threads()
+    sample = f"{per_step} cells x {wl.n_grains} grains per step (of {wl.n_cells} cells)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(wl, "oracle FP64 (CPU)"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def workload_config(wl, path):
+    nb = np.diff(wl.bin_off)
+    return {"workload": f"batched: {wl.n_cells} cells x {wl.n_grains} grains (3.5 A-1 um), "
+                        f"{int(nb.min())}-{int(nb.max())} bins, {wl.n_lambda} wavelengths",
+            "cells": wl.n_cells, "grains": wl.n_grains, "bins_total": int(wl.total_bins), "n_lambda": wl.n_lambda,
+            "path": path}
+
+
+# ---------------------------------------------------------------------------- GPU leg
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1311_4627_gb300 import heat
+    from paper_1311_4627_gb300 import workloads as W
+
+    wl = W.batched(cells=args.cells)
+    if rank > 0:  # each rank solves its own cells (weak scaling): a seeded permutation of the fields
+        rng = np.random.Generator(np.random.PCG64(5000 + rank))
+        wl.u = np.ascontiguousarray(wl.u[rng.permutation(wl.n_cells)])
+    G, N, cells = wl.n_grains, wl.n_lambda, wl.n_cells
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+
+    t0 = time.perf_counter()
+    ctx = heat.heat_create_grid(local, wl.lam)
+    heat.heat_set_grains(ctx, wl.radius, wl.cabs, wl.bin_off, wl.T, wl.E, wl.size_weight)
+    setup_s = time.perf_counter() - t0
+    band = heat.heat_band_elements(ctx)
+
+    u = torch.from_numpy(wl.u).to(dev)
+    heat.heat_set_fields(ctx, cells, u, heat.HEAT_F64, 1, sh)
+    j = torch.empty(cells, G, N, dtype=torch.float32, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def opts_for(path, timing=0, host_io=0):
+        return heat.heat_default_opts(build=heat.HEAT_BUILD_F32 if path == "batched" else heat.HEAT_BUILD_F64,
+                                      emis=heat.HEAT_EMIS_F64, j_dtype=heat.HEAT_F32, timing=timing, host_io=host_io)
+
+    def timed_run(path, steps, warmup, sample_clocks=False):
+        for _ in range(warmup):
+            heat.heat_solve(ctx, opts_for(path), None, j, sh)
+        heat.heat_sync(ctx)
+        heat.heat_get_timing(ctx, reset=True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        sampler = ClockSampler(local) if sample_clocks else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        w0 = time.perf_counter()
+        for s in range(steps):
+            flush.zero_()  # evict L2 between steps (outside the per-step events)
+            evs[s][0].record(stream)
+            heat.heat_solve(ctx, opts_for(path, timing=1), None, j, sh)
+            evs[s][1].record(stream)
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            torch.distributed.barrier()
+        wall = time.perf_counter() - w0
+        clocks = sampler.stop() if sampler else None
+        heat.heat_sync(ctx)
+        step_ms = [a.elapsed_time(b) for a, b in evs]
+        kt = heat.heat_get_timing(ctx, reset=True)
+        return float(np.mean(step_ms)), step_ms, kt, clocks, wall
+
+    ms, step_ms, kt, clocks, wall = timed_run(args.path, args.steps, args.warmup, sample_clocks=True)
+    total_ms = float(np.sum(step_ms))
+    if ws > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * cells * G * args.steps / (total_ms / 1e3)
+    gpu_launches = int(sum(n for _, n in kt.values()))
+
+    # roofline of the dominant kernel
+    dom = max(kt, key=lambda k: kt[k][0])
+    dom_ms = kt[dom][0] / max(1, kt[dom][1])
+    nbt = wl.total_bins
+    if dom == "emis":
+        launches_per_step = kt[dom][1] / args.steps
+        flops = 2.0 * cells * nbt * N / launches_per_step
+        work = f"2 x cells x total bins x wavelengths = {2.0 * cells * nbt * N:.3e} FP64 flop per step"
+    elif dom == "recur":
+        launches_per_step = kt[dom][1] / args.steps
+        flops = 2.0 * cells * (band + nbt) / launches_per_step
+        work = f"2 x cells x (band elements + rows) = {2.0 * cells * (band + nbt):.3e} FP64 flop per step"
+    else:
+        flops = float("nan")
+        work = "n/a"
+    achieved = flops / (dom_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "nominal dense FP64 1.25 TFLOP/s (profiling recipe table); FP64 FMA pipe",
+                "algorithmic_work": work}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if args.path == "batched" else "f64", "data": "synthetic",
+            "config": dict(workload_config(wl, {"batched": "FP32 build, FP64 recursion, FP64 emissivity",
+                                                "exact": "FP64 build, FP64 recursion, FP64 emissivity"}[args.path]),
+                           l2="flushed between steps (256 MiB write outside the per-step events)",
+                           band_elements_per_cell=band, grain_setup_s=round(setup_s, 3)),
+            "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
+            "roofline": roofline, "clocks": clocks, "gpu_launches": gpu_launches,
+            "wall_s_timed_region": wall}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    if not args.no_e2e:
+        u_host = torch.from_numpy(wl.u).pin_memory()
+        j_host = torch.empty(cells, G, N, dtype=torch.float32).pin_memory()
+        oe = opts_for(args.path, host_io=1)
+        for _ in range(2):
+            heat.heat_set_fields(ctx, cells, u_host, heat.HEAT_F64, 0, sh)
+            heat.heat_solve(ctx, oe, None, j_host, sh)
+        heat.heat_sync(ctx)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            heat.heat_set_fields(ctx, cells, u_host, heat.HEAT_F64, 0, sh)
+            heat.heat_solve(ctx, oe, None, j_host, sh)
+        torch.cuda.synchronize(dev)
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        heat.heat_sync(ctx)
+        line["e2e"] = {"value": ws * cells * G / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(u_host.numel() * 8),
+                       "d2h_bytes_per_step": int(j_host.numel() * 4)}
+        heat.heat_set_fields(ctx, cells, u, heat.HEAT_F64, 1, sh)
+
+    # the other exact-method path, for the plain-vs-mixed comparison
+    paths = {args.path: {"spectra_per_s": value, "ms_per_step": ms}}
+    if not args.no_exact and args.path != "exact":
+        ms_e, _, kt_e, _, _ = timed_run("exact", max(2, args.steps // 2), 1)
+        paths["exact"] = {"spectra_per_s": cells * G / (ms_e / 1e3), "ms_per_step": ms_e,
+                          "kernels_ms_per_step": {k: v[0] / max(2, args.steps // 2) for k, v in kt_e.items()}}
+
+    # oracle on the host cores (rank 0, N = 1), its outputs double as the error reference
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cb, P_ref, j_ref, Cf = oracle_sample(wl, args.oracle_cells)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        nsub = args.oracle_cells
+        for path in paths:
+            P_sub = torch.empty(nsub, nbt, dtype=torch.float64, device=dev)
+            j_sub = torch.empty(nsub, G, N, dtype=torch.float64, device=dev)
+            o_sub = heat.heat_default_opts(build=heat.HEAT_BUILD_F32 if path == "batched" else heat.HEAT_BUILD_F64,
+                                           cell_count=nsub, emis=heat.HEAT_EMIS_F64, j_dtype=heat.HEAT_F64)
+            heat.heat_solve(ctx, o_sub, P_sub, j_sub, sh)
+            heat.heat_sync(ctx)
+            Pg, jg = P_sub.cpu().numpy(), j_sub.cpu().numpy()
+            m = np.abs(P_ref) > 1e-280
+            rel_P = float(np.max(np.abs(Pg[m] - P_ref[m]) / np.abs(P_ref[m])))
+            peak = j_ref.max(axis=-1, keepdims=True)
+            mj = j_ref > 1e-6 * peak
+            rel_j = float(np.max(np.abs(jg[mj] - j_ref[mj]) / j_ref[mj]))
+            mj_all = np.abs(j_ref) > 1e-280
+            rel_j_all = float(np.max(np.abs(jg[mj_all] - j_ref[mj_all]) / np.abs(j_ref[mj_all])))
+            paths[path]["max_rel_err"] = {"P": rel_P, "j_masked_1e-6_peak": rel_j, "j_all_above_1e-280": rel_j_all,
+                                          "sample": f"{nsub} cells x {G} grains vs the FP64 oracle"}
+    line["paths"] = paths
+    if rank == 0:
+        print(json.dumps(line))
+    heat.heat_destroy(ctx)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -74,10 +74,20 @@ typedef struct heat_opts {
     int chunk_cells;    /* cells per internal chunk (multiple of 32; 0 = library default)         */
     int host_io;        /* 1: P_out and j_out are host pointers; the library stages through device
                            memory and the call returns after the results are on the host          */
+    int timing;         /* 1: record CUDA events around every kernel launch (see heat_get_timing)  */
 } heat_opts;
 
+/* kernel classes reported by heat_get_timing */
+enum {
+    HEAT_T_FIELD = 0, /* field transpose and u slopes                     */
+    HEAT_T_PREP = 1,  /* per-cell wavelength prefix tables, intra-bin terms */
+    HEAT_T_RECUR = 2, /* band-limited recursion and renormalisation (Eq. xf) */
+    HEAT_T_EMIS = 3,  /* emissivity contraction (Eq. emission)              */
+    HEAT_T_COUNT = 4
+};
+
 /* Fill *opts with defaults: exact FP64 build, FP64 emissivity, FP64 j, per-grain j,
- * all cells, device outputs. */
+ * all cells, device outputs, no timing. */
 void heat_default_opts(heat_opts* opts);
 
 /* Create a context on CUDA device `device` for the wavelength grid lambda_cm[n_lambda]
@@ -135,6 +145,12 @@ heat_status heat_get_cooling(heat_ctx* ctx, double* Cf_host);
 /* Number of band elements (f, j), j < f, that a photon on the grid can reach, summed over
  * grains: the FP64 FMAs of one spectrum set's recursion.  Errors: HEAT_ESTATE. */
 heat_status heat_band_elements(const heat_ctx* ctx, long long* per_cell);
+
+/* Device time per kernel class, summed over the launches recorded by solves with
+ * opts->timing = 1 since the last reset: ms[HEAT_T_COUNT] (milliseconds, CUDA events on
+ * the launching stream) and launches[HEAT_T_COUNT].  Waits for the recorded events.
+ * reset = 1 clears the record afterwards.  Errors: HEAT_ECUDA. */
+heat_status heat_get_timing(heat_ctx* ctx, double* ms, long long* launches, int reset);
 
 /* Release the ctx and all device memory it owns (no-op on NULL). */
 void heat_destroy(heat_ctx* ctx);

@@ -65,6 +65,23 @@ struct heat_ctx {
         s_pabs, s_P, s_j;
     int tasks_NG = -1;
     DevBuf d_status;
+    // per-kernel event timing
+    struct TimedLaunch {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<TimedLaunch> timed;
+    std::vector<cudaEvent_t> event_pool;
+    cudaEvent_t take_event() {
+        if (!event_pool.empty()) {
+            cudaEvent_t e = event_pool.back();
+            event_pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
 
     heat_status fail(heat_status s, const std::string& m) {
         err = m;
@@ -75,6 +92,22 @@ struct heat_ctx {
         return HEAT_ECUDA;
     }
 };
+
+// launch `call` on stream st, bracketed by timing events when o.timing is set
+#define TIMED(kind, call)                                  \
+    do {                                                   \
+        cudaEvent_t ea_ = nullptr, eb_ = nullptr;          \
+        if (o.timing) {                                    \
+            ea_ = ctx->take_event();                       \
+            CKR(cudaEventRecord(ea_, st));                 \
+        }                                                  \
+        CKR(call);                                         \
+        if (o.timing) {                                    \
+            eb_ = ctx->take_event();                       \
+            CKR(cudaEventRecord(eb_, st));                 \
+            ctx->timed.push_back({(kind), ea_, eb_});      \
+        }                                                  \
+    } while (0)
 
 #define CKR(call)                                         \
     do {                                                  \
@@ -150,6 +183,7 @@ void heat_default_opts(heat_opts* o) {
     o->cell_count = 0;
     o->chunk_cells = 0;
     o->host_io = 0;
+    o->timing = 0;
 }
 
 heat_status heat_create_grid(heat_ctx** out, int device, int n_lambda, const double* lambda_cm) {
@@ -517,17 +551,27 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
         ch.ldP = nbt;
         ch.P = internal_P ? ctx->s_P.as<double>() : P_out + (size_t)c0 * nbt;
         long long cell0 = (long long)c_begin + c0;
-        CKR(launch_field(gd, ctx->u_dev, ctx->u_dtype, cell0, ch, build, st));
-        CKR(launch_prep(gd, ch, build, st));
-        CKR(launch_recur(gd, ch, build, st));
+        TIMED(HEAT_T_FIELD, launch_field(gd, ctx->u_dev, ctx->u_dtype, cell0, ch, build, st));
+        TIMED(HEAT_T_PREP, launch_prep(gd, ch, build, st));
+        TIMED(HEAT_T_RECUR, launch_recur(gd, ch, build, st));
         if (want_j) {
             char* jdst = o.host_io ? ctx->s_j.as<char>() : (char*)j_out + (size_t)c0 * jrow * jel;
+            cudaEvent_t ta = nullptr;
+            if (o.timing) {
+                ta = ctx->take_event();
+                CKR(cudaEventRecord(ta, st));
+            }
             if (o.size_integrate)
                 CKR(launch_gemm_f64(cells, N, 1, ctx->d_koff_all.as<int>(), ch.P, nbt, ctx->d_Kw.as<double>(), N, jdst,
                                     N, 0, o.j_dtype == HEAT_F32, st));
             else
                 CKR(launch_gemm_f64(cells, N, G, ctx->d_bin_off.as<int>(), ch.P, nbt, ctx->d_K.as<double>(), N, jdst,
                                     (long long)G * N, N, o.j_dtype == HEAT_F32, st));
+            if (o.timing) {
+                cudaEvent_t tb = ctx->take_event();
+                CKR(cudaEventRecord(tb, st));
+                ctx->timed.push_back({HEAT_T_EMIS, ta, tb});
+            }
             if (o.host_io)
                 CKR(cudaMemcpyAsync((char*)j_out + (size_t)c0 * jrow * jel, jdst, (size_t)cells * jrow * jel,
                                     cudaMemcpyDeviceToHost, st));
@@ -563,6 +607,32 @@ heat_status heat_get_cooling(heat_ctx* ctx, double* Cf) {
     return HEAT_OK;
 }
 
+heat_status heat_get_timing(heat_ctx* ctx, double* ms, long long* launches, int reset) {
+    if (!ctx) return HEAT_EINVAL;
+    CKR(cudaSetDevice(ctx->device));
+    double acc[HEAT_T_COUNT] = {0, 0, 0, 0};
+    long long cnt[HEAT_T_COUNT] = {0, 0, 0, 0};
+    for (auto& t : ctx->timed) {
+        CKR(cudaEventSynchronize(t.b));
+        float v = 0.0f;
+        CKR(cudaEventElapsedTime(&v, t.a, t.b));
+        acc[t.kind] += v;
+        cnt[t.kind] += 1;
+    }
+    for (int k = 0; k < HEAT_T_COUNT; ++k) {
+        if (ms) ms[k] = acc[k];
+        if (launches) launches[k] = cnt[k];
+    }
+    if (reset) {
+        for (auto& t : ctx->timed) {
+            ctx->event_pool.push_back(t.a);
+            ctx->event_pool.push_back(t.b);
+        }
+        ctx->timed.clear();
+    }
+    return HEAT_OK;
+}
+
 heat_status heat_band_elements(const heat_ctx* ctx, long long* per_cell) {
     if (!ctx || !per_cell) return HEAT_EINVAL;
     if (ctx->G == 0) return HEAT_ESTATE;
@@ -581,6 +651,11 @@ void heat_destroy(heat_ctx* ctx) {
                       &ctx->s_su32, &ctx->s_phi64, &ctx->s_aq64, &ctx->s_q64, &ctx->s_phi32, &ctx->s_intra64,
                       &ctx->s_intra32, &ctx->s_xs, &ctx->s_pabs, &ctx->s_P, &ctx->s_j, &ctx->d_status};
     for (DevBuf* b : bufs) b->release();
+    for (auto& t : ctx->timed) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     delete ctx;
 }
 

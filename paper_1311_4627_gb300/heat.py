@@ -22,6 +22,8 @@ HEAT_OK, HEAT_EINVAL, HEAT_ENOMEM, HEAT_ECUDA, HEAT_ENUMERIC, HEAT_ETIMEOUT, HEA
 HEAT_F64, HEAT_F32 = 0, 1
 HEAT_BUILD_F64, HEAT_BUILD_F32 = 0, 1
 HEAT_EMIS_NONE, HEAT_EMIS_F64 = -1, 0
+HEAT_T_FIELD, HEAT_T_PREP, HEAT_T_RECUR, HEAT_T_EMIS, HEAT_T_COUNT = range(5)
+TIMING_NAMES = ("field", "prep", "recur", "emis")
 
 _STATUS = {0: "HEAT_OK", 1: "HEAT_EINVAL", 2: "HEAT_ENOMEM", 3: "HEAT_ECUDA", 4: "HEAT_ENUMERIC",
            5: "HEAT_ETIMEOUT", 6: "HEAT_ESTATE"}
@@ -36,7 +38,7 @@ class HeatError(RuntimeError):
 class heat_opts(ctypes.Structure):
     _fields_ = [("build", ctypes.c_int), ("emis", ctypes.c_int), ("j_dtype", ctypes.c_int),
                 ("size_integrate", ctypes.c_int), ("cell_begin", ctypes.c_int), ("cell_count", ctypes.c_int),
-                ("chunk_cells", ctypes.c_int), ("host_io", ctypes.c_int)]
+                ("chunk_cells", ctypes.c_int), ("host_io", ctypes.c_int), ("timing", ctypes.c_int)]
 
 
 _lib = None
@@ -73,6 +75,8 @@ def lib():
         L.heat_get_cooling.argtypes = [_vp, _vp]
         L.heat_band_elements.restype = ctypes.c_int
         L.heat_band_elements.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong)]
+        L.heat_get_timing.restype = ctypes.c_int
+        L.heat_get_timing.argtypes = [_vp, _vp, _vp, ctypes.c_int]
         L.heat_destroy.restype = None
         L.heat_destroy.argtypes = [_vp]
         _lib = L
@@ -158,6 +162,14 @@ def heat_band_elements(ctx) -> int:
     v = ctypes.c_longlong()
     _check(ctx, lib().heat_band_elements(ctx, ctypes.byref(v)))
     return v.value
+
+
+def heat_get_timing(ctx, reset=True):
+    """{kernel class: (ms, launches)} recorded by solves with timing=1."""
+    ms = np.zeros(HEAT_T_COUNT)
+    n = np.zeros(HEAT_T_COUNT, dtype=np.int64)
+    _check(ctx, lib().heat_get_timing(ctx, ms.ctypes.data, n.ctypes.data, int(reset)))
+    return {TIMING_NAMES[k]: (float(ms[k]), int(n[k])) for k in range(HEAT_T_COUNT)}
 
 
 def heat_destroy(ctx):
