@@ -152,6 +152,32 @@ heat_status heat_band_elements(const heat_ctx* ctx, long long* per_cell);
  * reset = 1 clears the record afterwards.  Errors: HEAT_ECUDA. */
 heat_status heat_get_timing(heat_ctx* ctx, double* ms, long long* launches, int reset);
 
+/* ---- Solve without allocating (the paper has no counterpart) -------------------------
+ * For callers that cannot allocate device memory once their loop runs: codes that keep
+ * the GPU under a fixed memory budget owned by their own allocator, and time-critical
+ * loops that cannot pay for cudaMalloc/cudaFree, which wait for the whole device to go
+ * idle and so stall every other stream.  Such callers create the ctx, set the grains
+ * (which allocates) once up front, then call this in the loop.
+ *
+ * Computes P exactly as heat_solve does (same kernels, same results) for the FP64 fields
+ * u_dev[n_cells][n_lambda] (device) into P_out[n_cells][bin_offset[n_grains]] (device, FP64),
+ * with build = HEAT_BUILD_F64 or HEAT_BUILD_F32, on `cuda_stream`; no emissivity.  It uses
+ * no memory but the caller's buffers, the ctx's grain tables and one static device array of
+ * HEAT_NOALLOC_SCRATCH_BYTES that every GPU which loads the library keeps until exit; it
+ * calls no allocating routine.
+ *   - The first call on each device looks up the array's device address with that device
+ *     current (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls on a device share the array and it keeps the last call's contents: calls
+ *     whose work overlaps on the GPU (other streams or host threads) race.  Serialise them.
+ *   - Cells are processed in groups of 32; one group needs
+ *       G*N*32*(24 bytes FP64 build | 4 bytes FP32 build) + nbt*32*(16 | 12) + N*32*(16 | 8) + G*8 + 2048
+ *     bytes (G grains, N wavelengths, nbt total bins).  If that exceeds the array, the call
+ *     returns HEAT_EINVAL with a message (heat_last_error) and queues nothing.
+ * Errors: HEAT_EINVAL, HEAT_ESTATE (grains not set), HEAT_ECUDA; device-side errors at heat_sync. */
+#define HEAT_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+heat_status heat_solve_noalloc(heat_ctx* ctx, int build, const double* u_dev, int n_cells, double* P_out,
+                               void* cuda_stream);
+
 /* Release the ctx and all device memory it owns (no-op on NULL). */
 void heat_destroy(heat_ctx* ctx);
 

@@ -660,3 +660,39 @@ void heat_destroy(heat_ctx* ctx) {
 }
 
 }  // extern "C"
+
+// Internal (not part of the C ABI): read-only view of a ctx's grain tables for the
+// no-allocation solve in noalloc.cu.
+__attribute__((visibility("hidden"))) heat_status heat_internal_grain_view(heat_ctx* ctx, GrainDev* gd, int* device,
+                                                                           int** status) {
+    if (!ctx) return HEAT_EINVAL;
+    if (ctx->G == 0) return ctx->fail(HEAT_ESTATE, "heat_solve_noalloc: grains not set");
+    gd->N = ctx->N;
+    gd->G = ctx->G;
+    gd->nbt = ctx->nbt;
+    gd->lam = ctx->d_lam.as<double>();
+    gd->dln = ctx->d_dln.as<double>();
+    gd->bin_off = ctx->d_bin_off.as<int>();
+    gd->Cact = ctx->d_Cact.as<double>();
+    gd->sC = ctx->d_sC.as<double>();
+    gd->lam32 = ctx->d_lam32.as<float>();
+    gd->dln32 = ctx->d_dln32.as<float>();
+    gd->ca32 = ctx->d_ca32.as<float>();
+    gd->ce32 = ctx->d_ce32.as<float>();
+    gd->sC32 = ctx->d_sC32.as<float>();
+    gd->invdE32 = ctx->d_invdE32.as<float>();
+    gd->invC = ctx->d_invC.as<double>();
+    gd->invdE = ctx->d_invdE.as<double>();
+    gd->rowptr = ctx->d_rowptr.as<int>();
+    gd->el64 = ctx->d_el64.as<ElemF64>();
+    gd->el32 = ctx->d_el32.as<ElemF32>();
+    gd->soft = ctx->d_soft.as<SoftF64>();
+    gd->soft_off = ctx->d_soft_off.as<int>();
+    *device = ctx->device;
+    *status = ctx->d_status.as<int>();
+    return HEAT_OK;
+}
+
+__attribute__((visibility("hidden"))) void heat_internal_fail(heat_ctx* ctx, const char* msg) {
+    if (ctx) ctx->err = msg;
+}

@@ -77,6 +77,8 @@ def lib():
         L.heat_band_elements.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong)]
         L.heat_get_timing.restype = ctypes.c_int
         L.heat_get_timing.argtypes = [_vp, _vp, _vp, ctypes.c_int]
+        L.heat_solve_noalloc.restype = ctypes.c_int
+        L.heat_solve_noalloc.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]
         L.heat_destroy.restype = None
         L.heat_destroy.argtypes = [_vp]
         _lib = L
@@ -170,6 +172,13 @@ def heat_get_timing(ctx, reset=True):
     n = np.zeros(HEAT_T_COUNT, dtype=np.int64)
     _check(ctx, lib().heat_get_timing(ctx, ms.ctypes.data, n.ctypes.data, int(reset)))
     return {TIMING_NAMES[k]: (float(ms[k]), int(n[k])) for k in range(HEAT_T_COUNT)}
+
+
+def heat_solve_noalloc(ctx, build, u_dev, n_cells, P_out, stream=None):
+    _check(ctx, lib().heat_solve_noalloc(ctx, int(build), _ptr(u_dev), int(n_cells), _ptr(P_out), stream))
+
+
+HEAT_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
 def heat_destroy(ctx):
