@@ -8,8 +8,13 @@ in [-1, 1] (seeded, synthetic).  One step = one heat_solve over all cells: field
 tables, B-matrix build, FP64 recursion, renormalisation and the emissivity of every
 (cell, grain) pair, with inputs resident in HBM.
 
-Paths (``--path``): ``batched`` = FP32 matrix build, FP64 recursion, FP64 emissivity
-(the batched configuration's stated precisions); ``exact`` = FP64 everywhere.
+Paths (``--path``):
+  ``mixed``      FP32 matrix build, FP64 recursion, BF16x3 tensor-core emissivity (default)
+  ``mixed_tf32`` FP32 matrix build, FP64 recursion, TF32x3 tensor-core emissivity
+  ``batched``    FP32 matrix build, FP64 recursion, FP64 emissivity
+  ``exact``      FP64 everywhere (the plain path)
+The headline line reports ``--path``; the other exact-method paths are timed after it
+for the plain-vs-mixed comparison (``paths``), each with its error against the oracle.
 The JSON line adds the roofline of the dominant kernel, an end-to-end number
 through the C ABI with host buffers, the oracle timed on the host cores, and the
 SM clocks sampled during the timed region.
@@ -35,6 +40,12 @@ sys.path.insert(0, ROOT)
 METRIC = "cell×grain emissivity spectra/s on 1 GB300: plain vs mixed vs surrogate @ rel err"
 UNIT = "spectra/s"
 FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of a GB300 (no measured figure in the peaks file)
+PATHS = {  # name: (build, emissivity, description, dtype)
+    "mixed": ("f32", "bf16x3", "FP32 build, FP64 recursion, BF16x3 tensor-core emissivity", "f32+f64+bf16"),
+    "mixed_tf32": ("f32", "tf32x3", "FP32 build, FP64 recursion, TF32x3 tensor-core emissivity", "f32+f64+tf32"),
+    "batched": ("f32", "f64", "FP32 build, FP64 recursion, FP64 emissivity", "f32+f64"),
+    "exact": ("f64", "f64", "FP64 build, FP64 recursion, FP64 emissivity", "f64"),
+}
 L2_BYTES = 129 * 1024 * 1024
 
 
@@ -44,11 +55,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--path", default="batched", choices=["batched", "exact"])
+    ap.add_argument("--path", default="mixed", choices=list(PATHS))
     ap.add_argument("--cells", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-exact", action="store_true", help="skip the extra exact-path measurement")
+    ap.add_argument("--no-compare", action="store_true", help="time only --path")
     ap.add_argument("--oracle-cells", type=int, default=24, help="cells in the oracle sample")
     return ap.parse_args()
 
@@ -224,9 +235,12 @@ def main():
     j = torch.empty(cells, G, N, dtype=torch.float32, device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
 
-    def opts_for(path, timing=0, host_io=0):
-        return heat.heat_default_opts(build=heat.HEAT_BUILD_F32 if path == "batched" else heat.HEAT_BUILD_F64,
-                                      emis=heat.HEAT_EMIS_F64, j_dtype=heat.HEAT_F32, timing=timing, host_io=host_io)
+    emis_code = {"f64": heat.HEAT_EMIS_F64, "bf16x3": heat.HEAT_EMIS_BF16X3, "tf32x3": heat.HEAT_EMIS_TF32X3}
+
+    def opts_for(path, timing=0, host_io=0, **kw):
+        b, e, _, _ = PATHS[path]
+        return heat.heat_default_opts(build=heat.HEAT_BUILD_F32 if b == "f32" else heat.HEAT_BUILD_F64,
+                                      emis=emis_code[e], j_dtype=heat.HEAT_F32, timing=timing, host_io=host_io, **kw)
 
     def timed_run(path, steps, warmup, sample_clocks=False):
         for _ in range(warmup):
@@ -266,36 +280,50 @@ def main():
     value = ws * cells * G * args.steps / (total_ms / 1e3)
     gpu_launches = int(sum(n for _, n in kt.values()))
 
-    # roofline of the dominant kernel
-    dom = max(kt, key=lambda k: kt[k][0])
-    dom_ms = kt[dom][0] / max(1, kt[dom][1])
+    # roofline of every kernel class, the dominant one as "roofline"
     nbt = wl.total_bins
-    if dom == "emis":
-        launches_per_step = kt[dom][1] / args.steps
-        flops = 2.0 * cells * nbt * N / launches_per_step
-        work = f"2 x cells x total bins x wavelengths = {2.0 * cells * nbt * N:.3e} FP64 flop per step"
-    elif dom == "recur":
-        launches_per_step = kt[dom][1] / args.steps
-        flops = 2.0 * cells * (band + nbt) / launches_per_step
-        work = f"2 x cells x (band elements + rows) = {2.0 * cells * (band + nbt):.3e} FP64 flop per step"
-    else:
-        flops = float("nan")
-        work = "n/a"
-    achieved = flops / (dom_ms / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "nominal dense FP64 1.25 TFLOP/s (profiling recipe table); FP64 FMA pipe",
-                "algorithmic_work": work}
+    peaks, peaks_src = measured_peaks()
+    rooflines = {}
+    for name, (tot_ms, n_launch) in kt.items():
+        if n_launch == 0:
+            continue
+        per_step = n_launch / args.steps
+        launch_ms = tot_ms / n_launch
+        if name == "recur":
+            work = 2.0 * cells * (band + nbt)
+            r = {"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
+                 "peak_source": "nominal dense FP64 1.25 TFLOP/s (profiling recipe table)",
+                 "algorithmic_work": f"2 x cells x (band elements + rows) = {work:.3e} FP64 flop per step"}
+        elif name == "emis" and PATHS[args.path][1] == "f64":
+            work = 2.0 * cells * nbt * N
+            r = {"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
+                 "peak_source": "nominal dense FP64 1.25 TFLOP/s (profiling recipe table)",
+                 "algorithmic_work": f"2 x cells x total bins x wavelengths = {work:.3e} FP64 flop per step"}
+        elif name == "emis":
+            work = 2.0 * cells * nbt * N
+            tf32 = PATHS[args.path][1].startswith("tf32")
+            pk = peaks["bf16_tflops"] / (2.0 if tf32 else 1.0)
+            r = {"bound": "tensor", "unit": "TFLOP/s", "peak": pk,
+                 "peak_source": ("measured bf16 burst" + (" x 1/2 (nominal tf32:bf16 ratio)" if tf32 else "")
+                                 + f" ({peaks_src})"),
+                 "algorithmic_work": f"2 x cells x total bins x wavelengths = {work:.3e} flop per step "
+                                     f"(the split executes 3x this on the tensor pipe, plus operand packing)"}
+        else:
+            continue
+        ach = work / per_step / (launch_ms / 1e3) / 1e12
+        r.update({"kernel": name, "achieved": ach, "frac": ach / r["peak"], "traffic": None})
+        rooflines[name] = r
+    dom = max(rooflines, key=lambda k: kt[k][0])
+    roofline = dict(rooflines[dom])
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64" if args.path == "batched" else "f64", "data": "synthetic",
-            "config": dict(workload_config(wl, {"batched": "FP32 build, FP64 recursion, FP64 emissivity",
-                                                "exact": "FP64 build, FP64 recursion, FP64 emissivity"}[args.path]),
+            "vs_baseline": None, "dtype": PATHS[args.path][3], "data": "synthetic",
+            "config": dict(workload_config(wl, PATHS[args.path][2]),
                            l2="flushed between steps (256 MiB write outside the per-step events)",
                            band_elements_per_cell=band, grain_setup_s=round(setup_s, 3)),
             "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
-            "roofline": roofline, "clocks": clocks, "gpu_launches": gpu_launches,
+            "roofline": roofline, "kernel_rooflines": rooflines, "clocks": clocks, "gpu_launches": gpu_launches,
             "wall_s_timed_region": wall}
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
@@ -319,12 +347,20 @@ def main():
                        "d2h_bytes_per_step": int(j_host.numel() * 4)}
         heat.heat_set_fields(ctx, cells, u, heat.HEAT_F64, 1, sh)
 
-    # the other exact-method path, for the plain-vs-mixed comparison
-    paths = {args.path: {"spectra_per_s": value, "ms_per_step": ms}}
-    if not args.no_exact and args.path != "exact":
-        ms_e, _, kt_e, _, _ = timed_run("exact", max(2, args.steps // 2), 1)
-        paths["exact"] = {"spectra_per_s": cells * G / (ms_e / 1e3), "ms_per_step": ms_e,
-                          "kernels_ms_per_step": {k: v[0] / max(2, args.steps // 2) for k, v in kt_e.items()}}
+    # the other exact-method paths, for the plain-vs-mixed comparison
+    paths = {args.path: {"spectra_per_s": value, "ms_per_step": ms, "precision": PATHS[args.path][2]}}
+    if not args.no_compare:
+        for other in PATHS:
+            if other == args.path:
+                continue
+            k2 = max(2, args.steps // 2)
+            ms_o, _, kt_o, _, _ = timed_run(other, k2, 1)
+            paths[other] = {"spectra_per_s": cells * G / (ms_o / 1e3), "ms_per_step": ms_o,
+                            "precision": PATHS[other][2],
+                            "kernels_ms_per_step": {k: v[0] / k2 for k, v in kt_o.items()}}
+        base = paths["exact"]["spectra_per_s"]
+        for v in paths.values():
+            v["x_plain_exact"] = v["spectra_per_s"] / base
 
     # oracle on the host cores (rank 0, N = 1), its outputs double as the error reference
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -334,8 +370,8 @@ def main():
         for path in paths:
             P_sub = torch.empty(nsub, nbt, dtype=torch.float64, device=dev)
             j_sub = torch.empty(nsub, G, N, dtype=torch.float64, device=dev)
-            o_sub = heat.heat_default_opts(build=heat.HEAT_BUILD_F32 if path == "batched" else heat.HEAT_BUILD_F64,
-                                           cell_count=nsub, emis=heat.HEAT_EMIS_F64, j_dtype=heat.HEAT_F64)
+            o_sub = opts_for(path, cell_count=nsub)
+            o_sub.j_dtype = heat.HEAT_F64
             heat.heat_solve(ctx, o_sub, P_sub, j_sub, sh)
             heat.heat_sync(ctx)
             Pg, jg = P_sub.cpu().numpy(), j_sub.cpu().numpy()

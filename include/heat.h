@@ -60,15 +60,22 @@ enum { HEAT_BUILD_F64 = 0, HEAT_BUILD_F32 = 1 };
 
 /* emissivity contraction (Eq. emission) */
 enum {
-    HEAT_EMIS_NONE = -1, /* no emissivity */
-    HEAT_EMIS_F64 = 0    /* FP64 FMA contraction (exact path) */
+    HEAT_EMIS_NONE = -1,  /* no emissivity */
+    HEAT_EMIS_F64 = 0,    /* FP64 FMA contraction (exact path) */
+    HEAT_EMIS_BF16X3 = 1, /* tensor cores: P and K scaled by powers of two per (cell, grain) row and
+                             per (grain, wavelength) column, split into BF16 hi + lo, three products
+                             (hi*hi + hi*lo + lo*hi) accumulated in FP32 */
+    HEAT_EMIS_TF32X3 = 2, /* same with TF32 hi + lo */
+    HEAT_EMIS_BF16 = 3,   /* single BF16 product (hi*hi), FP32 accumulation */
+    HEAT_EMIS_TF32 = 4    /* single TF32 product, FP32 accumulation */
 };
 
 typedef struct heat_opts {
     int build;          /* HEAT_BUILD_F64 (exact) or HEAT_BUILD_F32 (mixed)                      */
     int emis;           /* HEAT_EMIS_*                                                             */
     int j_dtype;        /* HEAT_F64 or HEAT_F32 element type of j_out                              */
-    int size_integrate; /* 0: j_out is [cells][grains][n_lambda]; 1: [cells][n_lambda], sum_g w_g j_g */
+    int size_integrate; /* 0: j_out is [cells][grains][n_lambda]; 1: [cells][n_lambda], sum_g w_g j_g
+                           (size integration needs HEAT_EMIS_F64 for now)                         */
     int cell_begin;     /* first cell solved (0-based)                                             */
     int cell_count;     /* cells solved; <= 0 means all cells from cell_begin                      */
     int chunk_cells;    /* cells per internal chunk (multiple of 32; 0 = library default)         */
@@ -80,7 +87,7 @@ typedef struct heat_opts {
 /* kernel classes reported by heat_get_timing */
 enum {
     HEAT_T_FIELD = 0, /* field transpose and u slopes                     */
-    HEAT_T_PREP = 1,  /* per-cell wavelength prefix tables, intra-bin terms */
+    HEAT_T_BUILD = 1, /* matrix build: B band (Eq. bmatrix) and intra-bin terms */
     HEAT_T_RECUR = 2, /* band-limited recursion and renormalisation (Eq. xf) */
     HEAT_T_EMIS = 3,  /* emissivity contraction (Eq. emission)              */
     HEAT_T_COUNT = 4
@@ -170,8 +177,9 @@ heat_status heat_get_timing(heat_ctx* ctx, double* ms, long long* launches, int 
  *   - All calls on a device share the array and it keeps the last call's contents: calls
  *     whose work overlaps on the GPU (other streams or host threads) race.  Serialise them.
  *   - Cells are processed in groups of 32; one group needs
- *       G*N*32*(24 bytes FP64 build | 4 bytes FP32 build) + nbt*32*(16 | 12) + N*32*(16 | 8) + G*8 + 2048
- *     bytes (G grains, N wavelengths, nbt total bins).  If that exceeds the array, the call
+ *       band*32*(8 bytes FP64 build | 4 bytes FP32 build) + nbt*32*10 + N*32*(16 | 8) + G*8 + 2304
+ *     bytes (band = heat_band_elements, G grains, N wavelengths, nbt total bins).  If that
+ *     exceeds the array, the call
  *     returns HEAT_EINVAL with a message (heat_last_error) and queues nothing.
  * Errors: HEAT_EINVAL, HEAT_ESTATE (grains not set), HEAT_ECUDA; device-side errors at heat_sync. */
 #define HEAT_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)

@@ -19,18 +19,21 @@ constexpr int kStatTimeout = 4;   // bounded wait gave up
 constexpr double kRescaleBig = 0x1p800;     // exact power of two
 constexpr double kRescaleSmall = 0x1p-800;
 
-// Band element of the exact (FP64) build: wavelength segment and log offset.
-struct ElemF64 {
-    int n;       // segment index; N-1 means the abscissa is past the last node
+// Pattern entry of a band element, grouped by wavelength segment (the matrix build walks
+// the segments in order and fills every element whose transition wavelength
+// hc/(Elo_f - E_j) lies in the current one).  e is the element's index in the band
+// storage (row-major over f, then j); t = ln(lambda_fj / lambda_n), 0 past the last node.
+struct PatF64 {
+    int e;
     int pad;
-    double t;    // ln(lambda_fj / lambda_n) (0 for n = N-1)
+    double t;
 };
 
-// Band element of the FP32 build.  With a_n = u_n * ca_n and z = (su_n + s2_n) t:
-//   B_fj = Phi_n + u_n * cat * E1(fma(su_n, t, zt)),   cat = ca_n t,  zt = s2_n t,
-// where ca_n = C_n lambda_n^2 / h (0 on an inactive C segment), s2_n = sC_n + 2.
-struct ElemF32 {
-    int n;
+// FP32 build: with a_n = u_n ca_n and z = (su_n + sC_n + 2) t,
+//   B = Phi_n + u_n cat E1(fma(su_n, t, zt)),   cat = ca_n t,  zt = (sC_n + 2) t,
+// where ca_n = C_n lambda_n^2 / h (0 on an inactive C segment).
+struct PatF32 {
+    int e;
     float t;
     float cat;
     float zt;
@@ -39,14 +42,25 @@ struct ElemF32 {
 // Soft-photon abscissa for the intra-bin term of row j+1:
 // lambda_s = hc / (Elo_{j+1} - E_j) in segment n with offset t; n = -1 below the
 // grid (all absorbed power counts), n = N-1 at or above the last node (none).
+// The term is added to the diagonal band element (j+1, j), at band index e_diag;
+// diag_in_band = 0 when that element's transition wavelength is below the grid (its
+// photon part is zero and only the intra-bin term remains).
 struct SoftF64 {
     int j;
     int n;
     double t;
+    int e_diag;
+    int diag_in_band;
 };
 
+// X > 2^800 for a positive finite double, tested on the exponent bits (integer pipe).
+__device__ __forceinline__ bool above_rescale(double x) {
+    return __double2hiint(x) > (int)((1023 + 800) << 20) - 1;
+}
+
 // E1(z) = (e^z - 1)/z in FP32: Taylor series for |z| < 0.5 (truncation below
-// 2^-24 relative), library expm1f otherwise.
+// 1.2e-8 relative); for |z| >= 0.5, where e^z - 1 has no cancellation, the fast
+// exponential (relative error a few 1e-7).
 __device__ __forceinline__ float e1f(float z) {
     if (fabsf(z) < 0.5f) {
         float p = 1.0f / 40320.0f;
@@ -59,7 +73,8 @@ __device__ __forceinline__ float e1f(float z) {
         p = fmaf(p, z, 1.0f);
         return p;
     }
-    return expm1f(z) / z;
+    // |z| >= 0.5: e^z - 1 loses no digits here; hardware exp2 and a fast divide
+    return __fdividef(__expf(z) - 1.0f, z);
 }
 
 // E1(z) in FP64 (library expm1; exact at z = 0).

@@ -7,8 +7,11 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "../../include/heat.h"
 #include "common.cuh"
+#include "emis_tc.h"
 #include "internal.h"
 
 using namespace heat;
@@ -54,17 +57,27 @@ struct heat_ctx {
     long long band_per_cell = 0;
     std::vector<int> grain_order;
     DevBuf d_bin_off, d_cabs, d_T, d_E, d_Cf, d_invC, d_invdE, d_invdE32, d_Cact, d_sC, d_ca32, d_ce32, d_sC32,
-        d_rowptr, d_el64, d_el32, d_soft, d_soft_off, d_K, d_Kw, d_w, d_koff_all;
+        d_rowptr, d_seg_ptr, d_pat64, d_pat32, d_soft, d_soft_off, d_K, d_Kw, d_w, d_koff_all;
     // fields
     int n_cells = 0;
     const void* u_dev = nullptr;
     int u_dtype = 0;
     DevBuf d_u_own;
     // chunk scratch
-    DevBuf s_tasks, s_ua64, s_su64, s_ua32, s_su32, s_phi64, s_aq64, s_q64, s_phi32, s_intra64, s_intra32, s_xs,
-        s_pabs, s_P, s_j;
+    DevBuf s_tasks, s_ua64, s_su64, s_ua32, s_Bb64, s_Bb32, s_xs, s_ep, s_pabs, s_P, s_j;
     int tasks_NG = -1;
     DevBuf d_status;
+    int sms = 0;
+    // tensor-core emissivity operands, per mode (index = HEAT_EMIS_*)
+    struct TcMode {
+        bool built = false;
+        DevBuf B, colscale, kp, boff, aoff;
+        std::vector<int> kp_h;
+        std::vector<long long> boff_h, aoff_h;
+        int aoff_cells = -1;
+        std::vector<int> order;  // grains by K extent, largest first
+    } tc[5];
+    DevBuf s_A, s_rowscale;
     // per-kernel event timing
     struct TimedLaunch {
         int kind;
@@ -169,7 +182,118 @@ cudaError_t upload(DevBuf& b, const std::vector<T>& v) {
     return cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        cudaDriverEntryPointQueryResult q;
+        void* f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+    }
+    return fn;
+}
+
+// 2D K-major operand map: rows x kp elements, 128-byte swizzle, box = (128-byte slice, box_rows).
+bool encode_operand(CUtensorMap* m, void* base, bool tf32, long long kp, long long rows, int box_rows) {
+    auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    size_t es = tf32 ? 4 : 2;
+    cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(kp * es)};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims,
+                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+bool mode_tf32(int m) { return m == HEAT_EMIS_TF32X3 || m == HEAT_EMIS_TF32; }
+bool mode_split(int m) { return m == HEAT_EMIS_BF16X3 || m == HEAT_EMIS_TF32X3; }
+
 }  // namespace
+
+// Build the per-grain B' operands and column scales of a tensor-core mode (once per mode).
+static heat_status ensure_tc_mode(heat_ctx* ctx, int m, cudaStream_t st) {
+    auto& t = ctx->tc[m];
+    if (t.built) return HEAT_OK;
+    const int G = ctx->G, N = ctx->N;
+    const bool tf32 = mode_tf32(m), split = mode_split(m);
+    const int ke = tf32 ? 32 : 64;
+    t.kp_h.resize(G);
+    t.boff_h.resize(G + 1);
+    t.boff_h[0] = 0;
+    for (int g = 0; g < G; ++g) {
+        int nb = ctx->bin_off[g + 1] - ctx->bin_off[g];
+        int k = (split ? 3 : 1) * nb;
+        t.kp_h[g] = (k + ke - 1) / ke * ke;
+        t.boff_h[g + 1] = t.boff_h[g] + (long long)N * t.kp_h[g];
+    }
+    t.order.resize(G);
+    for (int g = 0; g < G; ++g) t.order[g] = g;
+    std::stable_sort(t.order.begin(), t.order.end(), [&](int a, int b) { return t.kp_h[a] > t.kp_h[b]; });
+    size_t es = tf32 ? 4 : 2;
+    if (t.B.ensure(es * (size_t)t.boff_h[G]) || t.colscale.ensure(sizeof(float) * (size_t)G * N) ||
+        upload(t.kp, t.kp_h) || upload(t.boff, t.boff_h))
+        return ctx->fail(HEAT_ENOMEM, "heat_solve: allocation of tensor-core operands failed");
+    CKR(launch_pack_k(N, G, ctx->d_bin_off.as<int>(), ctx->d_K.as<double>(), t.boff.as<long long>(), t.kp.as<int>(),
+                      split, tf32, t.B.p, t.colscale.as<float>(), st));
+    t.built = true;
+    return HEAT_OK;
+}
+
+// Tensor-core emissivity of one chunk whose P rows are ready at P (row stride nbt).
+static heat_status emis_tc_chunk(heat_ctx* ctx, int m, const double* P, int cells, int Cc_alloc, void* jdst,
+                                 bool j_f64, cudaStream_t st) {
+    auto& t = ctx->tc[m];
+    const int G = ctx->G, N = ctx->N;
+    const bool tf32 = mode_tf32(m), split = mode_split(m);
+    const size_t es = tf32 ? 4 : 2;
+    if (t.aoff_cells != Cc_alloc) {
+        t.aoff_h.assign(G + 1, 0);
+        for (int g = 0; g < G; ++g) t.aoff_h[g + 1] = t.aoff_h[g] + (long long)Cc_alloc * t.kp_h[g];
+        CKR(cudaStreamSynchronize(st));
+        if (upload(t.aoff, t.aoff_h)) return ctx->fail(HEAT_ENOMEM, "heat_solve: allocation failed");
+        t.aoff_cells = Cc_alloc;
+    }
+    if (ctx->s_A.ensure(es * (size_t)t.aoff_h[G]) || ctx->s_rowscale.ensure(sizeof(float) * (size_t)Cc_alloc * G))
+        return ctx->fail(HEAT_ENOMEM, "heat_solve: allocation of tensor-core operands failed");
+    CKR(launch_pack_p(cells, G, ctx->d_bin_off.as<int>(), P, ctx->nbt, t.aoff.as<long long>(), t.kp.as<int>(), split,
+                      tf32, ctx->s_A.p, ctx->s_rowscale.as<float>(), st));
+    EmisTcParams prm;  // ~25 KB of tensor maps, copied into the launch's parameters
+    for (int g0 = 0; g0 < G; g0 += kMaxTcGrains) {
+        int ng = std::min(kMaxTcGrains, G - g0);
+        std::memset(&prm, 0, sizeof(prm));
+        for (int i = 0; i < ng; ++i) {
+            int g = t.order[g0 + i];
+            char* abase = (char*)ctx->s_A.p + es * (size_t)t.aoff_h[g];
+            char* bbase = (char*)t.B.p + es * (size_t)t.boff_h[g];
+            if (!encode_operand(&prm.ta[i], abase, tf32, t.kp_h[g], cells, 128) ||
+                !encode_operand(&prm.tb[i], bbase, tf32, t.kp_h[g], N, 256))
+                return ctx->fail(HEAT_ECUDA, "heat_solve: cuTensorMapEncodeTiled failed");
+            prm.ksteps[i] = t.kp_h[g] / (tf32 ? 32 : 64);
+            prm.grain[i] = g;
+        }
+        prm.ng = ng;
+        prm.cells = cells;
+        prm.N = N;
+        prm.G = G;
+        prm.mtiles = (cells + 127) / 128;
+        prm.ntiles = (N + 255) / 256;
+        prm.rowscale = ctx->s_rowscale.as<float>();
+        prm.colscale = t.colscale.as<float>();
+        prm.j = jdst;
+        prm.ldj = (long long)G * N;
+        prm.j_f64 = j_f64 ? 1 : 0;
+        prm.status = ctx->d_status.as<int>();
+        CKR(launch_emis_tc(prm, tf32, ctx->sms, st));
+    }
+    return HEAT_OK;
+}
 
 extern "C" {
 
@@ -215,6 +339,8 @@ heat_status heat_create_grid(heat_ctx** out, int device, int n_lambda, const dou
         return cleanup(HEAT_ENOMEM);
     if (ctx->d_status.ensure(sizeof(int)) != cudaSuccess) return cleanup(HEAT_ENOMEM);
     if (cudaMemset(ctx->d_status.p, 0, sizeof(int)) != cudaSuccess) return cleanup(HEAT_ECUDA);
+    if (cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return cleanup(HEAT_ECUDA);
     double glx[kGLPoints], glw[kGLPoints];
     gauss_legendre(kGLPoints, glx, glw);
     if (set_gauss_legendre(glx, glw) != cudaSuccess) return cleanup(HEAT_ECUDA);
@@ -259,6 +385,10 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
     ctx->w.assign(G, 0.0);
     if (size_weight) std::copy(size_weight, size_weight + G, ctx->w.begin());
     ctx->tasks_NG = -1;
+    for (auto& t : ctx->tc) {
+        t.built = false;
+        t.aoff_cells = -1;
+    }
 
     // per-grain cross-section tables
     std::vector<double> Cact((size_t)G * N, 0.0), sC((size_t)G * N, 0.0);
@@ -281,13 +411,19 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
     std::vector<float> invdE32(nbt, 0.0f);
     std::vector<int> rowptr;
     rowptr.reserve(nbt + G);
-    std::vector<ElemF64> el64;
-    std::vector<ElemF32> el32;
+    std::vector<PatF64> pat64;
+    std::vector<PatF32> pat32;
+    std::vector<int> seg_ptr((size_t)G * (N + 1), 0);
     std::vector<SoftF64> soft;
     std::vector<int> soft_off(G + 1, 0);
     std::vector<int> bin_grain(nbt);
     std::vector<long long> cost(G, 0);
     long long band_total = 0;
+    struct Ent {
+        int n, e;
+        double t;
+    };
+    std::vector<int> diag_e(nbt, 0), diag_ok(nbt, 0);
     for (int g = 0; g < G; ++g) {
         const int off = bin_offset[g], nb = bin_offset[g + 1] - off, M = nb - 1;
         const double* E = H_bins_erg + off;
@@ -300,66 +436,97 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
             invdE32[off + j] = (float)invdE[off + j];
         }
         long long band = 0;
+        std::vector<Ent> ents;
         // row 0 has no elements
-        rowptr.push_back((int)el64.size());
+        rowptr.push_back((int)band_total);
         for (int f = 1; f <= M; ++f) {
-            rowptr.push_back((int)el64.size());
+            rowptr.push_back((int)(band_total + band));
             int jlo = f;
             for (int j = f - 1; j >= 0; --j) {
                 if (kHChost / (Elo[f] - E[j]) < lam[0]) break;
                 jlo = j;
             }
+            // the diagonal element (f, f-1) is always stored: it carries the intra-bin
+            // term even when no photon on the grid reaches bin f from bin f-1
+            const bool diag_in_band = jlo < f;
+            if (!diag_in_band) jlo = f - 1;
+            diag_e[off + f - 1] = (int)(band_total + band + (f - 1 - jlo));
+            diag_ok[off + f - 1] = diag_in_band ? 1 : 0;
             for (int j = jlo; j < f; ++j) {
                 double lf = kHChost / (Elo[f] - E[j]);
-                ElemF64 a;
-                ElemF32 b;
-                a.pad = 0;
-                if (lf >= lam[N - 1]) {
-                    a.n = N - 1;
-                    a.t = 0.0;
-                } else {
-                    a.n = segment_of(lam, lf);
-                    a.t = std::log(lf / lam[a.n]);
+                Ent en;
+                en.e = (int)(band_total + band);
+                if (!diag_in_band) {  // below the grid: no photon part, no pattern entry
+                    ++band;
+                    continue;
                 }
-                size_t k = (size_t)g * N + a.n;
-                double ca = (a.n < N - 1) ? Cact[k] * lam[a.n] * lam[a.n] / kHhost : 0.0;
-                double s2 = (a.n < N - 1) ? sC[k] + 2.0 : 0.0;
-                b.n = a.n;
-                b.t = (float)a.t;
-                b.cat = (float)(ca * a.t);
-                b.zt = (float)(s2 * a.t);
-                el64.push_back(a);
-                el32.push_back(b);
+                if (lf >= lam[N - 1]) {
+                    en.n = N - 1;
+                    en.t = 0.0;
+                } else {
+                    en.n = segment_of(lam, lf);
+                    en.t = std::log(lf / lam[en.n]);
+                }
+                ents.push_back(en);
                 ++band;
             }
         }
-        rowptr.push_back((int)el64.size());
+        rowptr.push_back((int)(band_total + band));
+        // pattern: the grain's elements grouped by segment
+        std::stable_sort(ents.begin(), ents.end(), [](const Ent& a, const Ent& b) { return a.n < b.n; });
+        size_t base = pat64.size();
+        size_t k = 0;
+        for (int n = 0; n <= N; ++n) {
+            while (k < ents.size() && ents[k].n < n) ++k;
+            seg_ptr[(size_t)g * (N + 1) + n] = (int)(base + k);
+        }
+        for (const Ent& en : ents) {
+            size_t kk = (size_t)g * N + en.n;
+            double ca = (en.n < N - 1) ? Cact[kk] * lam[en.n] * lam[en.n] / kHhost : 0.0;
+            double s2 = (en.n < N - 1) ? sC[kk] + 2.0 : 0.0;
+            PatF64 a;
+            a.e = en.e;
+            a.pad = en.n;
+            a.t = en.t;
+            PatF32 b;
+            b.e = en.e;
+            b.t = (float)en.t;
+            b.cat = (float)(ca * en.t);
+            b.zt = (float)(s2 * en.t);
+            pat64.push_back(a);
+            pat32.push_back(b);
+        }
         // soft-photon abscissae, sorted by segment, descending
         soft_off[g] = (int)soft.size();
         std::vector<SoftF64> sg;
         for (int j = 0; j < M; ++j) {
             double ls = kHChost / (Elo[j + 1] - E[j]);
-            SoftF64 s;
-            s.j = j;
+            SoftF64 sf;
+            sf.j = j;
+            sf.e_diag = diag_e[off + j];
+            sf.diag_in_band = diag_ok[off + j];
             if (ls < lam[0]) {
-                s.n = -1;
-                s.t = 0.0;
+                sf.n = -1;
+                sf.t = 0.0;
             } else if (ls >= lam[N - 1]) {
-                s.n = N - 1;
-                s.t = 0.0;
+                sf.n = N - 1;
+                sf.t = 0.0;
             } else {
-                s.n = segment_of(lam, ls);
-                s.t = std::log(ls / lam[s.n]);
+                sf.n = segment_of(lam, ls);
+                sf.t = std::log(ls / lam[sf.n]);
             }
-            sg.push_back(s);
+            sg.push_back(sf);
         }
         std::stable_sort(sg.begin(), sg.end(), [](const SoftF64& a, const SoftF64& b) { return a.n > b.n; });
         soft.insert(soft.end(), sg.begin(), sg.end());
         band_total += band;
-        cost[g] = band + 4LL * nb + N;
+        if (band_total * 32 >= 0x7fffffffLL)
+            return ctx->fail(HEAT_EINVAL, "heat_set_grains: band of the grains too large (over 6.7e7 elements)");
+        // task order (longest first): a row costs about as much as 12 band elements in
+        // the recursion (its chain waits on dependent FP64 ops), so many-row grains start early
+        cost[g] = band + 12LL * nb;
     }
     soft_off[G] = (int)soft.size();
-    if (el64.size() > (size_t)0x7fffffff) return ctx->fail(HEAT_EINVAL, "heat_set_grains: band tables too large");
     ctx->band_per_cell = band_total;
     ctx->grain_order.resize(G);
     for (int g = 0; g < G; ++g) ctx->grain_order[g] = g;
@@ -372,8 +539,8 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
     if (upload(ctx->d_bin_off, boff) || upload(ctx->d_cabs, cabs) || upload(ctx->d_T, T) || upload(ctx->d_E, E) ||
         upload(ctx->d_invdE, invdE) || upload(ctx->d_invdE32, invdE32) || upload(ctx->d_Cact, Cact) ||
         upload(ctx->d_sC, sC) || upload(ctx->d_ca32, ca32) || upload(ctx->d_ce32, ce32) ||
-        upload(ctx->d_sC32, sC32) || upload(ctx->d_rowptr, rowptr) || upload(ctx->d_el64, el64) ||
-        upload(ctx->d_el32, el32) || upload(ctx->d_soft, soft) || upload(ctx->d_soft_off, soft_off) ||
+        upload(ctx->d_sC32, sC32) || upload(ctx->d_rowptr, rowptr) || upload(ctx->d_pat64, pat64) ||
+        upload(ctx->d_pat32, pat32) || upload(ctx->d_seg_ptr, seg_ptr) || upload(ctx->d_soft, soft) || upload(ctx->d_soft_off, soft_off) ||
         upload(ctx->d_w, ctx->w))
         return ctx->fail(HEAT_ENOMEM, "heat_set_grains: device allocation failed");
     std::vector<int> koff_all = {0, nbt};
@@ -433,10 +600,12 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
     if (ctx->G == 0) return ctx->fail(HEAT_ESTATE, "heat_solve: grains not set");
     if (!ctx->u_dev && ctx->n_cells > 0) return ctx->fail(HEAT_ESTATE, "heat_solve: fields not set");
     const heat_opts& o = *opts;
-    if ((o.build != HEAT_BUILD_F64 && o.build != HEAT_BUILD_F32) || (o.emis != HEAT_EMIS_NONE && o.emis != HEAT_EMIS_F64) ||
+    if ((o.build != HEAT_BUILD_F64 && o.build != HEAT_BUILD_F32) || o.emis < HEAT_EMIS_NONE || o.emis > HEAT_EMIS_TF32 ||
         (o.j_dtype != HEAT_F64 && o.j_dtype != HEAT_F32))
         return ctx->fail(HEAT_EINVAL, "heat_solve: bad precision option");
     if (o.size_integrate && !ctx->has_w) return ctx->fail(HEAT_EINVAL, "heat_solve: size integration needs weights");
+    if (o.size_integrate && o.emis > HEAT_EMIS_F64)
+        return ctx->fail(HEAT_EINVAL, "heat_solve: size integration needs HEAT_EMIS_F64");
     if (o.chunk_cells < 0 || (o.chunk_cells % 32) != 0)
         return ctx->fail(HEAT_EINVAL, "heat_solve: chunk_cells must be a non-negative multiple of 32");
     int c_begin = o.cell_begin, count = o.cell_count > 0 ? o.cell_count : ctx->n_cells - o.cell_begin;
@@ -452,11 +621,12 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
     const size_t jel = o.j_dtype == HEAT_F64 ? 8 : 4;
     const size_t jrow = (size_t)(o.size_integrate ? 1 : G) * N;
 
-    // chunk size: bound the per-task wavelength tables to ~2 GiB
+    // chunk size: bound the scratch of one chunk (B band, X history, field tables) to ~16 GiB
     int chunk = o.chunk_cells;
     if (chunk == 0) {
-        size_t per_group = (size_t)G * N * 32 * (build == 0 ? 24 : 4) + (size_t)nbt * 32 * 16;
-        size_t groups = std::max<size_t>(1, (size_t(2) << 30) / per_group);
+        size_t per_group = (size_t)ctx->band_per_cell * 32 * (build == 0 ? 8 : 4) + (size_t)nbt * 32 * 10 +
+                           (size_t)N * 32 * 16;
+        size_t groups = std::max<size_t>(1, (size_t(16) << 30) / per_group);
         chunk = (int)std::min<size_t>(groups * 32, 16384);
     }
     int span = std::min(count, chunk);
@@ -469,17 +639,13 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
     if (build == 0) {
         ok &= !ctx->s_ua64.ensure(sizeof(double) * (size_t)N * Cc);
         ok &= !ctx->s_su64.ensure(sizeof(double) * (size_t)N * Cc);
-        ok &= !ctx->s_phi64.ensure(sizeof(double) * tasks_n * N * 32);
-        ok &= !ctx->s_aq64.ensure(sizeof(double) * tasks_n * N * 32);
-        ok &= !ctx->s_q64.ensure(sizeof(double) * tasks_n * N * 32);
-        ok &= !ctx->s_intra64.ensure(sizeof(double) * (size_t)NG * nbt * 32);
+        ok &= !ctx->s_Bb64.ensure(sizeof(double) * (size_t)NG * std::max(1LL, ctx->band_per_cell) * 32);
     } else {
-        ok &= !ctx->s_ua32.ensure(sizeof(float) * (size_t)N * Cc);
-        ok &= !ctx->s_su32.ensure(sizeof(float) * (size_t)N * Cc);
-        ok &= !ctx->s_phi32.ensure(sizeof(float) * tasks_n * N * 32);
-        ok &= !ctx->s_intra32.ensure(sizeof(float) * (size_t)NG * nbt * 32);
+        ok &= !ctx->s_ua32.ensure(sizeof(float2) * (size_t)N * Cc);  // (u, slope) pairs
+        ok &= !ctx->s_Bb32.ensure(sizeof(float) * (size_t)NG * std::max(1LL, ctx->band_per_cell) * 32);
     }
     ok &= !ctx->s_xs.ensure(sizeof(double) * (size_t)NG * nbt * 32);
+    ok &= !ctx->s_ep.ensure(sizeof(unsigned short) * (size_t)NG * nbt * 32);
     ok &= !ctx->s_pabs.ensure(sizeof(double) * (size_t)Cc * G);
     bool internal_P = (P_out == nullptr) || o.host_io;
     if (internal_P) ok &= !ctx->s_P.ensure(sizeof(double) * (size_t)Cc * nbt);
@@ -512,11 +678,18 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
     gd.invC = ctx->d_invC.as<double>();
     gd.invdE = ctx->d_invdE.as<double>();
     gd.rowptr = ctx->d_rowptr.as<int>();
-    gd.el64 = ctx->d_el64.as<ElemF64>();
-    gd.el32 = ctx->d_el32.as<ElemF32>();
+    gd.band_total = ctx->band_per_cell;
+    gd.seg_ptr = ctx->d_seg_ptr.as<int>();
+    gd.pat64 = ctx->d_pat64.as<PatF64>();
+    gd.pat32 = ctx->d_pat32.as<PatF32>();
     gd.soft = ctx->d_soft.as<SoftF64>();
     gd.soft_off = ctx->d_soft_off.as<int>();
 
+    if (want_j && o.emis > HEAT_EMIS_F64) {
+        if (!tensor_map_encoder()) return ctx->fail(HEAT_ECUDA, "heat_solve: cuTensorMapEncodeTiled unavailable");
+        heat_status hs = ensure_tc_mode(ctx, o.emis, st);
+        if (hs != HEAT_OK) return hs;
+    }
     for (int c0 = 0; c0 < count; c0 += chunk) {
         int cells = std::min(chunk, count - c0);
         int cc_pad = (cells + 31) / 32 * 32;
@@ -538,21 +711,17 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
         ch.ua64 = ctx->s_ua64.as<double>();
         ch.su64 = ctx->s_su64.as<double>();
         ch.ua32 = ctx->s_ua32.as<float>();
-        ch.su32 = ctx->s_su32.as<float>();
-        ch.phi64 = ctx->s_phi64.as<double>();
-        ch.aq64 = ctx->s_aq64.as<double>();
-        ch.q64 = ctx->s_q64.as<double>();
-        ch.phi32 = ctx->s_phi32.as<float>();
-        ch.intra64 = ctx->s_intra64.as<double>();
-        ch.intra32 = ctx->s_intra32.as<float>();
+        ch.Bb64 = ctx->s_Bb64.as<double>();
+        ch.Bb32 = ctx->s_Bb32.as<float>();
         ch.xs = ctx->s_xs.as<double>();
+        ch.ep = ctx->s_ep.as<unsigned short>();
         ch.pabs = ctx->s_pabs.as<double>();
         ch.status = ctx->d_status.as<int>();
         ch.ldP = nbt;
         ch.P = internal_P ? ctx->s_P.as<double>() : P_out + (size_t)c0 * nbt;
         long long cell0 = (long long)c_begin + c0;
         TIMED(HEAT_T_FIELD, launch_field(gd, ctx->u_dev, ctx->u_dtype, cell0, ch, build, st));
-        TIMED(HEAT_T_PREP, launch_prep(gd, ch, build, st));
+        TIMED(HEAT_T_BUILD, launch_build(gd, ch, build, st));
         TIMED(HEAT_T_RECUR, launch_recur(gd, ch, build, st));
         if (want_j) {
             char* jdst = o.host_io ? ctx->s_j.as<char>() : (char*)j_out + (size_t)c0 * jrow * jel;
@@ -561,7 +730,10 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
                 ta = ctx->take_event();
                 CKR(cudaEventRecord(ta, st));
             }
-            if (o.size_integrate)
+            if (o.emis > HEAT_EMIS_F64) {
+                heat_status hs = emis_tc_chunk(ctx, o.emis, ch.P, cells, Cc, jdst, o.j_dtype == HEAT_F64, st);
+                if (hs != HEAT_OK) return hs;
+            } else if (o.size_integrate)
                 CKR(launch_gemm_f64(cells, N, 1, ctx->d_koff_all.as<int>(), ch.P, nbt, ctx->d_Kw.as<double>(), N, jdst,
                                     N, 0, o.j_dtype == HEAT_F32, st));
             else
@@ -645,12 +817,20 @@ void heat_destroy(heat_ctx* ctx) {
     cudaSetDevice(ctx->device);
     DevBuf* bufs[] = {&ctx->d_lam, &ctx->d_dln, &ctx->d_lam32, &ctx->d_dln32, &ctx->d_bin_off, &ctx->d_cabs,
                       &ctx->d_T, &ctx->d_E, &ctx->d_Cf, &ctx->d_invC, &ctx->d_invdE, &ctx->d_invdE32, &ctx->d_Cact,
-                      &ctx->d_sC, &ctx->d_ca32, &ctx->d_ce32, &ctx->d_sC32, &ctx->d_rowptr, &ctx->d_el64,
-                      &ctx->d_el32, &ctx->d_soft, &ctx->d_soft_off, &ctx->d_K, &ctx->d_Kw, &ctx->d_w,
+                      &ctx->d_sC, &ctx->d_ca32, &ctx->d_ce32, &ctx->d_sC32, &ctx->d_rowptr, &ctx->d_seg_ptr,
+                      &ctx->d_pat64, &ctx->d_pat32, &ctx->d_soft, &ctx->d_soft_off, &ctx->d_K, &ctx->d_Kw, &ctx->d_w,
                       &ctx->d_koff_all, &ctx->d_u_own, &ctx->s_tasks, &ctx->s_ua64, &ctx->s_su64, &ctx->s_ua32,
-                      &ctx->s_su32, &ctx->s_phi64, &ctx->s_aq64, &ctx->s_q64, &ctx->s_phi32, &ctx->s_intra64,
-                      &ctx->s_intra32, &ctx->s_xs, &ctx->s_pabs, &ctx->s_P, &ctx->s_j, &ctx->d_status};
+                      &ctx->s_Bb64, &ctx->s_Bb32, &ctx->s_xs, &ctx->s_ep, &ctx->s_pabs, &ctx->s_P, &ctx->s_j, &ctx->d_status};
     for (DevBuf* b : bufs) b->release();
+    for (auto& t : ctx->tc) {
+        t.B.release();
+        t.colscale.release();
+        t.kp.release();
+        t.boff.release();
+        t.aoff.release();
+    }
+    ctx->s_A.release();
+    ctx->s_rowscale.release();
     for (auto& t : ctx->timed) {
         cudaEventDestroy(t.a);
         cudaEventDestroy(t.b);
@@ -684,8 +864,10 @@ __attribute__((visibility("hidden"))) heat_status heat_internal_grain_view(heat_
     gd->invC = ctx->d_invC.as<double>();
     gd->invdE = ctx->d_invdE.as<double>();
     gd->rowptr = ctx->d_rowptr.as<int>();
-    gd->el64 = ctx->d_el64.as<ElemF64>();
-    gd->el32 = ctx->d_el32.as<ElemF32>();
+    gd->band_total = ctx->band_per_cell;
+    gd->seg_ptr = ctx->d_seg_ptr.as<int>();
+    gd->pat64 = ctx->d_pat64.as<PatF64>();
+    gd->pat32 = ctx->d_pat32.as<PatF32>();
     gd->soft = ctx->d_soft.as<SoftF64>();
     gd->soft_off = ctx->d_soft_off.as<int>();
     *device = ctx->device;

@@ -6,8 +6,8 @@ namespace heat {
 
 constexpr int kGLPoints = 16;
 
-struct ElemF64;
-struct ElemF32;
+struct PatF64;
+struct PatF32;
 struct SoftF64;
 
 // ---- grain set-up (k_setup.cu)
@@ -38,9 +38,12 @@ struct GrainDev {
     const double* invC;     // [nbt] 1/T_{f-1,f} (0 where the cooling rate is 0 and for f = 0)
     const double* invdE;    // [nbt] 1/(E_{j+1}-E_j) (0 for the last bin)
     const int* rowptr;      // [nbt + G] per grain, rows f = 0..M: band elements of row f at
-                            //   rowptr[off_g + g + f] .. rowptr[off_g + g + f + 1]
-    const ElemF64* el64;    // band elements (FP64 build)
-    const ElemF32* el32;    // band elements (FP32 build)
+                            //   rowptr[off_g + g + f] .. rowptr[off_g + g + f + 1] (global indices)
+    long long band_total;   // band elements of all grains (per cell)
+    const int* seg_ptr;     // [G][N+1] pattern entries of grain g in segment n at
+                            //   seg_ptr[g*(N+1)+n] .. seg_ptr[g*(N+1)+n+1]
+    const PatF64* pat64;    // pattern entries (FP64 build)
+    const PatF32* pat32;    // pattern entries (FP32 build)
     const SoftF64* soft;    // [nbt - G] per grain, sorted by segment (descending)
     const int* soft_off;    // [G+1] start of each grain's soft list
 };
@@ -54,13 +57,13 @@ struct ChunkDev {
     int n_tasks;
     // field tables, transposed [N][Cc]
     double* ua64; double* su64;
-    float* ua32; float* su32;
-    // per-task wavelength tables [task][N][32]
-    double* phi64; double* aq64; double* q64;
-    float* phi32;
+    float* ua32; float* su32;  // FP32 build: su32 unused; ua32 holds float2 (u_n, su_n) pairs
+    // band of B, [NG][band_total][32]: element e of group grp, lane l at (grp*band_total + e)*32 + l
+    double* Bb64;
+    float* Bb32;
     // per-group bin arrays [NG][nbt][32]
-    double* intra64; float* intra32;
     double* xs;         // X history of the recursion
+    unsigned short* ep; // rescale epoch at which each stored X was last written
     double* pabs;       // [Cc][G] absorbed power c int Omega dlambda (erg/s)
     double* P;          // [Cc][nbt] output distributions (row stride ldP)
     long long ldP;
@@ -69,7 +72,7 @@ struct ChunkDev {
 
 cudaError_t launch_field(const GrainDev& g, const void* u, int dtype, long long cell0, const ChunkDev& ch, int build,
                          cudaStream_t st);
-cudaError_t launch_prep(const GrainDev& g, const ChunkDev& ch, int build, cudaStream_t st);
+cudaError_t launch_build(const GrainDev& g, const ChunkDev& ch, int build, cudaStream_t st);
 cudaError_t launch_recur(const GrainDev& g, const ChunkDev& ch, int build, cudaStream_t st);
 
 // ---- emissivity (k_emis.cu)

@@ -1,0 +1,499 @@
+// Emissivity contraction on the tensor cores (Eq. emission, Eq. emission-lambda):
+//   j[c][g][n] = 2^{eP[c,g]} 2^{eK[g,n]} sum_k A'_g[c][k] B'_g[n][k]
+// with A' = the cell's P of grain g divided by its power-of-two row scale and B' = the
+// grain's Planck kernel C_abs B_lambda(T_i) [E_i >= hc/lambda] divided by its power-of-two
+// column scale, both rounded to BF16 or TF32.  In the split modes the k axis holds three
+// copies of the bins, [P_hi | P_hi | P_lo] against [K_hi | K_lo | K_hi], so one GEMM sums
+// P_hi K_hi + P_hi K_lo + P_lo K_hi with FP32 accumulation.
+//
+// tcgen05 GEMM, one persistent CTA per SM, warp-specialised:
+//   warp 0 lane 0 : TMA producer (2D tiled loads, 128B swizzle) into a 4-stage smem ring
+//   warp 1 lane 0 : MMA issuer (tcgen05.mma cta_group::1, M=128 N=256, FP32 in TMEM)
+//   warps 2..5    : epilogue (tcgen05.ld -> scale -> smem transpose -> coalesced stores)
+// Two TMEM accumulators (2 x 256 columns) let the epilogue of one tile overlap the MMAs
+// of the next.  Every mbarrier wait is bounded; on timeout the kernel flags
+// kStatTimeout, drains its own copies and MMAs with bounded waits, frees TMEM and exits.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+#include "common.cuh"
+#include "emis_tc.h"
+
+namespace heat {
+
+namespace {
+
+constexpr int kM = 128, kN = 256, kStages = 4;
+constexpr int kAStage = kM * 128;  // bytes: 128 rows x 128 B
+constexpr int kBStage = kN * 128;  // bytes: 256 rows x 128 B
+constexpr int kEpiWarps = 4;
+constexpr int kEpiTile = 32 * 33;  // floats per epilogue warp (32 x 32, padded)
+constexpr long long kSpinLimit = 1LL << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait; false when the limit is hit or another role has aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+    for (long long i = 0; i < kSpinLimit; ++i) {
+        if (mbar_try(bar, parity)) return true;
+        if ((i & 255) == 255 && *abort_flag) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// UMMA shared-memory descriptor: K-major operand tile, 128-byte swizzle, rows of 128 B
+// grouped in 8-row (1024 B) atoms.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);  // start address
+    d |= (uint64_t)1 << 16;                    // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset: next 8-row atom
+    d |= (uint64_t)1 << 46;                    // descriptor version
+    d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: D = F32, A/B K-major, M = 128, N = 256; a/b format 1 = BF16
+// (kind::f16) or 2 = TF32 (kind::tf32).
+__device__ __forceinline__ uint32_t idesc(int ab_format) {
+    uint32_t d = 0;
+    d |= 1u << 4;                         // D format F32
+    d |= (uint32_t)ab_format << 7;        // A format
+    d |= (uint32_t)ab_format << 10;       // B format
+    d |= (uint32_t)(kN >> 3) << 17;       // N
+    d |= (uint32_t)(kM >> 4) << 24;       // M
+    return d;
+}
+
+template <bool TF32>
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t id, uint32_t accum) {
+    if (TF32)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(id), "r"(accum)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(id), "r"(accum)
+            : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tile_of(const EmisTcParams& p, int t, int& gi, int& mt, int& nt) {
+    int per = p.mtiles * p.ntiles;
+    gi = t / per;
+    int r = t - gi * per;
+    mt = r / p.ntiles;
+    nt = r - mt * p.ntiles;
+}
+
+}  // namespace
+
+template <bool TF32>
+__global__ void __launch_bounds__(192, 1) k_emis_tc(const __grid_constant__ EmisTcParams p) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* sA = smem;
+    unsigned char* sB = smem + kStages * kAStage;
+    uint64_t* bars = (uint64_t*)(sB + kStages * kBStage);
+    // bars: full[kStages], empty[kStages], tfull[2], tempty[2], done
+    float* epi = (float*)(bars + 2 * kStages + 5);
+    uint32_t* tmem_slot = (uint32_t*)(epi + kEpiWarps * kEpiTile);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t b_full = smem_u32(bars), b_empty = smem_u32(bars + kStages);
+    const uint32_t b_tfull = smem_u32(bars + 2 * kStages), b_tempty = smem_u32(bars + 2 * kStages + 2);
+    const uint32_t b_done = smem_u32(bars + 2 * kStages + 4);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(b_full + 8 * s, 1);
+            mbar_init(b_empty + 8 * s, 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(b_tfull + 8 * a, 1);
+            mbar_init(b_tempty + 8 * a, kEpiWarps);
+        }
+        mbar_init(b_done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        tc_fence_before();
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const int total = p.ng * p.mtiles * p.ntiles;
+    const int KE = TF32 ? 32 : 64;  // elements per 128-byte k slice
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer
+            int stage = 0;
+            uint32_t phase = 0;
+            int last_phase[kStages];
+            for (int s = 0; s < kStages; ++s) last_phase[s] = -1;
+            bool ok = true;
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+                int gi, mt, nt;
+                tile_of(p, t, gi, mt, nt);
+                for (int ks = 0; ks < p.ksteps[gi]; ++ks) {
+                    if (!mbar_wait(b_empty + 8 * stage, phase ^ 1, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(b_full + 8 * stage, kAStage + kBStage);
+                    tma_load_2d(smem_u32(sA + stage * kAStage), &p.ta[gi], ks * KE, mt * kM, b_full + 8 * stage);
+                    tma_load_2d(smem_u32(sB + stage * kBStage), &p.tb[gi], ks * KE, nt * kN, b_full + 8 * stage);
+                    last_phase[stage] = (int)phase;
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                }
+            }
+            if (!ok) {
+                atomicOr(p.status, kStatTimeout);
+                *abort_flag = 1;
+            }
+            // every copy this thread issued has landed before the CTA may exit
+            for (int s = 0; s < kStages; ++s)
+                if (last_phase[s] >= 0) {
+                    for (long long i = 0; i < kSpinLimit; ++i)
+                        if (mbar_try(b_full + 8 * s, (uint32_t)last_phase[s])) break;
+                }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer
+            const uint32_t id = idesc(TF32 ? 2 : 1);
+            int stage = 0, acc = 0;
+            uint32_t phase = 0, acc_phase = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+                int gi, mt, nt;
+                tile_of(p, t, gi, mt, nt);
+                if (!mbar_wait(b_tempty + 8 * acc, acc_phase ^ 1, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem_base + (uint32_t)acc * kN;
+                for (int ks = 0; ks < p.ksteps[gi]; ++ks) {
+                    if (!mbar_wait(b_full + 8 * stage, phase, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t a0 = sdesc(smem_u32(sA + stage * kAStage));
+                    const uint64_t b0 = sdesc(smem_u32(sB + stage * kBStage));
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        umma<TF32>(d, a0 + 2 * kk, b0 + 2 * kk, id, (ks | kk) != 0 ? 1u : 0u);
+                    umma_commit(b_empty + 8 * stage);
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                }
+                if (!ok) break;
+                umma_commit(b_tfull + 8 * acc);
+                if (++acc == 2) {
+                    acc = 0;
+                    acc_phase ^= 1;
+                }
+            }
+            if (!ok) {
+                atomicOr(p.status, kStatTimeout);
+                *abort_flag = 1;
+            }
+            // all MMAs this thread issued have completed before TMEM is freed
+            umma_commit(b_done);
+            for (long long i = 0; i < kSpinLimit; ++i)
+                if (mbar_try(b_done, 0)) break;
+        }
+    } else {
+        // ---------------- epilogue: warps 2..5 own TMEM lane quarters (warp % 4)
+        const int q = warp & 3;
+        float* st = epi + (warp - 2) * kEpiTile;
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        for (int t = blockIdx.x; t < total; t += gridDim.x) {
+            int gi, mt, nt;
+            tile_of(p, t, gi, mt, nt);
+            bool ok = __all_sync(0xffffffffu, mbar_wait(b_tfull + 8 * acc, acc_phase, abort_flag));
+            if (!ok) {  // warp-uniform: the tcgen05.ld below is a warp-wide instruction
+                if (lane == 0) {
+                    atomicOr(p.status, kStatTimeout);
+                    *abort_flag = 1;
+                }
+                break;
+            }
+            tc_fence_after();
+            const int g = p.grain[gi];
+            const int row0 = mt * kM + q * 32;
+            const int my_row = row0 + lane;
+            const float rs = my_row < p.cells ? p.rowscale[(size_t)my_row * p.G + g] : 0.0f;
+            for (int c = 0; c < kN / 32; ++c) {
+                uint32_t v[32];
+                tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kN + c * 32), v);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) st[lane * 33 + i] = __uint_as_float(v[i]);
+                __syncwarp();
+                const int col = nt * kN + c * 32 + lane;
+                const float cs = col < p.N ? p.colscale[(size_t)g * p.N + col] : 0.0f;
+                for (int r = 0; r < 32; ++r) {
+                    const float rsr = __shfl_sync(0xffffffffu, rs, r);
+                    const int row = row0 + r;
+                    if (row < p.cells && col < p.N) {
+                        size_t o = (size_t)row * p.ldj + (size_t)g * p.N + col;
+                        float val = st[r * 33 + lane];
+                        if (p.j_f64)
+                            ((double*)p.j)[o] = (double)val * (double)rsr * (double)cs;
+                        else
+                            ((float*)p.j)[o] = val * rsr * cs;
+                    }
+                }
+                __syncwarp();
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(b_tempty + 8 * acc);
+            if (++acc == 2) {
+                acc = 0;
+                acc_phase ^= 1;
+            }
+        }
+    }
+    __syncwarp();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem_base) : "memory");
+    }
+}
+
+size_t emis_tc_smem_bytes() {
+    return 1024 + (size_t)kStages * (kAStage + kBStage) + (2 * kStages + 5) * 8 + kEpiWarps * kEpiTile * 4 + 16;
+}
+
+cudaError_t launch_emis_tc(const EmisTcParams& p, bool tf32, int sms, cudaStream_t st) {
+    int total = p.ng * p.mtiles * p.ntiles;
+    if (total <= 0) return cudaSuccess;
+    size_t smem = emis_tc_smem_bytes();
+    int grid = total < sms ? total : sms;
+    if (tf32) {
+        cudaError_t e = cudaFuncSetAttribute(k_emis_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_emis_tc<true><<<grid, 192, smem, st>>>(p);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(k_emis_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_emis_tc<false><<<grid, 192, smem, st>>>(p);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Operand packing.
+
+__device__ __forceinline__ uint16_t bf16_rn(float x) {
+    return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+__device__ __forceinline__ float bf16_f(uint16_t h) { return __bfloat162float(__ushort_as_bfloat16(h)); }
+
+// Round an FP32 value to TF32 (10 explicit mantissa bits), ties away from zero.
+__device__ __forceinline__ float tf32_rn(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// Split a value already scaled into [0, 1] into hi + lo for the operand format.
+__device__ __forceinline__ void split_bf16(double v, uint16_t& hi, uint16_t& lo) {
+    hi = bf16_rn((float)v);
+    lo = bf16_rn((float)(v - (double)bf16_f(hi)));
+}
+__device__ __forceinline__ void split_tf32(double v, float& hi, float& lo) {
+    hi = tf32_rn((float)v);
+    lo = tf32_rn((float)(v - (double)hi));
+}
+
+__device__ __forceinline__ int scale_exp(double m) {
+    // smallest e with m / 2^e < 1 (m > 0); 0 for m == 0
+    if (!(m > 0.0)) return 0;
+    int e;
+    frexp(m, &e);
+    return e;
+}
+
+// A' for one chunk: one warp per (cell, grain).  P [cells][nbt] FP64 in, per grain
+// A'_g [cells][Kp_g] (BF16 or TF32-in-FP32) out, and rowscale [cells][G] = 2^e.
+__global__ void k_pack_p(int cells, int G, const int* __restrict__ bin_off, const double* __restrict__ P,
+                         long long ldP, const long long* __restrict__ aoff, const int* __restrict__ kp, int split,
+                         int tf32, void* __restrict__ A, float* __restrict__ rowscale) {
+    long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (w >= (long long)cells * G) return;
+    int c = (int)(w / G), g = (int)(w % G);
+    int off = bin_off[g], nb = bin_off[g + 1] - off;
+    const double* pr = P + (size_t)c * ldP + off;
+    double m = 0.0;
+    for (int i = lane; i < nb; i += 32) m = fmax(m, pr[i]);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    int e = scale_exp(m);
+    double inv = ldexp(1.0, -e);
+    if (lane == 0) rowscale[(size_t)c * G + g] = ldexpf(1.0f, e);
+    int K = kp[g];
+    if (tf32) {
+        float* row = (float*)A + aoff[g] + (size_t)c * K;
+        for (int i = lane; i < nb; i += 32) {
+            float hi, lo;
+            split_tf32(pr[i] * inv, hi, lo);
+            row[i] = hi;
+            if (split) {
+                row[nb + i] = hi;
+                row[2 * nb + i] = lo;
+            }
+        }
+        for (int i = (split ? 3 : 1) * nb + lane; i < K; i += 32) row[i] = 0.0f;
+    } else {
+        uint16_t* row = (uint16_t*)A + aoff[g] + (size_t)c * K;
+        for (int i = lane; i < nb; i += 32) {
+            uint16_t hi, lo;
+            split_bf16(pr[i] * inv, hi, lo);
+            row[i] = hi;
+            if (split) {
+                row[nb + i] = hi;
+                row[2 * nb + i] = lo;
+            }
+        }
+        for (int i = (split ? 3 : 1) * nb + lane; i < K; i += 32) row[i] = 0;
+    }
+}
+
+// B' of every grain: one thread per (grain, wavelength).  K [nbt][N] FP64 in, per grain
+// B'_g [N][Kp_g] with parts [K_hi | K_lo | K_hi] (split) or [K_hi], and colscale [G][N].
+__global__ void k_pack_k(int N, int G, const int* __restrict__ bin_off, const double* __restrict__ K,
+                         const long long* __restrict__ boff, const int* __restrict__ kp, int split, int tf32,
+                         void* __restrict__ B, float* __restrict__ colscale) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)G * N) return;
+    int g = (int)(idx / N), n = (int)(idx % N);
+    int off = bin_off[g], nb = bin_off[g + 1] - off;
+    double m = 0.0;
+    for (int i = 0; i < nb; ++i) m = fmax(m, K[(size_t)(off + i) * N + n]);
+    int e = scale_exp(m);
+    double inv = ldexp(1.0, -e);
+    colscale[(size_t)g * N + n] = ldexpf(1.0f, e);
+    int Kp = kp[g];
+    if (tf32) {
+        float* row = (float*)B + boff[g] + (size_t)n * Kp;
+        for (int i = 0; i < nb; ++i) {
+            float hi, lo;
+            split_tf32(K[(size_t)(off + i) * N + n] * inv, hi, lo);
+            row[i] = hi;
+            if (split) {
+                row[nb + i] = lo;
+                row[2 * nb + i] = hi;
+            }
+        }
+        for (int i = (split ? 3 : 1) * nb; i < Kp; ++i) row[i] = 0.0f;
+    } else {
+        uint16_t* row = (uint16_t*)B + boff[g] + (size_t)n * Kp;
+        for (int i = 0; i < nb; ++i) {
+            uint16_t hi, lo;
+            split_bf16(K[(size_t)(off + i) * N + n] * inv, hi, lo);
+            row[i] = hi;
+            if (split) {
+                row[nb + i] = lo;
+                row[2 * nb + i] = hi;
+            }
+        }
+        for (int i = (split ? 3 : 1) * nb; i < Kp; ++i) row[i] = 0;
+    }
+}
+
+cudaError_t launch_pack_p(int cells, int G, const int* bin_off, const double* P, long long ldP, const long long* aoff,
+                          const int* kp, int split, int tf32, void* A, float* rowscale, cudaStream_t st) {
+    long long warps = (long long)cells * G;
+    if (warps <= 0) return cudaSuccess;
+    int threads = 256;
+    long long blocks = (warps * 32 + threads - 1) / threads;
+    k_pack_p<<<(unsigned)blocks, threads, 0, st>>>(cells, G, bin_off, P, ldP, aoff, kp, split, tf32, A, rowscale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_k(int N, int G, const int* bin_off, const double* K, const long long* boff, const int* kp,
+                          int split, int tf32, void* B, float* colscale, cudaStream_t st) {
+    long long total = (long long)G * N;
+    int threads = 128;
+    k_pack_k<<<(unsigned)((total + threads - 1) / threads), threads, 0, st>>>(N, G, bin_off, K, boff, kp, split, tf32,
+                                                                            B, colscale);
+    return cudaGetLastError();
+}
+
+}  // namespace heat

@@ -1,10 +1,10 @@
-// Per-solve kernels: field tables, wavelength prefix tables, and the
+// Per-solve kernels: field tables, the matrix build (B band, intra-bin terms) and the
 // Guhathakurta-Draine recursion (Eq. bmatrix, Eq. xf, Eq. renormalization).
 //
 // Work unit ("task") = one grain x 32 cells; one warp per task, one lane per cell.
-// All lanes of a warp walk the same band of the same grain, so the recursion has
-// no divergence and no cross-lane reduction: each band element costs one FP64 FMA
-// per cell.
+// All lanes of a warp walk the same band of the same grain, so neither kernel has
+// divergence or cross-lane reductions: in the recursion each band element costs one
+// FP64 FMA per cell.
 #include "common.cuh"
 #include "internal.h"
 
@@ -54,209 +54,298 @@ __global__ void k_field(int N, const double* __restrict__ dln, const TU* __restr
     for (int k = 0; k < 4; ++k) {
         int n = n0 + ty + 8 * k, c = c0 + tx;
         if (n < N && c < Cc) {
-            ua[(size_t)n * Cc + c] = t_ua[tx][ty + 8 * k];
-            su[(size_t)n * Cc + c] = t_su[tx][ty + 8 * k];
+            if (sizeof(TO) == 8) {
+                ua[(size_t)n * Cc + c] = t_ua[tx][ty + 8 * k];
+                su[(size_t)n * Cc + c] = t_su[tx][ty + 8 * k];
+            } else {  // FP32 build: interleaved (u, slope) pairs, one 8-byte load per element
+                float2 v = make_float2((float)t_ua[tx][ty + 8 * k], (float)t_su[tx][ty + 8 * k]);
+                ((float2*)ua)[(size_t)n * Cc + c] = v;
+            }
         }
     }
     if (bad) atomicOr(status, kStatBadInput);
 }
 
 // ---------------------------------------------------------------------------
-// k_prep (FP64 build).  Per cell and grain, with Omega = u C on the log-log
-// interpolant (Eq. interpolation), slope s_n and q = s_n + p + 1:
+// k_build: the matrix-build kernel.  One warp per task (grain x 32 cells), one lane
+// per cell.  With Omega = u C on the log-log interpolant (Eq. interpolation), slope
+// s_n and q = s_n + p + 1 on segment n:
 //   segment integral   int Omega lambda^p = Omega_n lambda_n^{p+1} dln_n E1(q dln_n)
-//   photon prefix      Phi_n = (1/h) sum_{m<n} int_m Omega lambda          (B_fj = Phi(lambda_fj))
-//   element constants  aq_n = (Omega_n lambda_n^2/h)/q_n,  q_n  (q_n = 0: aq_n = Omega_n lambda_n^2/h)
-//   intra-bin term     W_j = c int_{hc/(Elo_{j+1}-E_j)}^{lambda_{N-1}} Omega,  intra_j = W_j/(E_{j+1}-E_j)
+//   photon prefix      Phi_n = (1/h) sum_{m<n} int_m Omega lambda       (FP64 cumulative sum)
+//   band element       B_fj = Phi(lambda_fj) = Phi_n + (Omega_n lambda_n^2/h) t E1(q t)
+//                      (Eq. bmatrix telescoped: the bins' wavelength ranges tile [0, lambda_fj])
+//   intra-bin term     W_j = c int_{hc/(Elo_{j+1}-E_j)}^{lambda_{N-1}} Omega, added to the diagonal
+//                      element: B_{j+1,j} += W_j/(E_{j+1}-E_j)
 //   absorbed power     c int Omega over the grid
-__global__ void k_prep64(GrainDev gd, ChunkDev ch) {
+// The segments are walked in order; every band element whose transition wavelength
+// falls in the current segment (the grain's pattern list) is written to the band
+// storage Bb, so the recursion streams B instead of gathering tables.
+template <int BUILD>
+__global__ void __launch_bounds__(128) k_build(GrainDev gd, ChunkDev ch) {
     int task = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     int lane = threadIdx.x & 31;
     if (task >= ch.n_tasks) return;
     const int N = gd.N, Cc = ch.Cc, nbt = gd.nbt;
     int g = ch.tasks[task].x, grp = ch.tasks[task].y;
     int off = gd.bin_off[g];
-    const double* Cact = gd.Cact + (size_t)g * N;
-    const double* sC = gd.sC + (size_t)g * N;
     int cc = grp * 32 + lane;
-    size_t tb = (size_t)task * N * 32 + lane;
-    size_t ib = ((size_t)grp * nbt + off) * 32 + lane;
-
+    size_t bb = (size_t)grp * gd.band_total * 32 + lane;  // + e * 32
+    const int* sp = gd.seg_ptr + (size_t)g * (N + 1);
+    const SoftF64* soft = gd.soft;
+    int p = gd.soft_off[g], p1 = gd.soft_off[g + 1];
     double Phi = 0.0;
-    for (int n = 0; n < N - 1; ++n) {
-        double ua = ch.ua64[(size_t)n * Cc + cc], su = ch.su64[(size_t)n * Cc + cc];
-        double om = ua * Cact[n];
-        double q1 = su + sC[n] + 2.0;
-        double ln = gd.lam[n];
-        double a = om * ln * ln / kH;
-        ch.phi64[tb + (size_t)n * 32] = Phi;
-        ch.aq64[tb + (size_t)n * 32] = (q1 != 0.0) ? a / q1 : a;
-        ch.q64[tb + (size_t)n * 32] = q1;
-        if (om > 0.0) Phi += a * gd.dln[n] * e1d(q1 * gd.dln[n]);
-    }
-    ch.phi64[tb + (size_t)(N - 1) * 32] = Phi;
-    ch.aq64[tb + (size_t)(N - 1) * 32] = 0.0;
-    ch.q64[tb + (size_t)(N - 1) * 32] = 0.0;
 
-    const SoftF64* soft = gd.soft;
-    int p = gd.soft_off[g], p1 = gd.soft_off[g + 1];
-    while (p < p1 && soft[p].n == N - 1) {
-        ch.intra64[ib + (size_t)soft[p].j * 32] = 0.0;
-        ++p;
-    }
-    double Psi = 0.0;  // int Omega from lambda_{n+1} to lambda_{N-1}
-    for (int n = N - 2; n >= 0; --n) {
-        double ua = ch.ua64[(size_t)n * Cc + cc], su = ch.su64[(size_t)n * Cc + cc];
-        double om = ua * Cact[n];
-        double q0 = su + sC[n] + 1.0;
-        double b = om * gd.lam[n];
-        double dl = gd.dln[n];
-        while (p < p1 && soft[p].n == n) {
-            SoftF64 sf = soft[p];
-            double part = 0.0;
-            if (om > 0.0) {
-                double L = dl - sf.t;
-                part = b * exp(q0 * sf.t) * L * e1d(q0 * L);
+    if (BUILD == 0) {
+        const double* Cact = gd.Cact + (size_t)g * N;
+        const double* sC = gd.sC + (size_t)g * N;
+        for (int n = 0; n < N - 1; ++n) {
+            double ua = ch.ua64[(size_t)n * Cc + cc], su = ch.su64[(size_t)n * Cc + cc];
+            double om = ua * Cact[n];
+            double q1 = su + sC[n] + 2.0;
+            double ln = gd.lam[n];
+            double a = om * ln * ln / kH;
+            double aq = (q1 != 0.0) ? a / q1 : a;
+            for (int k = sp[n]; k < sp[n + 1]; ++k) {
+                PatF64 pt = gd.pat64[k];
+                double B = Phi + (q1 != 0.0 ? aq * expm1(q1 * pt.t) : aq * pt.t);
+                ch.Bb64[bb + (size_t)pt.e * 32] = B;
             }
-            ch.intra64[ib + (size_t)sf.j * 32] = kC * (part + Psi) * gd.invdE[off + sf.j];
+            if (om > 0.0) Phi += a * gd.dln[n] * e1d(q1 * gd.dln[n]);
+        }
+        for (int k = sp[N - 1]; k < sp[N]; ++k) ch.Bb64[bb + (size_t)gd.pat64[k].e * 32] = Phi;
+
+        // intra-bin terms go into the diagonal elements (j+1, j) of the band
+        auto put64 = [&](const SoftF64& sf, double v) {
+            size_t ix = bb + (size_t)sf.e_diag * 32;
+            ch.Bb64[ix] = (sf.diag_in_band ? ch.Bb64[ix] : 0.0) + v;
+        };
+        while (p < p1 && soft[p].n == N - 1) {
+            put64(soft[p], 0.0);
             ++p;
         }
-        if (om > 0.0) Psi += b * dl * e1d(q0 * dl);
-    }
-    for (; p < p1; ++p) ch.intra64[ib + (size_t)soft[p].j * 32] = kC * Psi * gd.invdE[off + soft[p].j];
-    if (ch.pabs) ch.pabs[(size_t)cc * gd.G + g] = kC * Psi;
-}
+        double Psi = 0.0;  // int Omega from lambda_{n+1} to lambda_{N-1}
+        for (int n = N - 2; n >= 0; --n) {
+            double ua = ch.ua64[(size_t)n * Cc + cc], su = ch.su64[(size_t)n * Cc + cc];
+            double om = ua * Cact[n];
+            double q0 = su + sC[n] + 1.0;
+            double b = om * gd.lam[n];
+            double dl = gd.dln[n];
+            while (p < p1 && soft[p].n == n) {
+                SoftF64 sf = soft[p];
+                double part = 0.0;
+                if (om > 0.0) {
+                    double L = dl - sf.t;
+                    part = b * exp(q0 * sf.t) * L * e1d(q0 * L);
+                }
+                put64(sf, kC * (part + Psi) * gd.invdE[off + sf.j]);
+                ++p;
+            }
+            if (om > 0.0) Psi += b * dl * e1d(q0 * dl);
+        }
+        for (; p < p1; ++p) put64(soft[p], kC * Psi * gd.invdE[off + soft[p].j]);
+        if (ch.pabs) ch.pabs[(size_t)cc * gd.G + g] = kC * Psi;
+    } else {
+        const float* ca = gd.ca32 + (size_t)g * N;
+        const float* ce = gd.ce32 + (size_t)g * N;
+        const float* sC = gd.sC32 + (size_t)g * N;
+        const float2* uasu = (const float2*)ch.ua32;
+        float* Bb = ch.Bb32 + bb;
+        float2 us_next = uasu[cc];
+        for (int n = 0; n < N - 1; ++n) {
+            float2 us = us_next;
+            if (n + 1 < N - 1) us_next = uasu[(size_t)(n + 1) * Cc + cc];  // one segment ahead
+            float ua = us.x, su = us.y;
+            float phi = __double2float_rn(Phi);
+            int k = sp[n], k1 = sp[n + 1];
+            for (; k + 2 <= k1; k += 2) {
+                PatF32 a0 = gd.pat32[k], a1 = gd.pat32[k + 1];
+                __stcs(Bb + (size_t)a0.e * 32, fmaf(ua * a0.cat, e1f(fmaf(su, a0.t, a0.zt)), phi));
+                __stcs(Bb + (size_t)a1.e * 32, fmaf(ua * a1.cat, e1f(fmaf(su, a1.t, a1.zt)), phi));
+            }
+            if (k < k1) {
+                PatF32 a0 = gd.pat32[k];
+                __stcs(Bb + (size_t)a0.e * 32, fmaf(ua * a0.cat, e1f(fmaf(su, a0.t, a0.zt)), phi));
+            }
+            float a = ua * ca[n];
+            if (a > 0.0f) {
+                float dl = gd.dln32[n];
+                Phi += widen_pos(a * dl * e1f((su + sC[n] + 2.0f) * dl));
+            }
+        }
+        float phi_end = __double2float_rn(Phi);
+        for (int k = sp[N - 1]; k < sp[N]; ++k) Bb[gd.pat32[k].e * 32] = phi_end;
 
-// k_prep (FP32 build): the photon prefix Phi_n and the intra-bin terms, in FP32 with
-// compensated (Kahan) running sums.  The element constants are formed in the
-// recursion from the shared field tables ua, su and the grain's ca, sC.
-__global__ void k_prep32(GrainDev gd, ChunkDev ch) {
-    int task = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    int lane = threadIdx.x & 31;
-    if (task >= ch.n_tasks) return;
-    const int N = gd.N, Cc = ch.Cc, nbt = gd.nbt;
-    int g = ch.tasks[task].x, grp = ch.tasks[task].y;
-    int off = gd.bin_off[g];
-    const float* ca = gd.ca32 + (size_t)g * N;
-    const float* ce = gd.ce32 + (size_t)g * N;
-    const float* sC = gd.sC32 + (size_t)g * N;
-    int cc = grp * 32 + lane;
-    size_t tb = (size_t)task * N * 32 + lane;
-    size_t ib = ((size_t)grp * nbt + off) * 32 + lane;
-
-    float Phi = 0.0f, cPhi = 0.0f;
-    for (int n = 0; n < N - 1; ++n) {
-        float ua = ch.ua32[(size_t)n * Cc + cc], su = ch.su32[(size_t)n * Cc + cc];
-        ch.phi32[tb + (size_t)n * 32] = Phi;
-        float a = ua * ca[n];
-        if (a > 0.0f) {
+        auto put32 = [&](const SoftF64& sf, float v) {
+            float* q = Bb + (size_t)sf.e_diag * 32;
+            *q = (sf.diag_in_band ? *q : 0.0f) + v;
+        };
+        while (p < p1 && soft[p].n == N - 1) {
+            put32(soft[p], 0.0f);
+            ++p;
+        }
+        double Psi = 0.0;  // c int Omega from lambda_{n+1} to lambda_{N-1} (FP64 cumulative sum)
+        us_next = uasu[(size_t)(N - 2) * Cc + cc];
+        for (int n = N - 2; n >= 0; --n) {
+            float2 us = us_next;
+            if (n > 0) us_next = uasu[(size_t)(n - 1) * Cc + cc];
+            float ua = us.x, su = us.y;
+            float b = ua * ce[n];
+            float q0 = su + sC[n] + 1.0f;
             float dl = gd.dln32[n];
-            float I = a * dl * e1f((su + sC[n] + 2.0f) * dl);
-            float y = I - cPhi, t = Phi + y;
-            cPhi = (t - Phi) - y;
-            Phi = t;
-        }
-    }
-    ch.phi32[tb + (size_t)(N - 1) * 32] = Phi;
-
-    const SoftF64* soft = gd.soft;
-    int p = gd.soft_off[g], p1 = gd.soft_off[g + 1];
-    while (p < p1 && soft[p].n == N - 1) {
-        ch.intra32[ib + (size_t)soft[p].j * 32] = 0.0f;
-        ++p;
-    }
-    float Psi = 0.0f, cPsi = 0.0f;  // c int Omega from lambda_{n+1} to lambda_{N-1}
-    for (int n = N - 2; n >= 0; --n) {
-        float ua = ch.ua32[(size_t)n * Cc + cc], su = ch.su32[(size_t)n * Cc + cc];
-        float b = ua * ce[n];
-        float q0 = su + sC[n] + 1.0f;
-        float dl = gd.dln32[n];
-        while (p < p1 && soft[p].n == n) {
-            SoftF64 sf = soft[p];
-            float part = 0.0f;
-            if (b > 0.0f) {
-                float ts = (float)sf.t;
-                float L = dl - ts;
-                part = b * expf(q0 * ts) * L * e1f(q0 * L);
+            while (p < p1 && soft[p].n == n) {
+                SoftF64 sf = soft[p];
+                float part = 0.0f;
+                if (b > 0.0f) {
+                    float ts = (float)sf.t;
+                    float L = dl - ts;
+                    part = b * __expf(q0 * ts) * L * e1f(q0 * L);
+                }
+                put32(sf, (part + __double2float_rn(Psi)) * gd.invdE32[off + sf.j]);
+                ++p;
             }
-            ch.intra32[ib + (size_t)sf.j * 32] = (part + Psi) * gd.invdE32[off + sf.j];
-            ++p;
+            if (b > 0.0f) Psi += widen_pos(b * dl * e1f(q0 * dl));
         }
-        if (b > 0.0f) {
-            float I = b * dl * e1f(q0 * dl);
-            float y = I - cPsi, t = Psi + y;
-            cPsi = (t - Psi) - y;
-            Psi = t;
-        }
+        float psi_end = __double2float_rn(Psi);
+        for (; p < p1; ++p) put32(soft[p], psi_end * gd.invdE32[off + soft[p].j]);
+        if (ch.pabs) ch.pabs[(size_t)cc * gd.G + g] = Psi;
     }
-    for (; p < p1; ++p) ch.intra32[ib + (size_t)soft[p].j * 32] = Psi * gd.invdE32[off + soft[p].j];
-    if (ch.pabs) ch.pabs[(size_t)cc * gd.G + g] = (double)Psi;
 }
 
 // ---------------------------------------------------------------------------
-// k_recur: X_0 = 1, X_f = (sum_{j in band(f)} B_fj X_j + intra_{f-1} X_{f-1}) / T_{f-1,f}
-// (Eq. xf; the band holds every j whose transition wavelength lies on the grid, all
-// other B_fj are exactly zero), power-of-two rescale of X_0..X_f when X_f > 2^800,
-// then P = X / sum X (Eq. renormalization) written to P[cell][off_g + i].
+// k_recur: the recursion kernel.  X_0 = 1,
+//   X_f = (sum_{j in band(f)} B_fj X_j) / T_{f-1,f}                              (Eq. xf)
+// in FP64, where the band holds every j whose transition wavelength lies on the grid
+// (all other B_fj are exactly zero) plus the diagonal j = f-1, which also carries the
+// intra-bin term; then P = X / sum X (Eq. renormalization) is written to P[cell][off_g + i].
+// Overflow guard: when X_f >= 2^800 every X is to be multiplied by 2^-800 (exact).  Only
+// the values later rows still read (j >= the next row's band start), the register window
+// and the running sum are scaled at once; each stored X keeps the epoch (count of
+// rescales) it was last written in, and the normalisation applies the missing powers of
+// two, so the work is O(band) per rescale instead of O(f) and the result is the same.
+// B streams from the band storage in element order with evict-first loads (it is read
+// once), eight elements per step, so that the X history stays in L2.
+template <int BUILD>
+__device__ __forceinline__ double band_b(const float* B32, const double* B64, int e) {
+    if (BUILD) return widen_pos(__ldcs(B32 + (size_t)e * 32));
+    return __ldcs(B64 + (size_t)e * 32);
+}
+
 template <int BUILD>
 __global__ void __launch_bounds__(128) k_recur(GrainDev gd, ChunkDev ch) {
     int task = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     int lane = threadIdx.x & 31;
     if (task >= ch.n_tasks) return;
-    const int N = gd.N, Cc = ch.Cc, nbt = gd.nbt;
+    const int nbt = gd.nbt;
     int g = ch.tasks[task].x, grp = ch.tasks[task].y;
     int off = gd.bin_off[g];
     int M = gd.bin_off[g + 1] - off - 1;
     int cc = grp * 32 + lane;
-    size_t tb = (size_t)task * N * 32 + lane;
     size_t xb = ((size_t)grp * nbt + off) * 32 + lane;
     const int* rp = gd.rowptr + off + g;
-    double* xs = ch.xs;
+    const double* ic_row = gd.invC + off;
+    double* xl = ch.xs + xb;
+    size_t bb = (size_t)grp * gd.band_total * 32 + lane;
+    const float* __restrict__ B32 = ch.Bb32 + (BUILD ? bb : 0);
+    const double* __restrict__ B64 = ch.Bb64 + (BUILD ? 0 : bb);
     bool numeric_bad = false;
 
-    xs[xb] = 1.0;
+    unsigned short* epl = ch.ep + xb;
+    int epoch = 0;
+    xl[0] = 1.0;
+    epl[0] = 0;
+    double total = 1.0;  // running sum of X, rescaled with it
+    // register window of the last 8 X values: w[k] = X_{f-1-k}; the band's last (most
+    // recent) elements read it instead of reloading what this thread just stored
+    double w[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) w[k] = 0.0;
+    w[0] = 1.0;
+    int e = rp[1];
+    const int e_end = rp[M + 1];
+    // L2 prefetch of the B stream, kept 64..96 elements ahead: lane k fetches the
+    // 128-byte line of element pf + k (lines of all 32 lanes of one element)
+    const size_t lane_base = bb - lane;
+    int pf = e;
     for (int f = 1; f <= M; ++f) {
-        int e0 = rp[f], e1 = rp[f + 1];
-        int j = f - (e1 - e0);
-        double S = 0.0;
-        if (BUILD == 0) {
-#pragma unroll 2
-            for (int e = e0; e < e1; ++e, ++j) {
-                ElemF64 el = gd.el64[e];
-                size_t ti = tb + (size_t)el.n * 32;
-                double ph = ch.phi64[ti], aq = ch.aq64[ti], q = ch.q64[ti];
-                double B = ph + (q != 0.0 ? aq * expm1(q * el.t) : aq * el.t);
-                S = fma(B, xs[xb + (size_t)j * 32], S);
+        const int e1 = rp[f + 1];
+        while (pf < e1 + 64 && pf < e_end) {
+            int q = pf + lane;
+            if (q < e_end) {
+                const void* a = BUILD ? (const void*)(ch.Bb32 + lane_base + (size_t)q * 32)
+                                      : (const void*)(ch.Bb64 + lane_base + (size_t)q * 32);
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
             }
-            S = fma(ch.intra64[xb + (size_t)(f - 1) * 32], xs[xb + (size_t)(f - 1) * 32], S);
-        } else {
-#pragma unroll 4
-            for (int e = e0; e < e1; ++e, ++j) {
-                ElemF32 el = gd.el32[e];
-                size_t fi = (size_t)el.n * Cc + cc;
-                float ph = ch.phi32[tb + (size_t)el.n * 32];
-                float ua = ch.ua32[fi], su = ch.su32[fi];
-                float B = fmaf(ua * el.cat, e1f(fmaf(su, el.t, el.zt)), ph);
-                S = fma(widen_pos(B), xs[xb + (size_t)j * 32], S);
-            }
-            S = fma(widen_pos(ch.intra32[xb + (size_t)(f - 1) * 32]), xs[xb + (size_t)(f - 1) * 32], S);
+            pf += 32;
         }
-        double ic = gd.invC[off + f];
+        const int width = e1 - e;          // band of row f: j in [f - width, f)
+        const int nreg = min(width, 8);    // its last nreg elements come from the window
+        const int e_mem = e1 - nreg;       // elements before e_mem read X from memory
+        int j = f - width;
+        double S = 0.0, S1 = 0.0;
+        for (; e + 8 <= e_mem; e += 8, j += 8) {
+            double b[8], x[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) b[k] = band_b<BUILD>(B32, B64, e + k);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) x[k] = xl[(j + k) * 32];
+#pragma unroll
+            for (int k = 0; k < 8; k += 2) {
+                S = fma(b[k], x[k], S);
+                S1 = fma(b[k + 1], x[k + 1], S1);
+            }
+        }
+        for (; e < e_mem; ++e, ++j) S1 = fma(band_b<BUILD>(B32, B64, e), xl[j * 32], S1);
+        // window part: element e1-1-k multiplies X_{f-1-k} = w[k], k < nreg
+        double br[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) br[k] = (k < nreg) ? band_b<BUILD>(B32, B64, e1 - 1 - k) : 0.0;
+        switch (nreg) {  // no predicated-off FMAs: jump into the unrolled tail
+            case 8: S1 = fma(br[7], w[7], S1);
+            case 7: S = fma(br[6], w[6], S);
+            case 6: S1 = fma(br[5], w[5], S1);
+            case 5: S = fma(br[4], w[4], S);
+            case 4: S1 = fma(br[3], w[3], S1);
+            case 3: S = fma(br[2], w[2], S);
+            case 2: S1 = fma(br[1], w[1], S1);
+            case 1: S = fma(br[0], w[0], S);
+            default: break;
+        }
+        e = e1;
+        if (width > 1) S += S1;
+        const double ic = ic_row[f];
         double X = S * ic;
-        if (!(ic > 0.0)) {
+        if (__double2hiint(ic) == 0 && __double2loint(ic) == 0) {  // zero cooling rate
             X = 0.0;
             if (S != 0.0) numeric_bad = true;
         }
-        xs[xb + (size_t)f * 32] = X;
-        if (X > kRescaleBig)
-            for (int i = 0; i <= f; ++i) xs[xb + (size_t)i * 32] *= kRescaleSmall;
+        xl[f * 32] = X;
+        epl[f * 32] = (unsigned short)epoch;
+        total += X;
+#pragma unroll
+        for (int k = 7; k > 0; --k) w[k] = w[k - 1];
+        w[0] = X;
+        if (above_rescale(X)) {
+            ++epoch;
+            const int lo = (f < M) ? (f + 1) - (rp[f + 2] - rp[f + 1]) : f + 1;  // next row's band start
+            for (int i = lo; i <= f; ++i) {
+                xl[i * 32] *= kRescaleSmall;
+                epl[i * 32] = (unsigned short)epoch;
+            }
+            total *= kRescaleSmall;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) w[k] *= kRescaleSmall;
+        }
     }
-    double sum = 0.0;
-    for (int i = 0; i <= M; ++i) sum += xs[xb + (size_t)i * 32];
-    double inv = 1.0 / sum;
     if (cc < ch.cells) {
+        const double inv = 1.0 / total;
         double* prow = ch.P + (size_t)cc * ch.ldP + off;
-        for (int i = 0; i <= M; ++i) prow[i] = xs[xb + (size_t)i * 32] * inv;
+        for (int i = 0; i <= M; ++i) {
+            const int d = epoch - (int)epl[i * 32];  // rescales this value has not seen
+            const double x = xl[i * 32];
+            // scale X first (as the plain rescale would have), then normalise: the factor
+            // alone could underflow where the product is still a normal number
+            prow[i] = d == 0 ? x * inv : ldexp(x, -800 * d) * inv;
+        }
     }
     if (numeric_bad) atomicOr(ch.status, kStatNumeric);
 }
@@ -282,12 +371,12 @@ cudaError_t launch_field(const GrainDev& g, const void* u, int dtype, long long 
     return cudaGetLastError();
 }
 
-cudaError_t launch_prep(const GrainDev& g, const ChunkDev& ch, int build, cudaStream_t st) {
+cudaError_t launch_build(const GrainDev& g, const ChunkDev& ch, int build, cudaStream_t st) {
     int threads = 128, blocks = (ch.n_tasks + 3) / 4;
     if (build == 0)
-        k_prep64<<<blocks, threads, 0, st>>>(g, ch);
+        k_build<0><<<blocks, threads, 0, st>>>(g, ch);
     else
-        k_prep32<<<blocks, threads, 0, st>>>(g, ch);
+        k_build<1><<<blocks, threads, 0, st>>>(g, ch);
     return cudaGetLastError();
 }
 

@@ -45,13 +45,12 @@ void* g_addr[kMaxDevices] = {};
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 // Bytes one 32-cell group needs in the scratch array.
-size_t group_bytes(int build, int G, int N, int nbt) {
-    size_t tab = (size_t)G * N * 32 * (build == HEAT_BUILD_F64 ? 3 * sizeof(double) : sizeof(float));
-    size_t intra = (size_t)nbt * 32 * (build == HEAT_BUILD_F64 ? sizeof(double) : sizeof(float));
-    size_t xs = (size_t)nbt * 32 * sizeof(double);
+size_t group_bytes(int build, int G, int N, int nbt, long long band) {
+    size_t tab = (size_t)band * 32 * (build == HEAT_BUILD_F64 ? sizeof(double) : sizeof(float));
+    size_t xs = (size_t)nbt * 32 * (sizeof(double) + sizeof(unsigned short));
     size_t uf = (size_t)N * 32 * 2 * (build == HEAT_BUILD_F64 ? sizeof(double) : sizeof(float));
     size_t tasks = (size_t)G * sizeof(int2);
-    return tab + intra + xs + uf + tasks + 8 * 256;  // plus alignment slack of the carve-up
+    return tab + xs + uf + tasks + 9 * 256;  // plus alignment slack of the carve-up
 }
 
 }  // namespace
@@ -85,7 +84,7 @@ extern "C" heat_status heat_solve_noalloc(heat_ctx* ctx, int build, const double
     }
 
     const int N = gd.N, G = gd.G, nbt = gd.nbt;
-    const size_t per_group = group_bytes(build, G, N, nbt);
+    const size_t per_group = group_bytes(build, G, N, nbt, gd.band_total);
     if (per_group > HEAT_NOALLOC_SCRATCH_BYTES) {
         heat_internal_fail(ctx, "heat_solve_noalloc: one 32-cell group of these grains needs more scratch than "
                                 "HEAT_NOALLOC_SCRATCH_BYTES (32 MiB); use heat_solve, or fewer grains/bins/wavelengths");
@@ -116,28 +115,24 @@ extern "C" heat_status heat_solve_noalloc(heat_ctx* ctx, int build, const double
         if (build == HEAT_BUILD_F64) {
             ch.ua64 = (double*)take(sizeof(double) * (size_t)N * Cc);
             ch.su64 = (double*)take(sizeof(double) * (size_t)N * Cc);
-            ch.phi64 = (double*)take(sizeof(double) * (size_t)ch.n_tasks * N * 32);
-            ch.aq64 = (double*)take(sizeof(double) * (size_t)ch.n_tasks * N * 32);
-            ch.q64 = (double*)take(sizeof(double) * (size_t)ch.n_tasks * N * 32);
-            ch.intra64 = (double*)take(sizeof(double) * (size_t)NG * nbt * 32);
+            ch.Bb64 = (double*)take(sizeof(double) * (size_t)NG * gd.band_total * 32);
         } else {
-            ch.ua32 = (float*)take(sizeof(float) * (size_t)N * Cc);
-            ch.su32 = (float*)take(sizeof(float) * (size_t)N * Cc);
-            ch.phi32 = (float*)take(sizeof(float) * (size_t)ch.n_tasks * N * 32);
-            ch.intra32 = (float*)take(sizeof(float) * (size_t)NG * nbt * 32);
+            ch.ua32 = (float*)take(sizeof(float2) * (size_t)N * Cc);  // (u, slope) pairs
+            ch.Bb32 = (float*)take(sizeof(float) * (size_t)NG * gd.band_total * 32);
         }
         ch.xs = (double*)take(sizeof(double) * (size_t)NG * nbt * 32);
+        ch.ep = (unsigned short*)take(sizeof(unsigned short) * (size_t)NG * nbt * 32);
         ch.pabs = nullptr;
         ch.P = P_out + (size_t)g0 * 32 * nbt;
         ch.ldP = nbt;
         ch.status = status;
         if ((size_t)(p - (unsigned char*)base) > HEAT_NOALLOC_SCRATCH_BYTES) return HEAT_EINVAL;
-        // Every scratch word is written before it is read (tasks, field tables, prefix
-        // tables, intra-bin terms, then X row by row), so nothing needs clearing.
+        // Every scratch word is written before it is read (tasks, field tables, the B band,
+        // intra-bin terms, then X row by row), so nothing needs clearing.
         k_noalloc_tasks<<<(ch.n_tasks + 127) / 128, 128, 0, st>>>(tasks, G, NG);
         if (cudaGetLastError() != cudaSuccess) return HEAT_ECUDA;
         if (launch_field(gd, u_dev, HEAT_F64, (long long)g0 * 32, ch, build, st) != cudaSuccess) return HEAT_ECUDA;
-        if (launch_prep(gd, ch, build, st) != cudaSuccess) return HEAT_ECUDA;
+        if (launch_build(gd, ch, build, st) != cudaSuccess) return HEAT_ECUDA;
         if (launch_recur(gd, ch, build, st) != cudaSuccess) return HEAT_ECUDA;
     }
     return HEAT_OK;

@@ -21,9 +21,11 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "heat.h")
 HEAT_OK, HEAT_EINVAL, HEAT_ENOMEM, HEAT_ECUDA, HEAT_ENUMERIC, HEAT_ETIMEOUT, HEAT_ESTATE = range(7)
 HEAT_F64, HEAT_F32 = 0, 1
 HEAT_BUILD_F64, HEAT_BUILD_F32 = 0, 1
-HEAT_EMIS_NONE, HEAT_EMIS_F64 = -1, 0
-HEAT_T_FIELD, HEAT_T_PREP, HEAT_T_RECUR, HEAT_T_EMIS, HEAT_T_COUNT = range(5)
-TIMING_NAMES = ("field", "prep", "recur", "emis")
+HEAT_EMIS_NONE, HEAT_EMIS_F64, HEAT_EMIS_BF16X3, HEAT_EMIS_TF32X3, HEAT_EMIS_BF16, HEAT_EMIS_TF32 = -1, 0, 1, 2, 3, 4
+EMIS_NAMES = {HEAT_EMIS_F64: "f64", HEAT_EMIS_BF16X3: "bf16x3", HEAT_EMIS_TF32X3: "tf32x3", HEAT_EMIS_BF16: "bf16",
+              HEAT_EMIS_TF32: "tf32"}
+HEAT_T_FIELD, HEAT_T_BUILD, HEAT_T_RECUR, HEAT_T_EMIS, HEAT_T_COUNT = range(5)
+TIMING_NAMES = ("field", "build", "recur", "emis")
 
 _STATUS = {0: "HEAT_OK", 1: "HEAT_EINVAL", 2: "HEAT_ENOMEM", 3: "HEAT_ECUDA", 4: "HEAT_ENUMERIC",
            5: "HEAT_ETIMEOUT", 6: "HEAT_ESTATE"}
