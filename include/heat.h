@@ -82,6 +82,11 @@ typedef struct heat_opts {
     int host_io;        /* 1: P_out and j_out are host pointers; the library stages through device
                            memory and the call returns after the results are on the host          */
     int timing;         /* 1: record CUDA events around every kernel launch (see heat_get_timing)  */
+    double* ledger_out; /* NULL, or FP64 [cell_count][n_grains][2] (device; host with host_io): the
+                           energy check of every spectrum, erg/s: [0] absorbed power c int u C dlambda
+                           on the grid, [1] emitted power of the discrete model
+                           sum_f P_f T_{f-1,f} (E_f - E_{f-1}) (Eq. cooling); they differ by the
+                           bin discretisation of the absorbed photon energies only                */
 } heat_opts;
 
 /* kernel classes reported by heat_get_timing */
@@ -94,7 +99,7 @@ enum {
 };
 
 /* Fill *opts with defaults: exact FP64 build, FP64 emissivity, FP64 j, per-grain j,
- * all cells, device outputs, no timing. */
+ * all cells, device outputs, no timing, no energy check. */
 void heat_default_opts(heat_opts* opts);
 
 /* Create a context on CUDA device `device` for the wavelength grid lambda_cm[n_lambda]

@@ -57,14 +57,14 @@ struct heat_ctx {
     long long band_per_cell = 0;
     std::vector<int> grain_order;
     DevBuf d_bin_off, d_cabs, d_T, d_E, d_Cf, d_invC, d_invdE, d_invdE32, d_Cact, d_sC, d_ca32, d_ce32, d_sC32,
-        d_rowptr, d_seg_ptr, d_pat64, d_pat32, d_soft, d_soft_off, d_K, d_Kw, d_w, d_koff_all;
+        d_rowptr, d_seg_ptr, d_pat64, d_pat32, d_soft, d_soft_off, d_K, d_Kw, d_w, d_koff_all, d_cde;
     // fields
     int n_cells = 0;
     const void* u_dev = nullptr;
     int u_dtype = 0;
     DevBuf d_u_own;
     // chunk scratch
-    DevBuf s_tasks, s_ua64, s_su64, s_ua32, s_Bb64, s_Bb32, s_xs, s_ep, s_pabs, s_P, s_j;
+    DevBuf s_tasks, s_ua64, s_su64, s_ua32, s_Bb64, s_Bb32, s_xs, s_ep, s_pabs, s_P, s_j, s_led;
     int tasks_NG = -1;
     DevBuf d_status;
     int sms = 0;
@@ -308,6 +308,7 @@ void heat_default_opts(heat_opts* o) {
     o->chunk_cells = 0;
     o->host_io = 0;
     o->timing = 0;
+    o->ledger_out = nullptr;
 }
 
 heat_status heat_create_grid(heat_ctx** out, int device, int n_lambda, const double* lambda_cm) {
@@ -566,11 +567,15 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
                       ctx->d_E.as<double>(), ctx->d_w.as<double>(), ctx->d_K.as<double>(),
                       ctx->has_w ? ctx->d_Kw.as<double>() : nullptr, 0));
     CKR(cudaDeviceSynchronize());
-    std::vector<double> Cf(nbt), invC(nbt, 0.0);
+    std::vector<double> Cf(nbt), invC(nbt, 0.0), cde(nbt, 0.0);
     CKR(cudaMemcpy(Cf.data(), ctx->d_Cf.p, sizeof(double) * nbt, cudaMemcpyDeviceToHost));
     for (int g = 0; g < G; ++g)
-        for (int i = bin_offset[g] + 1; i < bin_offset[g + 1]; ++i) invC[i] = Cf[i] > 0.0 ? 1.0 / Cf[i] : 0.0;
-    if (upload(ctx->d_invC, invC)) return ctx->fail(HEAT_ENOMEM, "heat_set_grains: allocation");
+        for (int i = bin_offset[g] + 1; i < bin_offset[g + 1]; ++i) {
+            invC[i] = Cf[i] > 0.0 ? 1.0 / Cf[i] : 0.0;
+            cde[i] = Cf[i] * (H_bins_erg[i] - H_bins_erg[i - 1]);
+        }
+    if (upload(ctx->d_invC, invC) || upload(ctx->d_cde, cde))
+        return ctx->fail(HEAT_ENOMEM, "heat_set_grains: allocation");
     d_work.release();
     d_bg.release();
     return HEAT_OK;
@@ -650,6 +655,7 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
     bool internal_P = (P_out == nullptr) || o.host_io;
     if (internal_P) ok &= !ctx->s_P.ensure(sizeof(double) * (size_t)Cc * nbt);
     if (want_j && o.host_io) ok &= !ctx->s_j.ensure(jel * (size_t)Cc * jrow);
+    if (o.ledger_out && o.host_io) ok &= !ctx->s_led.ensure(sizeof(double) * 2 * (size_t)Cc * G);
     if (!ok) return ctx->fail(HEAT_ENOMEM, "heat_solve: scratch allocation failed");
     if (ctx->tasks_NG != NG) {
         std::vector<int2> tasks;
@@ -677,6 +683,7 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
     gd.invdE32 = ctx->d_invdE32.as<float>();
     gd.invC = ctx->d_invC.as<double>();
     gd.invdE = ctx->d_invdE.as<double>();
+    gd.cde = ctx->d_cde.as<double>();
     gd.rowptr = ctx->d_rowptr.as<int>();
     gd.band_total = ctx->band_per_cell;
     gd.seg_ptr = ctx->d_seg_ptr.as<int>();
@@ -719,6 +726,8 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
         ch.status = ctx->d_status.as<int>();
         ch.ldP = nbt;
         ch.P = internal_P ? ctx->s_P.as<double>() : P_out + (size_t)c0 * nbt;
+        ch.ledger = !o.ledger_out ? nullptr
+                    : (o.host_io ? ctx->s_led.as<double>() : o.ledger_out + (size_t)c0 * G * 2);
         long long cell0 = (long long)c_begin + c0;
         TIMED(HEAT_T_FIELD, launch_field(gd, ctx->u_dev, ctx->u_dtype, cell0, ch, build, st));
         TIMED(HEAT_T_BUILD, launch_build(gd, ch, build, st));
@@ -748,6 +757,9 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
                 CKR(cudaMemcpyAsync((char*)j_out + (size_t)c0 * jrow * jel, jdst, (size_t)cells * jrow * jel,
                                     cudaMemcpyDeviceToHost, st));
         }
+        if (o.ledger_out && o.host_io)
+            CKR(cudaMemcpyAsync(o.ledger_out + (size_t)c0 * G * 2, ch.ledger, sizeof(double) * 2 * (size_t)cells * G,
+                                cudaMemcpyDeviceToHost, st));
         if (P_out && o.host_io)
             CKR(cudaMemcpyAsync(P_out + (size_t)c0 * nbt, ch.P, sizeof(double) * (size_t)cells * nbt,
                                 cudaMemcpyDeviceToHost, st));
@@ -819,8 +831,8 @@ void heat_destroy(heat_ctx* ctx) {
                       &ctx->d_T, &ctx->d_E, &ctx->d_Cf, &ctx->d_invC, &ctx->d_invdE, &ctx->d_invdE32, &ctx->d_Cact,
                       &ctx->d_sC, &ctx->d_ca32, &ctx->d_ce32, &ctx->d_sC32, &ctx->d_rowptr, &ctx->d_seg_ptr,
                       &ctx->d_pat64, &ctx->d_pat32, &ctx->d_soft, &ctx->d_soft_off, &ctx->d_K, &ctx->d_Kw, &ctx->d_w,
-                      &ctx->d_koff_all, &ctx->d_u_own, &ctx->s_tasks, &ctx->s_ua64, &ctx->s_su64, &ctx->s_ua32,
-                      &ctx->s_Bb64, &ctx->s_Bb32, &ctx->s_xs, &ctx->s_ep, &ctx->s_pabs, &ctx->s_P, &ctx->s_j, &ctx->d_status};
+                      &ctx->d_koff_all, &ctx->d_cde, &ctx->d_u_own, &ctx->s_tasks, &ctx->s_ua64, &ctx->s_su64, &ctx->s_ua32,
+                      &ctx->s_Bb64, &ctx->s_Bb32, &ctx->s_xs, &ctx->s_ep, &ctx->s_pabs, &ctx->s_P, &ctx->s_j, &ctx->s_led, &ctx->d_status};
     for (DevBuf* b : bufs) b->release();
     for (auto& t : ctx->tc) {
         t.B.release();
@@ -863,6 +875,7 @@ __attribute__((visibility("hidden"))) heat_status heat_internal_grain_view(heat_
     gd->invdE32 = ctx->d_invdE32.as<float>();
     gd->invC = ctx->d_invC.as<double>();
     gd->invdE = ctx->d_invdE.as<double>();
+    gd->cde = ctx->d_cde.as<double>();
     gd->rowptr = ctx->d_rowptr.as<int>();
     gd->band_total = ctx->band_per_cell;
     gd->seg_ptr = ctx->d_seg_ptr.as<int>();

@@ -36,6 +36,7 @@ struct GrainDev {
     const float* sC32;      // [G][N]
     const float* invdE32;   // [nbt]
     const double* invC;     // [nbt] 1/T_{f-1,f} (0 where the cooling rate is 0 and for f = 0)
+    const double* cde;      // [nbt] T_{f-1,f} (E_f - E_{f-1}) (0 for f = 0): emitted power of bin f
     const double* invdE;    // [nbt] 1/(E_{j+1}-E_j) (0 for the last bin)
     const int* rowptr;      // [nbt + G] per grain, rows f = 0..M: band elements of row f at
                             //   rowptr[off_g + g + f] .. rowptr[off_g + g + f + 1] (global indices)
@@ -67,6 +68,7 @@ struct ChunkDev {
     double* pabs;       // [Cc][G] absorbed power c int Omega dlambda (erg/s)
     double* P;          // [Cc][nbt] output distributions (row stride ldP)
     long long ldP;
+    double* ledger;     // [cells][G][2] energy check (absorbed, emitted), or null
     int* status;
 };
 

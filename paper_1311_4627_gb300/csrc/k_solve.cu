@@ -339,12 +339,21 @@ __global__ void __launch_bounds__(128) k_recur(GrainDev gd, ChunkDev ch) {
     if (cc < ch.cells) {
         const double inv = 1.0 / total;
         double* prow = ch.P + (size_t)cc * ch.ldP + off;
+        double emit = 0.0;
+        const double* cde = gd.cde + off;
         for (int i = 0; i <= M; ++i) {
             const int d = epoch - (int)epl[i * 32];  // rescales this value has not seen
             const double x = xl[i * 32];
             // scale X first (as the plain rescale would have), then normalise: the factor
             // alone could underflow where the product is still a normal number
-            prow[i] = d == 0 ? x * inv : ldexp(x, -800 * d) * inv;
+            const double p = d == 0 ? x * inv : ldexp(x, -800 * d) * inv;
+            prow[i] = p;
+            if (ch.ledger) emit = fma(p, cde[i], emit);
+        }
+        if (ch.ledger) {
+            double* lg = ch.ledger + ((size_t)cc * gd.G + g) * 2;
+            lg[0] = ch.pabs[(size_t)cc * gd.G + g];
+            lg[1] = emit;
         }
     }
     if (numeric_bad) atomicOr(ch.status, kStatNumeric);

@@ -40,7 +40,8 @@ class HeatError(RuntimeError):
 class heat_opts(ctypes.Structure):
     _fields_ = [("build", ctypes.c_int), ("emis", ctypes.c_int), ("j_dtype", ctypes.c_int),
                 ("size_integrate", ctypes.c_int), ("cell_begin", ctypes.c_int), ("cell_count", ctypes.c_int),
-                ("chunk_cells", ctypes.c_int), ("host_io", ctypes.c_int), ("timing", ctypes.c_int)]
+                ("chunk_cells", ctypes.c_int), ("host_io", ctypes.c_int), ("timing", ctypes.c_int),
+                ("ledger_out", ctypes.c_void_p)]
 
 
 _lib = None
@@ -111,10 +112,11 @@ def _check(ctx, st):
 
 
 def heat_default_opts(**kw) -> heat_opts:
+    """Defaults of the library; keyword overrides (ledger_out takes a pointer-like)."""
     o = heat_opts()
     lib().heat_default_opts(ctypes.byref(o))
     for k, v in kw.items():
-        setattr(o, k, int(v))
+        setattr(o, k, _ptr(v) if k == "ledger_out" else int(v))
     return o
 
 
