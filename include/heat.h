@@ -164,6 +164,69 @@ heat_status heat_band_elements(const heat_ctx* ctx, long long* per_cell);
  * reset = 1 clears the record afterwards.  Errors: HEAT_ECUDA. */
 heat_status heat_get_timing(heat_ctx* ctx, double* ms, long long* launches, int reset);
 
+/* ---- Learned surrogate (an extension: the paper's method has no surrogate) ------------
+ * An ensemble of MLPs maps the binned field and the grain to ln j_lambda; it is trained on
+ * spectra the exact path computes, and the exact path stays its fallback.
+ * Network per member: 128 inputs (ln field energy in 64 wavelength bands, ln radius, a
+ * composition flag, zero padding; standardised with training-set statistics) -> 4 hidden
+ * layers of 512 with GELU -> n_lambda outputs y = ln j - ln P_abs (P_abs = c int u C dlambda,
+ * standardised per wavelength).  BF16 operands on the tensor cores, FP32 accumulation and
+ * FP32 master weights; masked MSE (entries with j < 1e-6 of the spectrum's peak are left
+ * out); Adam.  Requires n_lambda to be a multiple of 64 and FP64 device fields. */
+
+/* Create (or recreate) the surrogate of ctx: `members` ensemble members (1..8), weights
+ * initialised from `seed`; grain_flag[n_grains] (host, or NULL = 0) is the composition input.
+ * Errors: HEAT_ESTATE (grains not set), HEAT_EINVAL, HEAT_ENOMEM, HEAT_ECUDA. */
+heat_status heat_surrogate_init(heat_ctx* ctx, int members, const float* grain_flag, unsigned long long seed);
+
+/* Samples of cells [cell_begin, cell_begin + cell_count), ordered (cell, grain), all device:
+ *   X   FP32 [cell_count * n_grains][128] raw inputs;
+ *   Y   FP32 [cell_count * n_grains][n_lambda] targets ln j - ln P_abs (NaN where masked), or NULL;
+ *       needs j (FP32 [cell_count][n_grains][n_lambda], e.g. from heat_solve) when given;
+ *   lnp FP32 [cell_count * n_grains] ln P_abs, or NULL.
+ * Synchronous.  Errors: HEAT_ESTATE, HEAT_EINVAL, HEAT_ENOMEM, HEAT_ECUDA. */
+heat_status heat_surrogate_samples(heat_ctx* ctx, int cell_begin, int cell_count, const float* j, float* X, float* Y,
+                                   float* lnp, void* cuda_stream);
+
+/* Standardisation statistics (per input, per wavelength) from n training samples. */
+heat_status heat_surrogate_fit_norm(heat_ctx* ctx, const float* X, const float* Y, long long n, void* cuda_stream);
+
+/* Train every member for `epochs` over the n samples (device X, Y) in shuffled batches of
+ * `batch` rows (a multiple of 64), Adam with learning rate lr; loss_history[epochs] (host,
+ * or NULL) receives member 0's mean loss per epoch (standardised units).  Synchronous. */
+heat_status heat_surrogate_train(heat_ctx* ctx, const float* X, const float* Y, long long n, int batch, int epochs,
+                                 float lr, unsigned long long seed, double* loss_history, void* cuda_stream);
+
+/* Ensemble prediction for n samples (device X and lnp from heat_surrogate_samples):
+ * lnj FP32 [n][n_lambda] = ln j (ensemble mean), spread FP32 [n] = the largest ensemble
+ * standard deviation of ln j over the predicted emission (within 1e-6 of its peak). */
+heat_status heat_surrogate_predict(heat_ctx* ctx, const float* X, const float* lnp, long long n, float* lnj,
+                                   float* spread, void* cuda_stream);
+
+/* Surrogate with exact fallback for the cells of fallback_opts (cell_begin, cell_count):
+ * j_out FP32 device [cells][n_grains][n_lambda] = exp(ln j) of the ensemble; every cell with
+ * a grain whose spread exceeds tol is solved again by heat_solve with fallback_opts (its
+ * exact/mixed precision choices; per-grain FP32 device j required) and overwritten.
+ * *n_fallback = cells solved exactly.  Synchronous. */
+heat_status heat_solve_surrogate(heat_ctx* ctx, const heat_opts* fallback_opts, float tol, float* j_out,
+                                 int* n_fallback, void* cuda_stream);
+
+/* Gradient check support: loss and gradient of member `member` for n (multiple of 64)
+ * already standardised samples (device Xn [n][128], Tn [n][n_lambda], NaN = masked); the
+ * gradient is written to grad_out (device FP32, flat layout: for each layer W [out][in]
+ * then b [out]); *loss_out = masked mean squared error. */
+heat_status heat_surrogate_grads(heat_ctx* ctx, int member, const float* Xn, const float* Tn, int n,
+                                 float* grad_out, double* loss_out, void* cuda_stream);
+
+/* Copy member parameters (flat FP32 layout above) to host (set = 0) or from host (set = 1);
+ * *nparams = their count.  host may be NULL to query the count. */
+heat_status heat_surrogate_params(heat_ctx* ctx, int member, float* host, int set, long long* nparams);
+
+/* Checkpoint: weights, Adam moments, step, seed, standardisation (save); load recreates the
+ * surrogate from such a file (the grid and grain count must match). */
+heat_status heat_surrogate_save(heat_ctx* ctx, const char* path);
+heat_status heat_surrogate_load(heat_ctx* ctx, const char* path);
+
 /* ---- Solve without allocating (the paper has no counterpart) -------------------------
  * For callers that cannot allocate device memory once their loop runs: codes that keep
  * the GPU under a fixed memory budget owned by their own allocator, and time-critical

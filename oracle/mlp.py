@@ -1,0 +1,80 @@
+"""FP64 CPU reference of the surrogate MLP (forward, masked-MSE loss, backward).
+
+TEST INFRASTRUCTURE: it checks the gradients of the GPU training kernels.  Plain numpy in
+float64; the architecture follows the library's surrogate: layers W_l [out][in], b_l, GELU
+(exact, with erf) after every layer but the last, loss = mean over non-NaN targets of
+(y - t)^2.  Parameters use the library's flat layout: for each layer W (row-major) then b.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+try:
+    from scipy.special import erf as _erf
+except ImportError:  # pragma: no cover - scipy is present where the tests run
+    _erf = np.vectorize(math.erf)
+
+SQRT1_2 = 1.0 / math.sqrt(2.0)
+
+
+def gelu(x):
+    return 0.5 * x * (1.0 + _erf(x * SQRT1_2))
+
+
+def gelu_grad(x):
+    return 0.5 * (1.0 + _erf(x * SQRT1_2)) + x * np.exp(-0.5 * x * x) / math.sqrt(2.0 * math.pi)
+
+
+def unflatten(flat, dims):
+    """dims = [in, h1, ..., out]; returns [(W, b), ...] views into float64 copies."""
+    flat = np.asarray(flat, dtype=np.float64)
+    out, k = [], 0
+    for i in range(len(dims) - 1):
+        n_in, n_out = dims[i], dims[i + 1]
+        W = flat[k:k + n_in * n_out].reshape(n_out, n_in)
+        k += n_in * n_out
+        b = flat[k:k + n_out]
+        k += n_out
+        out.append((W, b))
+    assert k == flat.size
+    return out
+
+
+def flatten(layers):
+    return np.concatenate([np.concatenate([W.ravel(), b]) for W, b in layers])
+
+
+def forward(layers, x):
+    a, zs, acts = np.asarray(x, np.float64), [], []
+    for i, (W, b) in enumerate(layers):
+        acts.append(a)
+        z = a @ W.T + b
+        zs.append(z)
+        a = gelu(z) if i + 1 < len(layers) else z
+    return a, zs, acts
+
+
+def loss(layers, x, t):
+    y, _, _ = forward(layers, x)
+    m = ~np.isnan(t)
+    d = np.where(m, y - np.nan_to_num(t), 0.0)
+    return float(np.sum(d * d) / max(1, m.sum()))
+
+
+def loss_and_grad(layers, x, t):
+    """Masked mean squared error and its gradient (same flat layout as the parameters)."""
+    y, zs, acts = forward(layers, x)
+    m = ~np.isnan(t)
+    cnt = max(1, int(m.sum()))
+    d = np.where(m, y - np.nan_to_num(t), 0.0)
+    L = float(np.sum(d * d) / cnt)
+    g = 2.0 * d / cnt
+    grads = [None] * len(layers)
+    for i in range(len(layers) - 1, -1, -1):
+        W, _ = layers[i]
+        grads[i] = (g.T @ acts[i], g.sum(axis=0))
+        if i > 0:
+            g = (g @ W) * gelu_grad(zs[i - 1])
+    return L, flatten(grads)

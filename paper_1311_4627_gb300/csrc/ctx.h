@@ -1,0 +1,106 @@
+// Private definition of heat_ctx, shared by the translation units of libheat.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/heat.h"
+
+namespace heat {
+struct Surrogate;
+void surrogate_free(Surrogate* s);
+}
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    cudaError_t ensure(size_t bytes) {
+        if (bytes <= cap) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e == cudaSuccess) cap = bytes;
+        return e;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+    template <typename T>
+    T* as() const { return (T*)p; }
+};
+
+struct heat_ctx {
+    int device = 0;
+    int N = 0;
+    std::vector<double> lam;
+    std::string err;
+
+    // grid
+    DevBuf d_lam, d_dln, d_lam32, d_dln32;
+    // grains
+    int G = 0, nbt = 0;
+    std::vector<int> bin_off;
+    std::vector<double> w;
+    bool has_w = false;
+    long long band_per_cell = 0;
+    std::vector<int> grain_order;
+    DevBuf d_bin_off, d_cabs, d_T, d_E, d_Cf, d_invC, d_invdE, d_invdE32, d_Cact, d_sC, d_ca32, d_ce32, d_sC32,
+        d_rowptr, d_seg_ptr, d_pat64, d_pat32, d_soft, d_soft_off, d_K, d_Kw, d_w, d_koff_all, d_cde;
+    // fields
+    int n_cells = 0;
+    const void* u_dev = nullptr;
+    int u_dtype = 0;
+    DevBuf d_u_own;
+    // chunk scratch
+    DevBuf s_tasks, s_ua64, s_su64, s_ua32, s_Bb64, s_Bb32, s_xs, s_ep, s_pabs, s_P, s_j, s_led;
+    int tasks_NG = -1;
+    DevBuf d_status;
+    int sms = 0;
+    std::vector<double> radius;
+    heat::Surrogate* sur = nullptr;  // learned surrogate (heat_surrogate_init)
+    // tensor-core emissivity operands, per mode (index = HEAT_EMIS_*)
+    struct TcMode {
+        bool built = false;
+        DevBuf B, colscale, kp, boff, aoff;
+        std::vector<int> kp_h;
+        std::vector<long long> boff_h, aoff_h;
+        int aoff_cells = -1;
+        std::vector<int> order;  // grains by K extent, largest first
+    } tc[5];
+    DevBuf s_A, s_rowscale;
+    // per-kernel event timing
+    struct TimedLaunch {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<TimedLaunch> timed;
+    std::vector<cudaEvent_t> event_pool;
+    cudaEvent_t take_event() {
+        if (!event_pool.empty()) {
+            cudaEvent_t e = event_pool.back();
+            event_pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+
+    heat_status fail(heat_status s, const std::string& m) {
+        err = m;
+        return s;
+    }
+    heat_status cuda_fail(cudaError_t e, const char* where) {
+        err = std::string(where) + ": " + cudaGetErrorString(e);
+        return HEAT_ECUDA;
+    }
+};
+

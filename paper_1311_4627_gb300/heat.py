@@ -82,6 +82,24 @@ def lib():
         L.heat_get_timing.argtypes = [_vp, _vp, _vp, ctypes.c_int]
         L.heat_solve_noalloc.restype = ctypes.c_int
         L.heat_solve_noalloc.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]
+        for name, args in [
+            ("heat_surrogate_init", [_vp, ctypes.c_int, _vp, ctypes.c_ulonglong]),
+            ("heat_surrogate_samples", [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]),
+            ("heat_surrogate_fit_norm", [_vp, _vp, _vp, ctypes.c_longlong, _vp]),
+            ("heat_surrogate_train", [_vp, _vp, _vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                      ctypes.c_ulonglong, _vp, _vp]),
+            ("heat_surrogate_predict", [_vp, _vp, _vp, ctypes.c_longlong, _vp, _vp, _vp]),
+            ("heat_solve_surrogate", [_vp, ctypes.POINTER(heat_opts), ctypes.c_float, _vp,
+                                      ctypes.POINTER(ctypes.c_int), _vp]),
+            ("heat_surrogate_grads", [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_double),
+                                      _vp]),
+            ("heat_surrogate_params", [_vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]),
+            ("heat_surrogate_save", [_vp, ctypes.c_char_p]),
+            ("heat_surrogate_load", [_vp, ctypes.c_char_p]),
+        ]:
+            fn = getattr(L, name)
+            fn.restype = ctypes.c_int
+            fn.argtypes = args
         L.heat_destroy.restype = None
         L.heat_destroy.argtypes = [_vp]
         _lib = L
@@ -183,6 +201,67 @@ def heat_solve_noalloc(ctx, build, u_dev, n_cells, P_out, stream=None):
 
 
 HEAT_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
+SURROGATE_INPUTS = 128
+
+
+def heat_surrogate_init(ctx, members, grain_flag=None, seed=0):
+    gf = None if grain_flag is None else np.ascontiguousarray(grain_flag, dtype=np.float32)
+    _check(ctx, lib().heat_surrogate_init(ctx, int(members), None if gf is None else gf.ctypes.data, int(seed)))
+
+
+def heat_surrogate_samples(ctx, cell_begin, cell_count, j, X, Y=None, lnp=None, stream=None):
+    _check(ctx, lib().heat_surrogate_samples(ctx, int(cell_begin), int(cell_count), _ptr(j), _ptr(X), _ptr(Y),
+                                             _ptr(lnp), stream))
+
+
+def heat_surrogate_fit_norm(ctx, X, Y, n, stream=None):
+    _check(ctx, lib().heat_surrogate_fit_norm(ctx, _ptr(X), _ptr(Y), int(n), stream))
+
+
+def heat_surrogate_train(ctx, X, Y, n, batch, epochs, lr, seed=0, stream=None):
+    hist = np.zeros(int(epochs))
+    _check(ctx, lib().heat_surrogate_train(ctx, _ptr(X), _ptr(Y), int(n), int(batch), int(epochs), float(lr),
+                                           int(seed), hist.ctypes.data, stream))
+    return hist
+
+
+def heat_surrogate_predict(ctx, X, lnp, n, lnj, spread, stream=None):
+    _check(ctx, lib().heat_surrogate_predict(ctx, _ptr(X), _ptr(lnp), int(n), _ptr(lnj), _ptr(spread), stream))
+
+
+def heat_solve_surrogate(ctx, fallback_opts, tol, j_out, stream=None):
+    nfb = ctypes.c_int(0)
+    _check(ctx, lib().heat_solve_surrogate(ctx, ctypes.byref(fallback_opts), float(tol), _ptr(j_out),
+                                           ctypes.byref(nfb), stream))
+    return nfb.value
+
+
+def heat_surrogate_grads(ctx, member, Xn, Tn, n, grad_out, stream=None):
+    loss = ctypes.c_double(0.0)
+    _check(ctx, lib().heat_surrogate_grads(ctx, int(member), _ptr(Xn), _ptr(Tn), int(n), _ptr(grad_out),
+                                           ctypes.byref(loss), stream))
+    return loss.value
+
+
+def heat_surrogate_params(ctx, member, values=None):
+    """Get (values None) or set the flat FP32 parameters of one member."""
+    n = ctypes.c_longlong(0)
+    _check(ctx, lib().heat_surrogate_params(ctx, int(member), None, 0, ctypes.byref(n)))
+    if values is None:
+        out = np.zeros(n.value, dtype=np.float32)
+        _check(ctx, lib().heat_surrogate_params(ctx, int(member), out.ctypes.data, 0, ctypes.byref(n)))
+        return out
+    v = np.ascontiguousarray(values, dtype=np.float32)
+    _check(ctx, lib().heat_surrogate_params(ctx, int(member), v.ctypes.data, 1, ctypes.byref(n)))
+    return v
+
+
+def heat_surrogate_save(ctx, path):
+    _check(ctx, lib().heat_surrogate_save(ctx, str(path).encode()))
+
+
+def heat_surrogate_load(ctx, path):
+    _check(ctx, lib().heat_surrogate_load(ctx, str(path).encode()))
 
 
 def heat_destroy(ctx):

@@ -1,0 +1,139 @@
+"""Surrogate on the GPU: gradients against the FP64 CPU MLP, training, the surrogate with
+exact fallback against the oracle, and checkpoints."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp
+from paper_1311_4627_gb300 import heat
+from paper_1311_4627_gb300 import workloads as W
+
+from .gpu_helpers import Lib, masked_relerr
+
+pytestmark = pytest.mark.gpu
+
+DIMS = None  # set from n_lambda
+
+
+def _bf16(a):
+    """Round float32 values to bfloat16 (nearest even), as float64."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@pytest.fixture(scope="module")
+def small():
+    """256 cells x 8 carbonaceous grains x 128 bins x 256 wavelengths."""
+    lam = W.wavelength_grid(256)
+    base = W.batched(cells=256, n_lambda=256, grains=8)
+    wl = W.custom(lam, base.radius, base.composition, [128] * 8, base.u)
+    lib = Lib(wl)
+    lib.set_fields(wl.u)
+    yield wl, lib
+    lib.close()
+
+
+def test_gradients_match_cpu_fp64_mlp(small):
+    import torch
+
+    wl, lib = small
+    heat.heat_surrogate_init(lib.ctx, 1, np.zeros(wl.n_grains), seed=3)
+    dims = [heat.SURROGATE_INPUTS, 512, 512, 512, 512, wl.n_lambda]
+    flat = heat.heat_surrogate_params(lib.ctx, 0)
+    # weights as the GPU uses them (BF16) so that only activation rounding differs
+    flat_b = _bf16(flat)
+    rng = np.random.default_rng(0)
+    n = 64
+    xn = _bf16(rng.normal(0, 1, (n, dims[0])))
+    tn = rng.normal(0, 1, (n, dims[-1]))
+    tn[rng.random(tn.shape) < 0.2] = np.nan
+    X = torch.tensor(xn, dtype=torch.float32, device="cuda")
+    T = torch.tensor(tn, dtype=torch.float32, device="cuda")
+    G = torch.zeros(flat.size, dtype=torch.float32, device="cuda")
+    loss_gpu = heat.heat_surrogate_grads(lib.ctx, 0, X, T, n, G, torch.cuda.current_stream().cuda_stream)
+    g_gpu = G.cpu().numpy().astype(np.float64)
+    loss_cpu, g_cpu = mlp.loss_and_grad(mlp.unflatten(flat_b, dims), xn, tn.astype(np.float64))
+    assert abs(loss_gpu / loss_cpu - 1.0) < 2e-2
+    k = 0
+    for i in range(len(dims) - 1):
+        for size in (dims[i] * dims[i + 1], dims[i + 1]):
+            a, b = g_gpu[k:k + size], g_cpu[k:k + size]
+            k += size
+            rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+            cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
+            assert rel < 5e-2 and cos > 0.998, (i, size, rel, cos)
+
+
+@pytest.fixture(scope="module")
+def trained(small, tmp_path_factory):
+    """Train 4 members on 192 cells x 8 grains of spectra from the mixed path."""
+    import torch
+
+    wl, lib = small
+    st = torch.cuda.current_stream().cuda_stream
+    heat.heat_surrogate_init(lib.ctx, 4, np.zeros(wl.n_grains), seed=11)
+    n_train = 192
+    j = torch.empty(n_train, wl.n_grains, wl.n_lambda, dtype=torch.float32, device="cuda")
+    heat.heat_solve(lib.ctx, heat.heat_default_opts(build=heat.HEAT_BUILD_F32, emis=heat.HEAT_EMIS_BF16X3,
+                                                    j_dtype=heat.HEAT_F32, cell_count=n_train), None, j, st)
+    heat.heat_sync(lib.ctx)
+    ns = n_train * wl.n_grains
+    X = torch.empty(ns, heat.SURROGATE_INPUTS, dtype=torch.float32, device="cuda")
+    Y = torch.empty(ns, wl.n_lambda, dtype=torch.float32, device="cuda")
+    heat.heat_surrogate_samples(lib.ctx, 0, n_train, j, X, Y, None, st)
+    heat.heat_surrogate_fit_norm(lib.ctx, X, Y, ns, st)
+    hist = heat.heat_surrogate_train(lib.ctx, X, Y, ns, 256, 40, 1e-3, seed=5, stream=st)
+    return wl, lib, hist
+
+
+def test_training_reduces_the_loss(trained):
+    _, _, hist = trained
+    assert np.all(np.isfinite(hist))
+    assert hist[-1] < 0.2 * hist[0], hist
+
+
+def test_surrogate_with_fallback_within_1e2_of_the_oracle(trained):
+    """Held-out cells: the surrogate answers where the ensemble agrees, the exact path
+    elsewhere; the result stays within 1e-2 of the FP64 oracle on j > 1e-6 of its peak."""
+    import torch
+
+    wl, lib, _ = trained
+    held = np.arange(192, 256)
+    sub = W.field_subset(wl, held)
+    Cf = oracle.grain_cooling(wl)
+    _, j_ref, _, _ = oracle.solve_batch(sub, Cf)
+    j = torch.empty(len(held), wl.n_grains, wl.n_lambda, dtype=torch.float32, device="cuda")
+    o = heat.heat_default_opts(build=heat.HEAT_BUILD_F32, emis=heat.HEAT_EMIS_BF16X3, j_dtype=heat.HEAT_F32,
+                               cell_begin=192, cell_count=len(held))
+    nfb = heat.heat_solve_surrogate(lib.ctx, o, 0.003, j, torch.cuda.current_stream().cuda_stream)
+    heat.heat_sync(lib.ctx)
+    err = masked_relerr(j.cpu().numpy().astype(np.float64), j_ref)
+    assert err <= 1e-2, (err, nfb)
+    assert 0 <= nfb <= len(held)
+
+
+def test_checkpoint_round_trip(trained, tmp_path):
+    import torch
+
+    wl, lib, _ = trained
+    st = torch.cuda.current_stream().cuda_stream
+    ns = 16 * wl.n_grains
+    X = torch.empty(ns, heat.SURROGATE_INPUTS, dtype=torch.float32, device="cuda")
+    lnp = torch.empty(ns, dtype=torch.float32, device="cuda")
+    heat.heat_surrogate_samples(lib.ctx, 200, 16, None, X, None, lnp, st)
+    out = []
+    for k in range(2):
+        lnj = torch.empty(ns, wl.n_lambda, dtype=torch.float32, device="cuda")
+        sp = torch.empty(ns, dtype=torch.float32, device="cuda")
+        heat.heat_surrogate_predict(lib.ctx, X, lnp, ns, lnj, sp, st)
+        heat.heat_sync(lib.ctx)
+        out.append((lnj.cpu().numpy(), sp.cpu().numpy()))
+        if k == 0:
+            path = os.path.join(tmp_path, "sur.bin")
+            heat.heat_surrogate_save(lib.ctx, path)
+            heat.heat_surrogate_load(lib.ctx, path)
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
