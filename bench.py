@@ -10,6 +10,8 @@ tables, B-matrix build, FP64 recursion, renormalisation and the emissivity of ev
 
 Paths (``--path``):
   ``mixed``      FP32 matrix build, FP64 recursion, BF16x3 tensor-core emissivity (default)
+  (``surrogate`` is measured after them: an MLP ensemble trained, untimed, on 1M
+  spectra of other cells, with the mixed path as fallback for uncertain cells)
   ``mixed_tf32`` FP32 matrix build, FP64 recursion, TF32x3 tensor-core emissivity
   ``batched``    FP32 matrix build, FP64 recursion, FP64 emissivity
   ``exact``      FP64 everywhere (the plain path)
@@ -60,6 +62,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="time only --path")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip training and timing the surrogate path")
+    ap.add_argument("--sur-cells", type=int, default=16384, help="training cells for the surrogate (x 64 grains)")
+    ap.add_argument("--sur-epochs", type=int, default=30)
+    ap.add_argument("--sur-tol", type=float, default=1e-2, help="ensemble spread (ln j) above which a cell falls back")
     ap.add_argument("--oracle-cells", type=int, default=24, help="cells in the oracle sample")
     return ap.parse_args()
 
@@ -362,12 +368,91 @@ def main():
         for v in paths.values():
             v["x_plain_exact"] = v["spectra_per_s"] / base
 
+    # the learned surrogate with exact fallback (trained untimed on other cells)
+    sur_j = None
+    if not args.no_surrogate:
+        tw = W.batched(cells=args.sur_cells, seed=2002)
+        t0 = time.perf_counter()
+        heat.heat_surrogate_init(ctx, 4, W.composition_flags(wl), seed=7)
+        ut = torch.from_numpy(tw.u).to(dev)
+        heat.heat_set_fields(ctx, tw.n_cells, ut, heat.HEAT_F64, 1, sh)
+        jt = torch.empty(tw.n_cells, G, N, dtype=torch.float32, device=dev)
+        heat.heat_solve(ctx, opts_for("mixed"), None, jt, sh)
+        heat.heat_sync(ctx)
+        ns = tw.n_cells * G
+        Xt = torch.empty(ns, heat.SURROGATE_INPUTS, dtype=torch.float32, device=dev)
+        Yt = torch.empty(ns, N, dtype=torch.float32, device=dev)
+        heat.heat_surrogate_samples(ctx, 0, tw.n_cells, jt, Xt, Yt, None, sh)
+        del jt
+        gen_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        heat.heat_surrogate_fit_norm(ctx, Xt, Yt, ns, sh)
+        hist = heat.heat_surrogate_train(ctx, Xt, Yt, ns, 8192, args.sur_epochs, 1e-3, seed=9, stream=sh)
+        train_s = time.perf_counter() - t0
+        del Xt, Yt, ut
+        heat.heat_set_fields(ctx, cells, u, heat.HEAT_F64, 1, sh)
+        fo = opts_for("mixed")
+        for _ in range(2):
+            heat.heat_solve_surrogate(ctx, fo, args.sur_tol, j, sh)
+        heat.heat_sync(ctx)
+        ks = max(2, args.steps // 2)
+        nfb = 0
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        for _ in range(ks):
+            nfb = heat.heat_solve_surrogate(ctx, fo, args.sur_tol, j, sh)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_s = ev0.elapsed_time(ev1) / ks
+        sur_j = j[: args.oracle_cells].double().cpu().numpy()
+        # the network alone: features + ensemble inference over the workload, and its raw
+        # accuracy (max relative error over the 1e-6 mask, per spectrum) against the mixed path
+        nsm = cells * G
+        Xs = torch.empty(nsm, heat.SURROGATE_INPUTS, dtype=torch.float32, device=dev)
+        lnp = torch.empty(nsm, dtype=torch.float32, device=dev)
+        lnj = torch.empty(nsm, N, dtype=torch.float32, device=dev)
+        spr = torch.empty(nsm, dtype=torch.float32, device=dev)
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        heat.heat_surrogate_samples(ctx, 0, cells, None, Xs, None, lnp, sh)
+        heat.heat_surrogate_predict(ctx, Xs, lnp, nsm, lnj, spr, sh)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_inf = ev0.elapsed_time(ev1)
+        nchk = min(cells, 512)
+        jm = torch.empty(nchk, G, N, dtype=torch.float32, device=dev)
+        heat.heat_solve(ctx, opts_for("mixed", cell_count=nchk), None, jm, sh)
+        heat.heat_sync(ctx)
+        ref = jm.reshape(nchk * G, N).double()
+        got = torch.exp(lnj[: nchk * G].double())
+        pk = ref.max(dim=1, keepdim=True).values
+        msk = ref > 1e-6 * pk
+        rel = torch.where(msk, (got - ref).abs() / ref.clamp_min(1e-300), torch.zeros_like(ref)).max(dim=1).values
+        rel = rel.cpu().numpy()
+        spq = spr[: nchk * G].cpu().numpy()
+        raw = {"inference_spectra_per_s": nsm / (ms_inf / 1e3), "inference_ms": ms_inf,
+               "max_rel_err_per_spectrum_quantiles": {q: float(np.quantile(rel, float(q))) for q in ("0.1", "0.5", "0.9")},
+               "spread_quantiles": {q: float(np.quantile(spq, float(q))) for q in ("0.1", "0.5", "0.9")},
+               "accepted_fraction_at_tol": float(np.mean(spq <= args.sur_tol)),
+               "sample": f"{nchk} cells x {G} grains vs the mixed path"}
+        del Xs, lnp, lnj, spr, jm
+        paths["surrogate"] = {"spectra_per_s": cells * G / (ms_s / 1e3), "ms_per_step": ms_s,
+                              "precision": "MLP ensemble (4 x 128-512x4-1024, BF16 tensor cores) + mixed-path fallback",
+                              "fallback_cells": nfb, "fallback_fraction": nfb / cells, "tol_spread": args.sur_tol,
+                              "network_alone": raw,
+                              "training": {"samples": ns, "epochs": args.sur_epochs, "data_s": round(gen_s, 2),
+                                           "train_s": round(train_s, 2), "loss_first": float(hist[0]),
+                                           "loss_last": float(hist[-1])}}
+        if "exact" in paths:
+            paths["surrogate"]["x_plain_exact"] = paths["surrogate"]["spectra_per_s"] / paths["exact"]["spectra_per_s"]
+
     # oracle on the host cores (rank 0, N = 1), its outputs double as the error reference
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb, P_ref, j_ref, Cf = oracle_sample(wl, args.oracle_cells)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
         nsub = args.oracle_cells
-        for path in paths:
+        for path in [q for q in paths if q in PATHS]:
             P_sub = torch.empty(nsub, nbt, dtype=torch.float64, device=dev)
             j_sub = torch.empty(nsub, G, N, dtype=torch.float64, device=dev)
             o_sub = opts_for(path, cell_count=nsub)
@@ -384,6 +469,12 @@ def main():
             rel_j_all = float(np.max(np.abs(jg[mj_all] - j_ref[mj_all]) / np.abs(j_ref[mj_all])))
             paths[path]["max_rel_err"] = {"P": rel_P, "j_masked_1e-6_peak": rel_j, "j_all_above_1e-280": rel_j_all,
                                           "sample": f"{nsub} cells x {G} grains vs the FP64 oracle"}
+        if sur_j is not None:
+            peak = j_ref.max(axis=-1, keepdims=True)
+            mj = j_ref > 1e-6 * peak
+            paths["surrogate"]["max_rel_err"] = {
+                "j_masked_1e-6_peak": float(np.max(np.abs(sur_j[mj] - j_ref[mj]) / j_ref[mj])),
+                "sample": f"{nsub} cells x {G} grains vs the FP64 oracle"}
     line["paths"] = paths
     if rank == 0:
         print(json.dumps(line))

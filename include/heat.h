@@ -167,12 +167,14 @@ heat_status heat_get_timing(heat_ctx* ctx, double* ms, long long* launches, int 
 /* ---- Learned surrogate (an extension: the paper's method has no surrogate) ------------
  * An ensemble of MLPs maps the binned field and the grain to ln j_lambda; it is trained on
  * spectra the exact path computes, and the exact path stays its fallback.
- * Network per member: 128 inputs (ln field energy in 64 wavelength bands, ln radius, a
- * composition flag, zero padding; standardised with training-set statistics) -> 4 hidden
- * layers of 512 with GELU -> n_lambda outputs y = ln j - ln P_abs (P_abs = c int u C dlambda,
- * standardised per wavelength).  BF16 operands on the tensor cores, FP32 accumulation and
- * FP32 master weights; masked MSE (entries with j < 1e-6 of the spectrum's peak are left
- * out); Adam.  Requires n_lambda to be a multiple of 64 and FP64 device fields. */
+ * Network per member: 128 inputs (ln of the power the grain absorbs in 64 wavelength bands,
+ * ln radius, a composition flag, ln of the total absorbed power, zero padding; standardised
+ * with training-set statistics) -> 4 hidden layers of 512 with GELU -> n_lambda outputs
+ * y = ln j - ln P_abs (P_abs = c int u C dlambda, standardised per wavelength).  BF16
+ * operands on the tensor cores, FP32 accumulation and FP32 master weights; masked MSE
+ * (entries with j < 1e-6 of the spectrum's peak are left out) plus a one-sided square penalty
+ * on masked entries predicted above that level; Adam.  Requires n_lambda to be a multiple of
+ * 64 and FP64 device fields. */
 
 /* Create (or recreate) the surrogate of ctx: `members` ensemble members (1..8), weights
  * initialised from `seed`; grain_flag[n_grains] (host, or NULL = 0) is the composition input.
@@ -192,8 +194,9 @@ heat_status heat_surrogate_samples(heat_ctx* ctx, int cell_begin, int cell_count
 heat_status heat_surrogate_fit_norm(heat_ctx* ctx, const float* X, const float* Y, long long n, void* cuda_stream);
 
 /* Train every member for `epochs` over the n samples (device X, Y) in shuffled batches of
- * `batch` rows (a multiple of 64), Adam with learning rate lr; loss_history[epochs] (host,
- * or NULL) receives member 0's mean loss per epoch (standardised units).  Synchronous. */
+ * `batch` rows (a multiple of 64), Adam with a learning rate decaying from lr to lr/100 on a
+ * cosine over the call's steps; loss_history[epochs] (host, or NULL) receives member 0's
+ * mean loss per epoch (standardised units).  Synchronous. */
 heat_status heat_surrogate_train(heat_ctx* ctx, const float* X, const float* Y, long long n, int batch, int epochs,
                                  float lr, unsigned long long seed, double* loss_history, void* cuda_stream);
 

@@ -277,15 +277,31 @@ __global__ void k_colsum_bf16(int rows, int cols, const __nv_bfloat16* __restric
 
 // Masked squared error: targets NaN are excluded.  dY = 2 (Y - T) / count (BF16);
 // loss partial sums per block into loss[blockIdx.x].
-__global__ void k_mse(long long n, const float* __restrict__ Y, const float* __restrict__ T, float inv_count,
-                      __nv_bfloat16* __restrict__ dY, float* __restrict__ loss) {
+// Weight of the one-sided penalty relative to the fitted entries (it only has to keep the
+// masked tail below the mask, not fit it).
+constexpr float kTailWeight = 0.3f;
+
+__global__ void k_mse(long long n, int N, const float* __restrict__ Y, const float* __restrict__ T,
+                      const float* __restrict__ tb, const float* __restrict__ ym, const float* __restrict__ ys,
+                      const unsigned long long* __restrict__ count, __nv_bfloat16* __restrict__ dY,
+                      double* __restrict__ loss_acc) {
     __shared__ float red[256];
+    const unsigned long long c = *count;
+    const float inv = c > 0 ? 1.0f / (float)c : 0.0f;
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     float e2 = 0.0f;
     if (i < n) {
-        float t = T[i];
-        float d = (t == t) ? Y[i] - t : 0.0f;
-        dY[i] = __float2bfloat16_rn(2.0f * d * inv_count);
+        float t = T[i], y = Y[i], d = 0.0f;
+        if (t == t) {
+            d = y - t;
+        } else if (tb) {
+            // masked entry: penalise only a prediction above the row's mask level
+            int k = (int)(i % N);
+            float bound = tb[i / N];
+            float over = y * ys[k] + ym[k] - bound;
+            if (bound == bound && over > 0.0f) d = kTailWeight * over / ys[k];
+        }
+        dY[i] = __float2bfloat16_rn(2.0f * d * inv);
         e2 = d * d;
     }
     red[threadIdx.x] = e2;
@@ -294,7 +310,7 @@ __global__ void k_mse(long long n, const float* __restrict__ Y, const float* __r
         if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0) loss[blockIdx.x] = red[0];
+    if (threadIdx.x == 0 && loss_acc && red[0] != 0.0f) atomicAdd(loss_acc, (double)red[0] * (double)inv);
 }
 
 // Adam step on FP32 master weights; refreshes the BF16 copy W [rows][cols] and, when
@@ -369,11 +385,10 @@ cudaError_t launch_colsum_bf16(int rows, int cols, const __nv_bfloat16* A, float
     k_colsum_bf16<<<(cols + 127) / 128, 128, 0, st>>>(rows, cols, A, out);
     return cudaGetLastError();
 }
-cudaError_t launch_mse(long long n, const float* Y, const float* T, float inv_count, __nv_bfloat16* dY, float* loss,
-                       int* blocks_out, cudaStream_t st) {
-    int blocks = (int)((n + 255) / 256);
-    *blocks_out = blocks;
-    k_mse<<<blocks, 256, 0, st>>>(n, Y, T, inv_count, dY, loss);
+cudaError_t launch_mse(long long n, int N, const float* Y, const float* T, const float* tb, const float* ym,
+                       const float* ys, const unsigned long long* count, __nv_bfloat16* dY, double* loss_acc,
+                       cudaStream_t st) {
+    k_mse<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, N, Y, T, tb, ym, ys, count, dY, loss_acc);
     return cudaGetLastError();
 }
 cudaError_t launch_adam(long long n, int rows, int cols, float* w, const float* g, float* m, float* v, float lr,

@@ -29,8 +29,13 @@ cudaError_t launch_gelu_fwd(long long n, const float* Z, __nv_bfloat16* X, cudaS
 cudaError_t launch_gelu_bwd(long long n, const float* dX, const float* Z, __nv_bfloat16* dZ, cudaStream_t st);
 cudaError_t launch_transpose_bf16(int rows, int cols, const __nv_bfloat16* in, __nv_bfloat16* out, cudaStream_t st);
 cudaError_t launch_colsum_bf16(int rows, int cols, const __nv_bfloat16* A, float* out, cudaStream_t st);
-cudaError_t launch_mse(long long n, const float* Y, const float* T, float inv_count, __nv_bfloat16* dY, float* loss,
-                       int* blocks_out, cudaStream_t st);
+// Rows of N standardised outputs Y against targets T: d = Y - T where T is finite; where T is
+// NaN and tb (per-row mask level in raw units, or null) is given, d = 0.3 max(0, raw Y - tb)
+// in standardised units (ym, ys de-standardise).  dY = 2 d / count, loss_acc (or null) += sum
+// d^2 / count, count = finite targets (device).
+cudaError_t launch_mse(long long n, int N, const float* Y, const float* T, const float* tb, const float* ym,
+                       const float* ys, const unsigned long long* count, __nv_bfloat16* dY, double* loss_acc,
+                       cudaStream_t st);
 cudaError_t launch_adam(long long n, int rows, int cols, float* w, const float* g, float* m, float* v, float lr,
                         float b1, float b2, float eps, float bc1, float bc2, __nv_bfloat16* Wb, __nv_bfloat16* WTb,
                         cudaStream_t st);

@@ -3,12 +3,14 @@
 // fallback where the ensemble disagrees.  The method itself (Sec. 2 of the paper) has no
 // surrogate; this is the serving-side extension built on top of it.
 //
-// Inputs per (cell, grain) sample: ln of the field energy in 64 wavelength bands, ln a,
-// a composition flag, zero padding; standardised with statistics of the training set.
+// Inputs per (cell, grain) sample: ln of the power the grain absorbs in 64 wavelength bands,
+// ln a, a composition flag, ln of the total absorbed power, zero padding; standardised with
+// statistics of the training set.
 // Output: y_lambda = ln j_lambda - ln P_abs (P_abs = c int u C dlambda on the grid, exact
-// and cheap), standardised per wavelength; targets are masked (NaN) where
-// j < 1e-6 of the spectrum's peak.  Training: masked MSE, Adam, FP32 master weights,
-// BF16 operands on tcgen05 with FP32 accumulation.
+// and cheap), standardised per wavelength; targets are masked (NaN) where j < 1e-6 of the
+// spectrum's peak.  Training: masked MSE plus a one-sided penalty that keeps masked entries
+// predicted below the mask, Adam with cosine decay, FP32 master weights, BF16 operands on
+// tcgen05 with FP32 accumulation.
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
@@ -31,7 +33,7 @@ constexpr int kFeat = 128;  // padded input width
 constexpr int kBands = 64;
 constexpr int kHidden = 512;
 constexpr int kLayers = 5;
-constexpr float kMaskRel = 1e-6f;
+constexpr float kMaskRel = 1e-6f;  // accuracy mask: j above this fraction of the peak
 
 struct Surrogate {
     int members = 0, N = 0, G = 0;
@@ -48,14 +50,14 @@ struct Surrogate {
     unsigned long long seed = 0;
     // work buffers for one member and a batch of B rows
     int B = 0;
-    DevBuf Xn, Tn, Z[kLayers], Act[kLayers], dYb, dXf, dZb, T1, T2, loss, ens_mean, ens_m2, idx, cnt;
+    DevBuf Xn, Tn, Z[kLayers], Act[kLayers], dYb, dXf, dZb, T1, T2, loss, ens_mean, ens_m2, tb, cnt;
 };
 
 void surrogate_free(Surrogate* s) {
     if (!s) return;
     DevBuf* bufs[] = {&s->params, &s->grads, &s->adam_m, &s->adam_v, &s->wb, &s->wtb, &s->xmean, &s->xstd,
                       &s->ymean, &s->ystd, &s->d_gfeat, &s->Xn, &s->Tn, &s->dYb, &s->dXf, &s->dZb, &s->T1,
-                      &s->T2, &s->loss, &s->ens_mean, &s->ens_m2, &s->idx, &s->cnt};
+                      &s->T2, &s->loss, &s->ens_mean, &s->ens_m2, &s->tb, &s->cnt};
     for (DevBuf* b : bufs) b->release();
     for (int l = 0; l < kLayers; ++l) {
         s->Z[l].release();
@@ -67,57 +69,52 @@ void surrogate_free(Surrogate* s) {
 // ---------------------------------------------------------------------------
 // feature, target and statistics kernels
 
-// ln of the field energy in each of 64 wavelength bands (trapezoid on the nodes), per cell.
-__global__ void k_band_energy(int N, int cells, const double* __restrict__ lam, const double* __restrict__ u,
-                              long long cell0, float* __restrict__ out) {
-    int c = blockIdx.x, b = threadIdx.x;
-    if (c >= cells || b >= kBands) return;
-    int n0 = (int)((long long)b * (N - 1) / kBands), n1 = (int)((long long)(b + 1) * (N - 1) / kBands);
-    const double* row = u + (size_t)(cell0 + c) * N;
-    double e = 0.0;
-    for (int n = n0; n < n1; ++n) e += 0.5 * (row[n] + row[n + 1]) * (lam[n + 1] - lam[n]);
-    out[(size_t)c * kBands + b] = (float)log(fmax(e, 1e-300));
-}
-
-// Absorbed power c int u C dlambda per (cell, grain) on the log-log interpolant (FP32 segment
-// integrals, FP64 sum); one warp per sample, lanes over segments.  Writes ln of it.
-__global__ void k_ln_absorbed(int N, int G, int cells, const float* __restrict__ uasu, int Cc,
-                              const float* __restrict__ ce, const float* __restrict__ sC,
-                              const float* __restrict__ dln, float* __restrict__ lnp) {
+// Inputs of each (cell, grain) sample, one warp per sample: the power the grain absorbs in
+// each of 64 wavelength bands, c int u C dlambda on the log-log interpolant (FP32 segment
+// integrals, FP64 sums), as ln, floored at 1e-12 of the total; ln a, the composition flag,
+// ln of the total; zero padding.  lnp receives ln of the total (the output normalisation).
+__global__ void __launch_bounds__(256) k_sample_features(int N, int G, int cells, const float* __restrict__ uasu,
+                                                         int Cc, const float* __restrict__ ce,
+                                                         const float* __restrict__ sC, const float* __restrict__ dln,
+                                                         const float* __restrict__ gfeat, float* __restrict__ X,
+                                                         float* __restrict__ lnp) {
+    __shared__ double band[8][kBands];
     long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (w >= (long long)cells * G) return;
     int c = (int)(w / G), g = (int)(w % G);
     const float2* us = (const float2*)uasu;
-    double acc = 0.0;
-    for (int n = lane; n < N - 1; n += 32) {
-        float2 v = us[(size_t)n * Cc + c];
-        float b = v.x * ce[(size_t)g * N + n];
-        if (b > 0.0f) {
-            float q0 = v.y + sC[(size_t)g * N + n] + 1.0f, dl = dln[n];
-            acc += (double)(b * dl * e1f(q0 * dl));
+    double total = 0.0;
+    for (int b = 0; b < kBands; ++b) {
+        int n0 = (int)((long long)b * (N - 1) / kBands), n1 = (int)((long long)(b + 1) * (N - 1) / kBands);
+        double acc = 0.0;
+        for (int n = n0 + lane; n < n1; n += 32) {
+            float2 v = us[(size_t)n * Cc + c];
+            float bb = v.x * ce[(size_t)g * N + n];
+            if (bb > 0.0f) {
+                float q0 = v.y + sC[(size_t)g * N + n] + 1.0f, dl = dln[n];
+                acc += (double)(bb * dl * e1f(q0 * dl));
+            }
         }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        total += acc;
+        if (lane == 0) band[wid][b] = acc;
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) lnp[w] = (float)log(fmax(acc, 1e-300));
+    __syncwarp();
+    float* row = X + (size_t)w * kFeat;
+    const double floor_v = fmax(total * 1e-12, 1e-300);
+    for (int f = lane; f < kFeat; f += 32) {
+        float v = 0.0f;
+        if (f < kBands) v = (float)log(fmax(band[wid][f], floor_v));
+        else if (f == kBands) v = gfeat[2 * g];
+        else if (f == kBands + 1) v = gfeat[2 * g + 1];
+        else if (f == kBands + 2) v = (float)log(fmax(total, 1e-300));
+        row[f] = v;
+    }
+    if (lane == 0) lnp[w] = (float)log(fmax(total, 1e-300));
 }
 
-// Raw feature rows of (cell, grain) samples: [64 band ln energies | ln a | composition | 0...].
-__global__ void k_feature_rows(int cells, int G, const float* __restrict__ band, const float* __restrict__ gfeat,
-                               float* __restrict__ X) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)cells * G * kFeat) return;
-    long long r = i / kFeat;
-    int f = (int)(i % kFeat);
-    int c = (int)(r / G), g = (int)(r % G);
-    float v = 0.0f;
-    if (f < kBands) v = band[(size_t)c * kBands + f];
-    else if (f == kBands) v = gfeat[2 * g];
-    else if (f == kBands + 1) v = gfeat[2 * g + 1];
-    X[i] = v;
-}
-
-// Targets y = ln j - ln P_abs where j > 1e-6 of the spectrum's peak, NaN elsewhere.
+// Targets y = ln j - ln P_abs where j > 1e-6 of the spectrum's peak, NaN (masked) elsewhere.
 // One block per sample.
 __global__ void k_targets(int N, const float* __restrict__ j, const float* __restrict__ lnp, float* __restrict__ Y) {
     __shared__ float red[256];
@@ -174,23 +171,35 @@ __global__ void k_colstats(long long rows, int cols, const float* __restrict__ A
 }
 
 // Normalised batch: Xn[b] = bf16((X[idx[b]] - mean) / std), Tn[b] = (T[idx[b]] - ymean) / ystd
-// (NaN kept); rows b >= count are padding (zero inputs, NaN targets).
+// (idx null: row b itself); tb[b] (when given) = the row's mask level in raw units, the
+// largest finite target + ln 1e-6 (NaN if it has none).  blockDim.x = 128.
 __global__ void k_gather_norm(int count, int B, int N, const int* __restrict__ idx, const float* __restrict__ X,
                               const float* __restrict__ T, const float* __restrict__ xm, const float* __restrict__ xs,
                               const float* __restrict__ ym, const float* __restrict__ ys,
-                              __nv_bfloat16* __restrict__ Xn, float* __restrict__ Tn) {
+                              __nv_bfloat16* __restrict__ Xn, float* __restrict__ Tn, float* __restrict__ tb) {
+    __shared__ float red[128];
     int b = blockIdx.x;
     if (b >= B) return;
-    long long r = b < count ? idx[b] : -1;
+    long long r = b < count ? (idx ? idx[b] : b) : -1;
     for (int f = threadIdx.x; f < kFeat; f += blockDim.x) {
         float v = r >= 0 ? (X[(size_t)r * kFeat + f] - xm[f]) / xs[f] : 0.0f;
         Xn[(size_t)b * kFeat + f] = __float2bfloat16_rn(v);
     }
-    if (Tn)
-        for (int n = threadIdx.x; n < N; n += blockDim.x) {
-            float v = r >= 0 ? T[(size_t)r * N + n] : __int_as_float(0x7fc00000);
-            Tn[(size_t)b * N + n] = (v == v) ? (v - ym[n]) / ys[n] : v;
-        }
+    if (!Tn) return;
+    float mx = -INFINITY;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        float v = r >= 0 ? T[(size_t)r * N + n] : __int_as_float(0x7fc00000);
+        if (v == v) mx = fmaxf(mx, v);
+        Tn[(size_t)b * N + n] = (v == v) ? (v - ym[n]) / ys[n] : v;
+    }
+    if (!tb) return;
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + k]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) tb[b] = red[0] > -INFINITY ? red[0] + logf(kMaskRel) : __int_as_float(0x7fc00000);
 }
 
 // Ensemble accumulation (Welford over members) of de-normalised outputs.
@@ -346,9 +355,9 @@ heat_status ensure_batch(heat_ctx* ctx, Surrogate* s, int B) {
     bool ok = !s->Xn.ensure(bf * (size_t)B * kFeat) && !s->Tn.ensure(f4 * (size_t)B * s->N) &&
               !s->dYb.ensure(bf * (size_t)B * wmax) && !s->dXf.ensure(f4 * (size_t)B * kHidden) &&
               !s->dZb.ensure(bf * (size_t)B * kHidden) && !s->T1.ensure(bf * (size_t)B * wmax) &&
-              !s->T2.ensure(bf * (size_t)B * std::max(kFeat, kHidden)) && !s->loss.ensure(f4 * ((size_t)B * s->N / 256 + 16)) &&
+              !s->T2.ensure(bf * (size_t)B * std::max(kFeat, kHidden)) && !s->loss.ensure(16) &&
               !s->ens_mean.ensure(f4 * (size_t)B * s->N) && !s->ens_m2.ensure(f4 * (size_t)B * s->N) &&
-              !s->idx.ensure(sizeof(int) * (size_t)B) && !s->cnt.ensure(16);
+              !s->tb.ensure(sizeof(float) * (size_t)B) && !s->cnt.ensure(16);
     for (int l = 0; l < kLayers; ++l) {
         ok = ok && !s->Z[l].ensure(f4 * (size_t)B * s->Nout[l]);
         ok = ok && !s->Act[l].ensure(bf * (size_t)B * s->Kin[l]);
@@ -402,20 +411,21 @@ heat_status backward(heat_ctx* ctx, Surrogate* s, int m, int B, cudaStream_t st)
 
 // Masked MSE of member m's prediction against s->Tn; dY into s->dYb; returns the loss
 // (mean over valid targets) through *loss when non-null (synchronises).
-heat_status loss_grad(heat_ctx* ctx, Surrogate* s, int B, long long valid, double* loss, cudaStream_t st) {
+// Loss gradient of the batch in Tn against the last layer's output: squared error on the
+// finite targets and, with `bounded`, a one-sided square penalty on masked entries predicted
+// above their row's mask level (tb), so that predictions stay below the mask where the
+// spectrum is; both divided by the number of finite targets (counted on the device).
+// loss_acc (or null) accumulates the batch loss.
+heat_status loss_grad(heat_ctx* ctx, Surrogate* s, int B, bool count, bool bounded, double* loss_acc,
+                      cudaStream_t st) {
     long long n = (long long)B * s->N;
-    int blocks = 0;
-    float inv = valid > 0 ? 1.0f / (float)valid : 0.0f;
-    SCK(launch_mse(n, s->Z[kLayers - 1].as<float>(), s->Tn.as<float>(), inv, s->dYb.as<__nv_bfloat16>(),
-                   s->loss.as<float>(), &blocks, st));
-    if (loss) {
-        std::vector<float> part(blocks);
-        SCK(cudaMemcpyAsync(part.data(), s->loss.p, sizeof(float) * blocks, cudaMemcpyDeviceToHost, st));
-        SCK(cudaStreamSynchronize(st));
-        double t = 0;
-        for (float v : part) t += v;
-        *loss = valid > 0 ? t / (double)valid : 0.0;
+    if (count) {
+        SCK(cudaMemsetAsync(s->cnt.p, 0, 8, st));
+        SCK(launch_count_valid(n, s->Tn.as<float>(), s->cnt.as<unsigned long long>(), st));
     }
+    SCK(launch_mse(n, s->N, s->Z[kLayers - 1].as<float>(), s->Tn.as<float>(), bounded ? s->tb.as<float>() : nullptr,
+                   s->ymean.as<float>(), s->ystd.as<float>(), s->cnt.as<unsigned long long>(),
+                   s->dYb.as<__nv_bfloat16>(), loss_acc, st));
     return HEAT_OK;
 }
 
@@ -500,8 +510,8 @@ heat_status heat_surrogate_samples(heat_ctx* ctx, int cell_begin, int cell_count
     const int N = ctx->N, G = ctx->G;
     // field tables of the range (FP32 u and slopes), reusing the solve's field kernel
     int Cc = (cell_count + 31) / 32 * 32;
-    DevBuf band, tab, lnp;
-    if (band.ensure(4 * (size_t)cell_count * kBands) || tab.ensure(8 * (size_t)N * Cc) ||
+    DevBuf tab, lnp;
+    if (tab.ensure(8 * (size_t)N * Cc) ||
         lnp.ensure(4 * (size_t)cell_count * G))
         return ctx->fail(HEAT_ENOMEM, "heat_surrogate_samples: allocation");
     GrainDev gd{};
@@ -513,15 +523,10 @@ heat_status heat_surrogate_samples(heat_ctx* ctx, int cell_begin, int cell_count
     ch.ua32 = tab.as<float>();
     ch.status = ctx->d_status.as<int>();
     SCK(launch_field(gd, ctx->u_dev, HEAT_F64, cell_begin, ch, HEAT_BUILD_F32, st));
-    k_band_energy<<<cell_count, kBands, 0, st>>>(N, cell_count, ctx->d_lam.as<double>(), (const double*)ctx->u_dev,
-                                                 cell_begin, band.as<float>());
     long long warps = (long long)cell_count * G;
-    k_ln_absorbed<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(N, G, cell_count, tab.as<float>(), Cc,
-                                                                       ctx->d_ce32.as<float>(), ctx->d_sC32.as<float>(),
-                                                                       ctx->d_dln32.as<float>(), lnp.as<float>());
-    long long nf = warps * kFeat;
-    k_feature_rows<<<(unsigned)((nf + 255) / 256), 256, 0, st>>>(cell_count, G, band.as<float>(), s->d_gfeat.as<float>(),
-                                                                X);
+    k_sample_features<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(
+        N, G, cell_count, tab.as<float>(), Cc, ctx->d_ce32.as<float>(), ctx->d_sC32.as<float>(),
+        ctx->d_dln32.as<float>(), s->d_gfeat.as<float>(), X, lnp.as<float>());
     if (j && Y) k_targets<<<(unsigned)warps, 256, 0, st>>>(N, j, lnp.as<float>(), Y);
     if (lnp_out) SCK(cudaMemcpyAsync(lnp_out, lnp.p, 4 * (size_t)warps, cudaMemcpyDeviceToDevice, st));
     SCK(cudaGetLastError());
@@ -552,43 +557,45 @@ heat_status heat_surrogate_train(heat_ctx* ctx, const float* X, const float* Y, 
     if (h != HEAT_OK) return h;
     std::mt19937_64 rng(seed);
     std::vector<int> perm((size_t)n);
+    DevBuf dperm;
+    if (dperm.ensure(sizeof(int) * (size_t)n)) return ctx->fail(HEAT_ENOMEM, "heat_surrogate_train: allocation");
+    const long long steps = (long long)epochs * ((n + batch - 1) / batch);
+    long long t = 0;
     for (int ep = 0; ep < epochs; ++ep) {
         for (long long i = 0; i < n; ++i) perm[i] = (int)i;
         std::shuffle(perm.begin(), perm.end(), rng);
-        double ep_loss = 0.0;
+        SCK(cudaMemcpyAsync(dperm.p, perm.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, st));
+        SCK(cudaMemsetAsync(s->loss.p, 0, sizeof(double), st));
         long long ep_batches = 0;
-        for (long long b0 = 0; b0 < n; b0 += batch) {
+        for (long long b0 = 0; b0 < n; b0 += batch, ++t) {
             int cnt = (int)std::min<long long>(batch, n - b0);
-            SCK(cudaMemcpyAsync(s->idx.p, perm.data() + b0, sizeof(int) * cnt, cudaMemcpyHostToDevice, st));
-            k_gather_norm<<<batch, 128, 0, st>>>(cnt, batch, s->N, s->idx.as<int>(), X, Y, s->xmean.as<float>(),
+            k_gather_norm<<<batch, 128, 0, st>>>(cnt, batch, s->N, dperm.as<int>() + b0, X, Y, s->xmean.as<float>(),
                                                  s->xstd.as<float>(), s->ymean.as<float>(), s->ystd.as<float>(),
-                                                 s->Act[0].as<__nv_bfloat16>(), s->Tn.as<float>());
+                                                 s->Act[0].as<__nv_bfloat16>(), s->Tn.as<float>(), s->tb.as<float>());
             SCK(cudaGetLastError());
-            // valid targets in the batch (the loss is their mean)
-            SCK(cudaMemsetAsync(s->cnt.p, 0, 8, st));
-            SCK(launch_count_valid((long long)batch * s->N, s->Tn.as<float>(), s->cnt.as<unsigned long long>(), st));
-            unsigned long long valid_u = 0;
-            SCK(cudaMemcpyAsync(&valid_u, s->cnt.p, 8, cudaMemcpyDeviceToHost, st));
-            SCK(cudaStreamSynchronize(st));
-            long long valid = (long long)valid_u;
             ++s->step;
             const float b1 = 0.9f, b2 = 0.999f;
             const float bc1 = 1.0f - std::pow(b1, (float)s->step), bc2 = 1.0f - std::pow(b2, (float)s->step);
+            // cosine decay from lr to lr/100 over the steps of this call
+            const float lr_t =
+                lr * (0.01f + 0.99f * 0.5f * (1.0f + std::cos(3.14159265358979f * (float)t / (float)steps)));
             for (int m = 0; m < s->members; ++m) {
                 if ((h = forward(ctx, s, m, batch, st)) != HEAT_OK) return h;
-                double l = 0.0;
-                if ((h = loss_grad(ctx, s, batch, valid, m == 0 ? &l : nullptr, st)) != HEAT_OK) return h;
-                if (m == 0) ep_loss += l;
+                if ((h = loss_grad(ctx, s, batch, m == 0, true, m == 0 ? s->loss.as<double>() : nullptr, st)) != HEAT_OK)
+                    return h;
                 if ((h = backward(ctx, s, m, batch, st)) != HEAT_OK) return h;
                 SCK(launch_adam(s->nparams, 1, (int)s->nparams, Pm(s, m), Gm(s, m),
                                 s->adam_m.as<float>() + (size_t)m * s->nparams,
-                                s->adam_v.as<float>() + (size_t)m * s->nparams, lr, b1, b2, 1e-8f, bc1, bc2, nullptr,
+                                s->adam_v.as<float>() + (size_t)m * s->nparams, lr_t, b1, b2, 1e-8f, bc1, bc2, nullptr,
                                 nullptr, st));
                 if ((h = refresh_bf16(ctx, s, m, st)) != HEAT_OK) return h;
             }
             ++ep_batches;
         }
-        if (loss_history) loss_history[ep] = ep_loss / (double)std::max(1LL, ep_batches);
+        double acc = 0.0;
+        SCK(cudaMemcpyAsync(&acc, s->loss.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        SCK(cudaStreamSynchronize(st));  // also keeps perm's upload ahead of the next shuffle
+        if (loss_history) loss_history[ep] = acc / (double)std::max(1LL, ep_batches);
     }
     SCK(cudaStreamSynchronize(st));
     return HEAT_OK;
@@ -603,14 +610,11 @@ heat_status heat_surrogate_predict(heat_ctx* ctx, const float* X, const float* l
     const int B = 16384;
     heat_status h = ensure_batch(ctx, s, B);
     if (h != HEAT_OK) return h;
-    std::vector<int> iota(B);
     for (long long b0 = 0; b0 < n; b0 += B) {
         int cnt = (int)std::min<long long>(B, n - b0);
-        for (int i = 0; i < cnt; ++i) iota[i] = (int)(b0 + i);
-        SCK(cudaMemcpyAsync(s->idx.p, iota.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, st));
-        k_gather_norm<<<cnt, 128, 0, st>>>(cnt, cnt, s->N, s->idx.as<int>(), X, nullptr, s->xmean.as<float>(),
-                                           s->xstd.as<float>(), s->ymean.as<float>(), s->ystd.as<float>(),
-                                           s->Act[0].as<__nv_bfloat16>(), nullptr);
+        k_gather_norm<<<cnt, 128, 0, st>>>(cnt, cnt, s->N, nullptr, X + (size_t)b0 * kFeat, nullptr,
+                                           s->xmean.as<float>(), s->xstd.as<float>(), s->ymean.as<float>(),
+                                           s->ystd.as<float>(), s->Act[0].as<__nv_bfloat16>(), nullptr, nullptr);
         int rows = (cnt + 63) / 64 * 64;  // GEMM rows in whole tiles of 64 (extra rows are ignored)
         for (int m = 0; m < s->members; ++m) {
             if ((h = forward(ctx, s, m, rows, st)) != HEAT_OK) return h;
@@ -622,7 +626,6 @@ heat_status heat_surrogate_predict(heat_ctx* ctx, const float* X, const float* l
         k_ens_final<<<cnt, 256, 0, st>>>(cnt, s->N, s->members, s->ens_mean.as<float>(), s->ens_m2.as<float>(),
                                          lnp + b0, lnj + (size_t)b0 * s->N, spread + b0);
         SCK(cudaGetLastError());
-        SCK(cudaStreamSynchronize(st));  // the host index buffer is reused
     }
     return HEAT_OK;
 }
@@ -642,15 +645,15 @@ heat_status heat_surrogate_grads(heat_ctx* ctx, int member, const float* Xn, con
     for (size_t i = 0; i < xh.size(); ++i) xb[i] = __float2bfloat16_rn(xh[i]);
     SCK(cudaMemcpy(s->Act[0].p, xb.data(), 2 * xb.size(), cudaMemcpyHostToDevice));
     SCK(cudaMemcpy(s->Tn.p, Tn, 4 * (size_t)n * s->N, cudaMemcpyDeviceToDevice));
-    std::vector<float> th((size_t)n * s->N);
-    SCK(cudaMemcpy(th.data(), Tn, 4 * th.size(), cudaMemcpyDeviceToHost));
-    long long valid = 0;
-    for (float v : th) valid += (v == v);
     if ((h = forward(ctx, s, member, n, st)) != HEAT_OK) return h;
-    if ((h = loss_grad(ctx, s, n, valid, loss_out, st)) != HEAT_OK) return h;
+    SCK(cudaMemsetAsync(s->loss.p, 0, sizeof(double), st));
+    if ((h = loss_grad(ctx, s, n, true, false, s->loss.as<double>(), st)) != HEAT_OK) return h;
     if ((h = backward(ctx, s, member, n, st)) != HEAT_OK) return h;
     SCK(cudaMemcpyAsync(grad_out, Gm(s, member), 4 * (size_t)s->nparams, cudaMemcpyDeviceToDevice, st));
+    double l = 0.0;
+    SCK(cudaMemcpyAsync(&l, s->loss.p, sizeof(double), cudaMemcpyDeviceToHost, st));
     SCK(cudaStreamSynchronize(st));
+    if (loss_out) *loss_out = l;
     return HEAT_OK;
 }
 

@@ -198,7 +198,7 @@ def batched_bins(g: int, G: int = 64) -> int:
     return 32 * int(round(4 + 28 * g / (G - 1)))
 
 
-def batched(cells: int = 4096, n_lambda: int = 1024, grains: int = 64) -> Workload:
+def batched(cells: int = 4096, n_lambda: int = 1024, grains: int = 64, seed: int = 1002) -> Workload:
     """cells x 64 radii (3.5 A - 1 um), alternating carbonaceous / silicate,
     128-1024 bins growing with radius, 1024 wavelengths, chi in [1e-2, 1e4]."""
     lam = wavelength_grid(n_lambda)
@@ -206,7 +206,12 @@ def batched(cells: int = 4096, n_lambda: int = 1024, grains: int = 64) -> Worklo
     comps = ["carbonaceous" if g % 2 == 0 else "silicate" for g in range(grains)]
     nb = [batched_bins(g, grains) for g in range(grains)]
     return _workload(f"batched {cells} cells x {grains} grains, 128-1024 bins, {n_lambda} wavelengths", lam,
-                     radii, comps, nb, cells, 1002, 1e-2, 1e4, -1.0, 1.0)
+                     radii, comps, nb, cells, seed, 1e-2, 1e4, -1.0, 1.0)
+
+
+def composition_flags(wl: Workload) -> np.ndarray:
+    """1 for silicate grains, 0 for carbonaceous (the surrogate's composition input)."""
+    return np.array([1.0 if c == "silicate" else 0.0 for c in wl.composition], dtype=np.float32)
 
 
 def emissivity_heavy(cells: int = 65536, n_lambda: int = 2048, grains: int = 32, nbins: int = 512) -> Workload:
