@@ -67,6 +67,10 @@ def parse():
     ap.add_argument("--sur-epochs", type=int, default=30)
     ap.add_argument("--sur-tol", type=float, default=1e-2, help="ensemble spread (ln j) above which a cell falls back")
     ap.add_argument("--oracle-cells", type=int, default=24, help="cells in the oracle sample")
+    ap.add_argument("--no-emis-heavy", action="store_true",
+                    help="skip the emissivity-heavy workload (65536 cells x 32 grains x 512 bins x 2048 wavelengths)")
+    ap.add_argument("--emis-heavy-oracle-cells", type=int, default=64,
+                    help="cells of the emissivity-heavy workload checked against the oracle")
     return ap.parse_args()
 
 
@@ -197,6 +201,85 @@ def workload_config(wl, path):
                         f"{int(nb.min())}-{int(nb.max())} bins, {wl.n_lambda} wavelengths",
             "cells": wl.n_cells, "grains": wl.n_grains, "bins_total": int(wl.total_bins), "n_lambda": wl.n_lambda,
             "path": path}
+
+
+# ---------------------------------------------------------------------------- emissivity-heavy workload
+def emissivity_heavy_section(args, dev, stream, peaks, peaks_src):
+    """65536 cells x 32 carbonaceous grains x 512 bins x 2048 wavelengths, per-grain FP32
+    output (17 GB): the BF16x3 and TF32x3 tensor-core paths timed, their error measured on
+    a seeded subsample against the oracle, and the emissivity kernel's roofline."""
+    import torch
+
+    import oracle
+    from paper_1311_4627_gb300 import heat
+    from paper_1311_4627_gb300 import workloads as W
+
+    sh = stream.cuda_stream
+    wl = W.emissivity_heavy()
+    cells, G, N, nbt = wl.n_cells, wl.n_grains, wl.n_lambda, wl.total_bins
+    ctx = heat.heat_create_grid(dev.index, wl.lam)
+    heat.heat_set_grains(ctx, wl.radius, wl.cabs, wl.bin_off, wl.T, wl.E, wl.size_weight)
+    u = torch.from_numpy(wl.u).to(dev)
+    heat.heat_set_fields(ctx, cells, u, heat.HEAT_F64, 1, sh)
+    j = torch.empty(cells, G, N, dtype=torch.float32, device=dev)
+    out = {"workload": f"emissivity-heavy: {cells} cells x {G} grains (3.5 A-1 um, carbonaceous), 512 bins, "
+                       f"{N} wavelengths; per-grain FP32 j ({j.numel() * 4 / 1e9:.1f} GB written per step)",
+           "band_elements_per_cell": heat.heat_band_elements(ctx), "paths": {}}
+    nsub = args.emis_heavy_oracle_cells
+    Cf = oracle.grain_cooling(wl)
+    t0 = time.perf_counter()
+    _, j_ref, _, _ = oracle.solve_batch(W.field_subset(wl, np.arange(nsub)), Cf)
+    ot = time.perf_counter() - t0
+    out["oracle"] = {"spectra_per_s": nsub * G / ot, "cores": oracle.max_threads(),
+                     "sample": f"first {nsub} cells x {G} grains"}
+    for name, emis in (("mixed", heat.HEAT_EMIS_BF16X3), ("mixed_tf32", heat.HEAT_EMIS_TF32X3)):
+        o = heat.heat_default_opts(build=heat.HEAT_BUILD_F32, emis=emis, j_dtype=heat.HEAT_F32)
+        heat.heat_solve(ctx, o, None, j, sh)
+        heat.heat_sync(ctx)
+        heat.heat_get_timing(ctx, reset=True)
+        steps = 2
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(steps):
+            heat.heat_solve(ctx, heat.heat_default_opts(build=heat.HEAT_BUILD_F32, emis=emis, j_dtype=heat.HEAT_F32,
+                                                        timing=1), None, j, sh)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        heat.heat_sync(ctx)
+        ms = e0.elapsed_time(e1) / steps
+        kt = heat.heat_get_timing(ctx, reset=True)
+        emis_ms, emis_n = kt["emis"]
+        flop = 2.0 * cells * nbt * N
+        tf32 = emis == heat.HEAT_EMIS_TF32X3
+        pk = peaks["bf16_tflops"] / (2.0 if tf32 else 1.0)
+        step_emis_s = emis_ms / steps / 1e3  # all emissivity launches of one step (chunks x launches)
+        ach = flop / step_emis_s / 1e12
+        bytes_out = 4.0 * cells * G * N
+        gbs = bytes_out / step_emis_s / 1e9
+        js = torch.empty(nsub, G, N, dtype=torch.float64, device=dev)
+        heat.heat_solve(ctx, heat.heat_default_opts(build=heat.HEAT_BUILD_F32, emis=emis, j_dtype=heat.HEAT_F64,
+                                                    cell_count=nsub), None, js, sh)
+        heat.heat_sync(ctx)
+        jg = js.cpu().numpy()
+        peak = j_ref.max(axis=-1, keepdims=True)
+        m = j_ref > 1e-6 * peak
+        err = float(np.max(np.abs(jg[m] - j_ref[m]) / j_ref[m]))
+        out["paths"][name] = {
+            "spectra_per_s": cells * G / (ms / 1e3), "ms_per_step": ms,
+            "kernels_ms_per_step": {k: v[0] / steps for k, v in kt.items()},
+            "emis_roofline": {"bound": "tensor", "unit": "TFLOP/s", "achieved": ach, "peak": pk, "frac": ach / pk,
+                              "launches_per_step": emis_n / steps,
+                              "peak_source": ("measured bf16 burst" + (" x 1/2 (nominal tf32:bf16)" if tf32 else "")
+                                              + f" ({peaks_src})"),
+                              "algorithmic_work": f"2 x cells x bins x wavelengths = {flop:.3e} flop per step",
+                              "output_write_gbs": gbs, "output_write_frac_of_hbm": gbs / peaks["hbm_gbs"]},
+            "max_rel_err_j_masked_1e-6_peak": err}
+        del js
+    heat.heat_destroy(ctx)
+    del j, u
+    torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------------------- GPU leg
@@ -476,6 +559,10 @@ def main():
                 "j_masked_1e-6_peak": float(np.max(np.abs(sur_j[mj] - j_ref[mj]) / j_ref[mj])),
                 "sample": f"{nsub} cells x {G} grains vs the FP64 oracle"}
     line["paths"] = paths
+    if rank == 0 and ws == 1 and not args.no_emis_heavy:
+        del j
+        torch.cuda.empty_cache()
+        line["emissivity_heavy"] = emissivity_heavy_section(args, dev, stream, peaks, peaks_src)
     if rank == 0:
         print(json.dumps(line))
     heat.heat_destroy(ctx)

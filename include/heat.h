@@ -75,7 +75,8 @@ typedef struct heat_opts {
     int emis;           /* HEAT_EMIS_*                                                             */
     int j_dtype;        /* HEAT_F64 or HEAT_F32 element type of j_out                              */
     int size_integrate; /* 0: j_out is [cells][grains][n_lambda]; 1: [cells][n_lambda], sum_g w_g j_g
-                           (size integration needs HEAT_EMIS_F64 for now)                         */
+                           (tensor-core modes: one GEMM over all grains' bins, the sum is formed
+                           in the accumulator)                                                    */
     int cell_begin;     /* first cell solved (0-based)                                             */
     int cell_count;     /* cells solved; <= 0 means all cells from cell_begin                      */
     int chunk_cells;    /* cells per internal chunk (multiple of 32; 0 = library default)         */

@@ -74,7 +74,7 @@ struct heat_ctx {
         std::vector<long long> boff_h, aoff_h;
         int aoff_cells = -1;
         std::vector<int> order;  // grains by K extent, largest first
-    } tc[5];
+    } tc[5], tc_si[5];           // per-grain output; size-integrated output (one operand over all bins)
     DevBuf s_A, s_rowscale;
     // per-kernel event timing
     struct TimedLaunch {

@@ -128,18 +128,21 @@ bool mode_split(int m) { return m == HEAT_EMIS_BF16X3 || m == HEAT_EMIS_TF32X3; 
 
 }  // namespace
 
-// Build the per-grain B' operands and column scales of a tensor-core mode (once per mode).
-static heat_status ensure_tc_mode(heat_ctx* ctx, int m, cudaStream_t st) {
-    auto& t = ctx->tc[m];
+// Build the B' operands and column scales of a tensor-core mode (once per mode).  Per-grain
+// output: one operand per grain from K_g.  Size-integrated output (si): a single operand over
+// all bins of all grains from the size-weighted kernel Kw, so that one GEMM with K = sum of
+// the grains' bins accumulates sum_g w_g j_g in the tensor memory.
+static heat_status ensure_tc_mode(heat_ctx* ctx, int m, bool si, cudaStream_t st) {
+    auto& t = si ? ctx->tc_si[m] : ctx->tc[m];
     if (t.built) return HEAT_OK;
-    const int G = ctx->G, N = ctx->N;
+    const int G = si ? 1 : ctx->G, N = ctx->N;
     const bool tf32 = mode_tf32(m), split = mode_split(m);
     const int ke = tf32 ? 32 : 64;
     t.kp_h.resize(G);
     t.boff_h.resize(G + 1);
     t.boff_h[0] = 0;
     for (int g = 0; g < G; ++g) {
-        int nb = ctx->bin_off[g + 1] - ctx->bin_off[g];
+        int nb = si ? ctx->nbt : ctx->bin_off[g + 1] - ctx->bin_off[g];
         int k = (split ? 3 : 1) * nb;
         t.kp_h[g] = (k + ke - 1) / ke * ke;
         t.boff_h[g + 1] = t.boff_h[g] + (long long)N * t.kp_h[g];
@@ -151,17 +154,19 @@ static heat_status ensure_tc_mode(heat_ctx* ctx, int m, cudaStream_t st) {
     if (t.B.ensure(es * (size_t)t.boff_h[G]) || t.colscale.ensure(sizeof(float) * (size_t)G * N) ||
         upload(t.kp, t.kp_h) || upload(t.boff, t.boff_h))
         return ctx->fail(HEAT_ENOMEM, "heat_solve: allocation of tensor-core operands failed");
-    CKR(launch_pack_k(N, G, ctx->d_bin_off.as<int>(), ctx->d_K.as<double>(), t.boff.as<long long>(), t.kp.as<int>(),
+    CKR(launch_pack_k(N, G, si ? ctx->d_koff_all.as<int>() : ctx->d_bin_off.as<int>(),
+                      si ? ctx->d_Kw.as<double>() : ctx->d_K.as<double>(), t.boff.as<long long>(), t.kp.as<int>(),
                       split, tf32, t.B.p, t.colscale.as<float>(), st));
     t.built = true;
     return HEAT_OK;
 }
 
-// Tensor-core emissivity of one chunk whose P rows are ready at P (row stride nbt).
-static heat_status emis_tc_chunk(heat_ctx* ctx, int m, const double* P, int cells, int Cc_alloc, void* jdst,
+// Tensor-core emissivity of one chunk whose P rows are ready at P (row stride nbt): per-grain
+// j [cells][G][N], or with si the size-integrated J [cells][N].
+static heat_status emis_tc_chunk(heat_ctx* ctx, int m, bool si, const double* P, int cells, int Cc_alloc, void* jdst,
                                  bool j_f64, cudaStream_t st) {
-    auto& t = ctx->tc[m];
-    const int G = ctx->G, N = ctx->N;
+    auto& t = si ? ctx->tc_si[m] : ctx->tc[m];
+    const int G = si ? 1 : ctx->G, N = ctx->N;
     const bool tf32 = mode_tf32(m), split = mode_split(m);
     const size_t es = tf32 ? 4 : 2;
     if (t.aoff_cells != Cc_alloc) {
@@ -173,8 +178,9 @@ static heat_status emis_tc_chunk(heat_ctx* ctx, int m, const double* P, int cell
     }
     if (ctx->s_A.ensure(es * (size_t)t.aoff_h[G]) || ctx->s_rowscale.ensure(sizeof(float) * (size_t)Cc_alloc * G))
         return ctx->fail(HEAT_ENOMEM, "heat_solve: allocation of tensor-core operands failed");
-    CKR(launch_pack_p(cells, G, ctx->d_bin_off.as<int>(), P, ctx->nbt, t.aoff.as<long long>(), t.kp.as<int>(), split,
-                      tf32, ctx->s_A.p, ctx->s_rowscale.as<float>(), st));
+    CKR(launch_pack_p(cells, G, si ? ctx->d_koff_all.as<int>() : ctx->d_bin_off.as<int>(), P, ctx->nbt,
+                      t.aoff.as<long long>(), t.kp.as<int>(), split, tf32, ctx->s_A.p, ctx->s_rowscale.as<float>(),
+                      st));
     EmisTcParams prm;  // ~25 KB of tensor maps, copied into the launch's parameters
     for (int g0 = 0; g0 < G; g0 += kMaxTcGrains) {
         int ng = std::min(kMaxTcGrains, G - g0);
@@ -298,10 +304,11 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
     ctx->w.assign(G, 0.0);
     if (size_weight) std::copy(size_weight, size_weight + G, ctx->w.begin());
     ctx->tasks_NG = -1;
-    for (auto& t : ctx->tc) {
-        t.built = false;
-        t.aoff_cells = -1;
-    }
+    for (auto* modes : {ctx->tc, ctx->tc_si})
+        for (int m = 0; m < 5; ++m) {
+            modes[m].built = false;
+            modes[m].aoff_cells = -1;
+        }
 
     // per-grain cross-section tables
     std::vector<double> Cact((size_t)G * N, 0.0), sC((size_t)G * N, 0.0);
@@ -521,8 +528,6 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
         (o.j_dtype != HEAT_F64 && o.j_dtype != HEAT_F32))
         return ctx->fail(HEAT_EINVAL, "heat_solve: bad precision option");
     if (o.size_integrate && !ctx->has_w) return ctx->fail(HEAT_EINVAL, "heat_solve: size integration needs weights");
-    if (o.size_integrate && o.emis > HEAT_EMIS_F64)
-        return ctx->fail(HEAT_EINVAL, "heat_solve: size integration needs HEAT_EMIS_F64");
     if (o.chunk_cells < 0 || (o.chunk_cells % 32) != 0)
         return ctx->fail(HEAT_EINVAL, "heat_solve: chunk_cells must be a non-negative multiple of 32");
     int c_begin = o.cell_begin, count = o.cell_count > 0 ? o.cell_count : ctx->n_cells - o.cell_begin;
@@ -606,7 +611,7 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
 
     if (want_j && o.emis > HEAT_EMIS_F64) {
         if (!tensor_map_encoder()) return ctx->fail(HEAT_ECUDA, "heat_solve: cuTensorMapEncodeTiled unavailable");
-        heat_status hs = ensure_tc_mode(ctx, o.emis, st);
+        heat_status hs = ensure_tc_mode(ctx, o.emis, o.size_integrate != 0, st);
         if (hs != HEAT_OK) return hs;
     }
     for (int c0 = 0; c0 < count; c0 += chunk) {
@@ -652,7 +657,8 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
                 CKR(cudaEventRecord(ta, st));
             }
             if (o.emis > HEAT_EMIS_F64) {
-                heat_status hs = emis_tc_chunk(ctx, o.emis, ch.P, cells, Cc, jdst, o.j_dtype == HEAT_F64, st);
+                heat_status hs =
+                    emis_tc_chunk(ctx, o.emis, o.size_integrate != 0, ch.P, cells, Cc, jdst, o.j_dtype == HEAT_F64, st);
                 if (hs != HEAT_OK) return hs;
             } else if (o.size_integrate)
                 CKR(launch_gemm_f64(cells, N, 1, ctx->d_koff_all.as<int>(), ch.P, nbt, ctx->d_Kw.as<double>(), N, jdst,
@@ -746,13 +752,14 @@ void heat_destroy(heat_ctx* ctx) {
                       &ctx->d_koff_all, &ctx->d_cde, &ctx->d_u_own, &ctx->s_tasks, &ctx->s_ua64, &ctx->s_su64, &ctx->s_ua32,
                       &ctx->s_Bb64, &ctx->s_Bb32, &ctx->s_xs, &ctx->s_ep, &ctx->s_pabs, &ctx->s_P, &ctx->s_j, &ctx->s_led, &ctx->d_status};
     for (DevBuf* b : bufs) b->release();
-    for (auto& t : ctx->tc) {
-        t.B.release();
-        t.colscale.release();
-        t.kp.release();
-        t.boff.release();
-        t.aoff.release();
-    }
+    for (auto* modes : {ctx->tc, ctx->tc_si})
+        for (int m = 0; m < 5; ++m) {
+            modes[m].B.release();
+            modes[m].colscale.release();
+            modes[m].kp.release();
+            modes[m].boff.release();
+            modes[m].aoff.release();
+        }
     ctx->s_A.release();
     ctx->s_rowscale.release();
     surrogate_free(ctx->sur);

@@ -78,3 +78,23 @@ def test_tc_deterministic(ragged):
     a = lib.solve(want_P=False, emis=heat.HEAT_EMIS_BF16X3, j_dtype=heat.HEAT_F32)[1]
     b = lib.solve(want_P=False, emis=heat.HEAT_EMIS_BF16X3, j_dtype=heat.HEAT_F32)[1]
     assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_tc_size_integrated(ragged, mode):
+    """Size-integrated output from one tensor-core GEMM over all grains' bins (Eq. convolution):
+    J = sum_g w_g j_g against the oracle's per-grain spectra summed in FP64."""
+    wl, _, j, lib = ragged
+    Jref = oracle.size_integrate(wl.size_weight, j)
+    _, J = lib.solve(want_P=False, build=heat.HEAT_BUILD_F64, emis=mode, j_dtype=heat.HEAT_F32, size_integrate=1)
+    assert J.shape == Jref.shape
+    err = masked_relerr(J, Jref)
+    assert err <= TOL[mode], (heat.EMIS_NAMES[mode], err)
+
+
+def test_mixed_size_integrated_meets_1e3(ragged):
+    wl, _, j, lib = ragged
+    Jref = oracle.size_integrate(wl.size_weight, j)
+    _, J = lib.solve(want_P=False, build=heat.HEAT_BUILD_F32, emis=heat.HEAT_EMIS_BF16X3, j_dtype=heat.HEAT_F32,
+                     size_integrate=1, chunk_cells=64)
+    assert masked_relerr(J, Jref) <= 1e-3
