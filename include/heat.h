@@ -88,6 +88,11 @@ typedef struct heat_opts {
                            on the grid, [1] emitted power of the discrete model
                            sum_f P_f T_{f-1,f} (E_f - E_{f-1}) (Eq. cooling); they differ by the
                            bin discretisation of the absorbed photon energies only                */
+    int streams;        /* chunks in flight (1..4), each on an internal stream forked from and
+                           joined back into cuda_stream, so that the recursion of one chunk
+                           overlaps the matrix build and emissivity of the next; 0 = the
+                           library default (or heat_autotune's choice).  Results do not depend
+                           on it or on chunk_cells (every spectrum is computed the same way)   */
 } heat_opts;
 
 /* kernel classes reported by heat_get_timing */
@@ -143,6 +148,14 @@ heat_status heat_set_fields(heat_ctx* ctx, int n_cells, const void* u_lambda, in
  * host_io; device-side errors surface at heat_sync.  Non-interacting grains give
  * P = delta_{i0} (no error).  Errors: HEAT_EINVAL, HEAT_ESTATE, HEAT_ENOMEM, HEAT_ECUDA. */
 heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void* j_out, void* cuda_stream);
+
+/* Time heat_solve on cells [opts->cell_begin, +opts->cell_count) of the current fields for
+ * a set of (streams, chunk_cells) pairs and keep the fastest: later solves whose opts leave
+ * both at 0 use it.  *streams_out / *chunk_out (or NULL) receive the choice.  Runs the
+ * candidates on cuda_stream and synchronises; j_out / P_out as in heat_solve (device, with
+ * room for the cells), overwritten.  Errors: as heat_solve. */
+heat_status heat_autotune(heat_ctx* ctx, const heat_opts* opts, double* P_out, void* j_out, void* cuda_stream,
+                          int* streams_out, int* chunk_out);
 
 /* Wait for all work of the ctx's last calls and return the device status:
  * HEAT_OK, HEAT_ENUMERIC, HEAT_EINVAL (bad field values) or HEAT_ECUDA.  Clears the status. */

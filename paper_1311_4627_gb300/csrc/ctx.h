@@ -53,15 +53,27 @@ struct heat_ctx {
     long long band_per_cell = 0;
     std::vector<int> grain_order;
     DevBuf d_bin_off, d_cabs, d_T, d_E, d_Cf, d_invC, d_invdE, d_invdE32, d_Cact, d_sC, d_ca32, d_ce32, d_sC32,
-        d_rowptr, d_seg_ptr, d_pat64, d_pat32, d_soft, d_soft_off, d_K, d_Kw, d_w, d_koff_all, d_cde;
+        d_rowptr, d_wmax, d_seg_ptr, d_pat64, d_pat32, d_soft, d_soft_off, d_K, d_Kw, d_w, d_koff_all, d_cde;
     // fields
     int n_cells = 0;
     const void* u_dev = nullptr;
     int u_dtype = 0;
     DevBuf d_u_own;
-    // chunk scratch
-    DevBuf s_tasks, s_ua64, s_su64, s_ua32, s_Bb64, s_Bb32, s_xs, s_ep, s_pabs, s_P, s_j, s_led;
-    int tasks_NG = -1;
+    // chunk task lists: (grain, group) pairs, grains in LPT order; `full` for chunks of
+    // tasks_NG groups, `tail` for the last, shorter chunk (tail_NG groups)
+    DevBuf s_tasks, s_tasks_tail;
+    int tasks_NG = -1, tail_NG = -1;
+    // scratch of one chunk in flight; chunks go round-robin over the slots, each slot on
+    // its own stream, so that the FP64 recursion of one chunk overlaps the build and the
+    // tensor-core emissivity of the next
+    static constexpr int kMaxSlots = 4;
+    struct Slot {
+        DevBuf ua64, su64, ua32, Bb64, Bb32, xs, ep, pabs, P, j, led, A, rowscale;
+        cudaStream_t stream = nullptr;  // created on first use
+        cudaEvent_t done = nullptr;
+    } slots[kMaxSlots];
+    cudaEvent_t ev_fork = nullptr;
+    int tuned_streams = 0, tuned_chunk = 0;  // heat_autotune's choice (0: none)
     DevBuf d_status;
     int sms = 0;
     std::vector<double> radius;
@@ -75,7 +87,6 @@ struct heat_ctx {
         int aoff_cells = -1;
         std::vector<int> order;  // grains by K extent, largest first
     } tc[5], tc_si[5];           // per-grain output; size-integrated output (one operand over all bins)
-    DevBuf s_A, s_rowscale;
     // per-kernel event timing
     struct TimedLaunch {
         int kind;

@@ -23,12 +23,12 @@ using namespace heat;
         cudaEvent_t ea_ = nullptr, eb_ = nullptr;          \
         if (o.timing) {                                    \
             ea_ = ctx->take_event();                       \
-            CKR(cudaEventRecord(ea_, st));                 \
+            CKR(cudaEventRecord(ea_, cs));                 \
         }                                                  \
         CKR(call);                                         \
         if (o.timing) {                                    \
             eb_ = ctx->take_event();                       \
-            CKR(cudaEventRecord(eb_, st));                 \
+            CKR(cudaEventRecord(eb_, cs));                 \
             ctx->timed.push_back({(kind), ea_, eb_});      \
         }                                                  \
     } while (0)
@@ -161,33 +161,38 @@ static heat_status ensure_tc_mode(heat_ctx* ctx, int m, bool si, cudaStream_t st
     return HEAT_OK;
 }
 
+// Row offsets of the packed P operands for chunks of Cc_alloc cells (uploaded once per
+// chunk size, before any chunk is launched).
+static heat_status prepare_tc_rows(heat_ctx* ctx, int m, bool si, int Cc_alloc) {
+    auto& t = si ? ctx->tc_si[m] : ctx->tc[m];
+    if (t.aoff_cells == Cc_alloc) return HEAT_OK;
+    const int G = si ? 1 : ctx->G;
+    t.aoff_h.assign(G + 1, 0);
+    for (int g = 0; g < G; ++g) t.aoff_h[g + 1] = t.aoff_h[g] + (long long)Cc_alloc * t.kp_h[g];
+    CKR(cudaDeviceSynchronize());  // earlier solves may still read the old offsets
+    if (upload(t.aoff, t.aoff_h)) return ctx->fail(HEAT_ENOMEM, "heat_solve: allocation failed");
+    t.aoff_cells = Cc_alloc;
+    return HEAT_OK;
+}
+
 // Tensor-core emissivity of one chunk whose P rows are ready at P (row stride nbt): per-grain
-// j [cells][G][N], or with si the size-integrated J [cells][N].
-static heat_status emis_tc_chunk(heat_ctx* ctx, int m, bool si, const double* P, int cells, int Cc_alloc, void* jdst,
-                                 bool j_f64, cudaStream_t st) {
+// j [cells][G][N], or with si the size-integrated J [cells][N].  A / rowscale: the slot's
+// operand buffers (sized by the caller).
+static heat_status emis_tc_chunk(heat_ctx* ctx, int m, bool si, const double* P, int cells, void* A, float* rowscale,
+                                 void* jdst, bool j_f64, cudaStream_t st) {
     auto& t = si ? ctx->tc_si[m] : ctx->tc[m];
     const int G = si ? 1 : ctx->G, N = ctx->N;
     const bool tf32 = mode_tf32(m), split = mode_split(m);
     const size_t es = tf32 ? 4 : 2;
-    if (t.aoff_cells != Cc_alloc) {
-        t.aoff_h.assign(G + 1, 0);
-        for (int g = 0; g < G; ++g) t.aoff_h[g + 1] = t.aoff_h[g] + (long long)Cc_alloc * t.kp_h[g];
-        CKR(cudaStreamSynchronize(st));
-        if (upload(t.aoff, t.aoff_h)) return ctx->fail(HEAT_ENOMEM, "heat_solve: allocation failed");
-        t.aoff_cells = Cc_alloc;
-    }
-    if (ctx->s_A.ensure(es * (size_t)t.aoff_h[G]) || ctx->s_rowscale.ensure(sizeof(float) * (size_t)Cc_alloc * G))
-        return ctx->fail(HEAT_ENOMEM, "heat_solve: allocation of tensor-core operands failed");
     CKR(launch_pack_p(cells, G, si ? ctx->d_koff_all.as<int>() : ctx->d_bin_off.as<int>(), P, ctx->nbt,
-                      t.aoff.as<long long>(), t.kp.as<int>(), split, tf32, ctx->s_A.p, ctx->s_rowscale.as<float>(),
-                      st));
+                      t.aoff.as<long long>(), t.kp.as<int>(), split, tf32, A, rowscale, st));
     EmisTcParams prm;  // ~25 KB of tensor maps, copied into the launch's parameters
     for (int g0 = 0; g0 < G; g0 += kMaxTcGrains) {
         int ng = std::min(kMaxTcGrains, G - g0);
         std::memset(&prm, 0, sizeof(prm));
         for (int i = 0; i < ng; ++i) {
             int g = t.order[g0 + i];
-            char* abase = (char*)ctx->s_A.p + es * (size_t)t.aoff_h[g];
+            char* abase = (char*)A + es * (size_t)t.aoff_h[g];
             char* bbase = (char*)t.B.p + es * (size_t)t.boff_h[g];
             if (!encode_operand(&prm.ta[i], abase, tf32, t.kp_h[g], cells, 128) ||
                 !encode_operand(&prm.tb[i], bbase, tf32, t.kp_h[g], N, 256))
@@ -201,7 +206,7 @@ static heat_status emis_tc_chunk(heat_ctx* ctx, int m, bool si, const double* P,
         prm.G = G;
         prm.mtiles = (cells + 127) / 128;
         prm.ntiles = (N + 255) / 256;
-        prm.rowscale = ctx->s_rowscale.as<float>();
+        prm.rowscale = rowscale;
         prm.colscale = t.colscale.as<float>();
         prm.j = jdst;
         prm.ldj = (long long)G * N;
@@ -210,6 +215,15 @@ static heat_status emis_tc_chunk(heat_ctx* ctx, int m, bool si, const double* P,
         CKR(launch_emis_tc(prm, tf32, ctx->sms, st));
     }
     return HEAT_OK;
+}
+
+// (grain, group) task list of a chunk of NG groups, grains in LPT order.
+static std::vector<int2> make_tasks(const heat_ctx* ctx, int NG) {
+    std::vector<int2> tasks;
+    tasks.reserve((size_t)ctx->G * NG);
+    for (int gi = 0; gi < ctx->G; ++gi)
+        for (int grp = 0; grp < NG; ++grp) tasks.push_back(make_int2(ctx->grain_order[gi], grp));
+    return tasks;
 }
 
 extern "C" {
@@ -226,6 +240,7 @@ void heat_default_opts(heat_opts* o) {
     o->host_io = 0;
     o->timing = 0;
     o->ledger_out = nullptr;
+    o->streams = 0;
 }
 
 heat_status heat_create_grid(heat_ctx** out, int device, int n_lambda, const double* lambda_cm) {
@@ -304,6 +319,8 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
     ctx->w.assign(G, 0.0);
     if (size_weight) std::copy(size_weight, size_weight + G, ctx->w.begin());
     ctx->tasks_NG = -1;
+    ctx->tail_NG = -1;
+    ctx->tuned_streams = ctx->tuned_chunk = 0;
     for (auto* modes : {ctx->tc, ctx->tc_si})
         for (int m = 0; m < 5; ++m) {
             modes[m].built = false;
@@ -336,6 +353,7 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
     std::vector<int> seg_ptr((size_t)G * (N + 1), 0);
     std::vector<SoftF64> soft;
     std::vector<int> soft_off(G + 1, 0);
+    std::vector<int> wmax(G, 1);
     std::vector<int> bin_grain(nbt);
     std::vector<long long> cost(G, 0);
     long long band_total = 0;
@@ -370,6 +388,7 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
             // term even when no photon on the grid reaches bin f from bin f-1
             const bool diag_in_band = jlo < f;
             if (!diag_in_band) jlo = f - 1;
+            wmax[g] = std::max(wmax[g], f - jlo);
             diag_e[off + f - 1] = (int)(band_total + band + (f - 1 - jlo));
             diag_ok[off + f - 1] = diag_in_band ? 1 : 0;
             for (int j = jlo; j < f; ++j) {
@@ -459,7 +478,7 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
     if (upload(ctx->d_bin_off, boff) || upload(ctx->d_cabs, cabs) || upload(ctx->d_T, T) || upload(ctx->d_E, E) ||
         upload(ctx->d_invdE, invdE) || upload(ctx->d_invdE32, invdE32) || upload(ctx->d_Cact, Cact) ||
         upload(ctx->d_sC, sC) || upload(ctx->d_ca32, ca32) || upload(ctx->d_ce32, ce32) ||
-        upload(ctx->d_sC32, sC32) || upload(ctx->d_rowptr, rowptr) || upload(ctx->d_pat64, pat64) ||
+        upload(ctx->d_sC32, sC32) || upload(ctx->d_rowptr, rowptr) || upload(ctx->d_wmax, wmax) || upload(ctx->d_pat64, pat64) ||
         upload(ctx->d_pat32, pat32) || upload(ctx->d_seg_ptr, seg_ptr) || upload(ctx->d_soft, soft) || upload(ctx->d_soft_off, soft_off) ||
         upload(ctx->d_w, ctx->w))
         return ctx->fail(HEAT_ENOMEM, "heat_set_grains: device allocation failed");
@@ -543,45 +562,90 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
     const size_t jel = o.j_dtype == HEAT_F64 ? 8 : 4;
     const size_t jrow = (size_t)(o.size_integrate ? 1 : G) * N;
 
-    // chunk size: bound the scratch of one chunk (B band, X history, field tables) to ~16 GiB
+    // chunks in flight and cells per chunk: the caller's, else heat_autotune's, else the
+    // default: one stream, chunks as large as ~16 GiB of scratch (B band, X history, field
+    // tables) allows, since a chunk's recursion time is bounded below by its longest tasks;
+    // with streams > 1 and no chunk size, the range is split evenly over the streams
+    int nslots = o.streams > 0 ? o.streams : 0;
     int chunk = o.chunk_cells;
+    if (nslots == 0 && chunk == 0 && ctx->tuned_streams > 0) {
+        nslots = ctx->tuned_streams;
+        chunk = ctx->tuned_chunk;
+    }
+    if (nslots == 0) nslots = 1;
+    nslots = std::min(nslots, (int)heat_ctx::kMaxSlots);
     if (chunk == 0) {
         size_t per_group = (size_t)ctx->band_per_cell * 32 * (build == 0 ? 8 : 4) + (size_t)nbt * 32 * 10 +
                            (size_t)N * 32 * 16;
-        size_t groups = std::max<size_t>(1, (size_t(16) << 30) / per_group);
+        size_t groups = std::max<size_t>(1, (size_t(16) << 30) / nslots / per_group);
         chunk = (int)std::min<size_t>(groups * 32, 16384);
+        if (nslots > 1) chunk = std::min(chunk, ((count + nslots - 1) / nslots + 31) / 32 * 32);
     }
-    int span = std::min(count, chunk);
-    int Cc = (span + 31) / 32 * 32, NG = Cc / 32;
+    const int n_chunks = (count + chunk - 1) / chunk;
+    nslots = std::max(1, std::min(nslots, n_chunks));
+    const int span = std::min(count, chunk);
+    const int Cc = (span + 31) / 32 * 32, NG = Cc / 32;
+    const int tail_cells = count - (n_chunks - 1) * chunk;
+    const int tail_NG = (tail_cells + 31) / 32;
+    const bool tc = want_j && o.emis > HEAT_EMIS_F64;
+    const bool si = o.size_integrate != 0;
 
-    // scratch
-    size_t tasks_n = (size_t)G * NG;
-    bool ok = true;
-    ok &= !ctx->s_tasks.ensure(sizeof(int2) * tasks_n);
-    if (build == 0) {
-        ok &= !ctx->s_ua64.ensure(sizeof(double) * (size_t)N * Cc);
-        ok &= !ctx->s_su64.ensure(sizeof(double) * (size_t)N * Cc);
-        ok &= !ctx->s_Bb64.ensure(sizeof(double) * (size_t)NG * std::max(1LL, ctx->band_per_cell) * 32);
-    } else {
-        ok &= !ctx->s_ua32.ensure(sizeof(float2) * (size_t)N * Cc);  // (u, slope) pairs
-        ok &= !ctx->s_Bb32.ensure(sizeof(float) * (size_t)NG * std::max(1LL, ctx->band_per_cell) * 32);
-    }
-    ok &= !ctx->s_xs.ensure(sizeof(double) * (size_t)NG * nbt * 32);
-    ok &= !ctx->s_ep.ensure(sizeof(unsigned short) * (size_t)NG * nbt * 32);
-    ok &= !ctx->s_pabs.ensure(sizeof(double) * (size_t)Cc * G);
-    bool internal_P = (P_out == nullptr) || o.host_io;
-    if (internal_P) ok &= !ctx->s_P.ensure(sizeof(double) * (size_t)Cc * nbt);
-    if (want_j && o.host_io) ok &= !ctx->s_j.ensure(jel * (size_t)Cc * jrow);
-    if (o.ledger_out && o.host_io) ok &= !ctx->s_led.ensure(sizeof(double) * 2 * (size_t)Cc * G);
-    if (!ok) return ctx->fail(HEAT_ENOMEM, "heat_solve: scratch allocation failed");
+    // task lists (uploaded before any chunk is launched: nothing in the chunk loop waits for the host)
     if (ctx->tasks_NG != NG) {
-        std::vector<int2> tasks;
-        tasks.reserve(tasks_n);
-        for (int gi = 0; gi < G; ++gi)
-            for (int grp = 0; grp < NG; ++grp) tasks.push_back(make_int2(ctx->grain_order[gi], grp));
-        CKR(cudaMemcpy(ctx->s_tasks.p, tasks.data(), sizeof(int2) * tasks_n, cudaMemcpyHostToDevice));
+        auto tasks = make_tasks(ctx, NG);
+        if (ctx->s_tasks.ensure(sizeof(int2) * tasks.size()))
+            return ctx->fail(HEAT_ENOMEM, "heat_solve: scratch allocation failed");
+        CKR(cudaDeviceSynchronize());
+        CKR(cudaMemcpy(ctx->s_tasks.p, tasks.data(), sizeof(int2) * tasks.size(), cudaMemcpyHostToDevice));
         ctx->tasks_NG = NG;
     }
+    if (tail_NG != NG && ctx->tail_NG != tail_NG) {
+        auto tasks = make_tasks(ctx, tail_NG);
+        if (ctx->s_tasks_tail.ensure(sizeof(int2) * tasks.size()))
+            return ctx->fail(HEAT_ENOMEM, "heat_solve: scratch allocation failed");
+        CKR(cudaDeviceSynchronize());
+        CKR(cudaMemcpy(ctx->s_tasks_tail.p, tasks.data(), sizeof(int2) * tasks.size(), cudaMemcpyHostToDevice));
+        ctx->tail_NG = tail_NG;
+    }
+    if (tc) {
+        if (!tensor_map_encoder()) return ctx->fail(HEAT_ECUDA, "heat_solve: cuTensorMapEncodeTiled unavailable");
+        heat_status hs = ensure_tc_mode(ctx, o.emis, si, st);
+        if (hs != HEAT_OK) return hs;
+        if ((hs = prepare_tc_rows(ctx, o.emis, si, Cc)) != HEAT_OK) return hs;
+    }
+
+    // scratch of every slot in use
+    bool internal_P = (P_out == nullptr) || o.host_io;
+    for (int k = 0; k < nslots; ++k) {
+        auto& sl = ctx->slots[k];
+        bool ok = true;
+        if (build == 0) {
+            ok &= !sl.ua64.ensure(sizeof(double) * (size_t)N * Cc);
+            ok &= !sl.su64.ensure(sizeof(double) * (size_t)N * Cc);
+            ok &= !sl.Bb64.ensure(sizeof(double) * (size_t)NG * std::max(1LL, ctx->band_per_cell) * 32);
+        } else {
+            ok &= !sl.ua32.ensure(sizeof(float2) * (size_t)N * Cc);  // (u, slope) pairs
+            ok &= !sl.Bb32.ensure(sizeof(float) * (size_t)NG * std::max(1LL, ctx->band_per_cell) * 32);
+        }
+        ok &= !sl.xs.ensure(sizeof(double) * (size_t)NG * nbt * 32);
+        ok &= !sl.ep.ensure(sizeof(unsigned short) * (size_t)NG * nbt * 32);
+        ok &= !sl.pabs.ensure(sizeof(double) * (size_t)Cc * G);
+        if (internal_P) ok &= !sl.P.ensure(sizeof(double) * (size_t)Cc * nbt);
+        if (want_j && o.host_io) ok &= !sl.j.ensure(jel * (size_t)Cc * jrow);
+        if (o.ledger_out && o.host_io) ok &= !sl.led.ensure(sizeof(double) * 2 * (size_t)Cc * G);
+        if (tc) {
+            auto& t = si ? ctx->tc_si[o.emis] : ctx->tc[o.emis];
+            const int Gt = si ? 1 : G;
+            ok &= !sl.A.ensure((mode_tf32(o.emis) ? 4 : 2) * (size_t)t.aoff_h[Gt]);
+            ok &= !sl.rowscale.ensure(sizeof(float) * (size_t)Cc * Gt);
+        }
+        if (!ok) return ctx->fail(HEAT_ENOMEM, "heat_solve: scratch allocation failed");
+        if (nslots > 1 && !sl.stream) {
+            CKR(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking));
+            CKR(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
+        }
+    }
+    if (nslots > 1 && !ctx->ev_fork) CKR(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
 
     GrainDev gd;
     gd.N = N;
@@ -602,6 +666,7 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
     gd.invdE = ctx->d_invdE.as<double>();
     gd.cde = ctx->d_cde.as<double>();
     gd.rowptr = ctx->d_rowptr.as<int>();
+    gd.wmax = ctx->d_wmax.as<int>();
     gd.band_total = ctx->band_per_cell;
     gd.seg_ptr = ctx->d_seg_ptr.as<int>();
     gd.pat64 = ctx->d_pat64.as<PatF64>();
@@ -609,80 +674,142 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
     gd.soft = ctx->d_soft.as<SoftF64>();
     gd.soft_off = ctx->d_soft_off.as<int>();
 
-    if (want_j && o.emis > HEAT_EMIS_F64) {
-        if (!tensor_map_encoder()) return ctx->fail(HEAT_ECUDA, "heat_solve: cuTensorMapEncodeTiled unavailable");
-        heat_status hs = ensure_tc_mode(ctx, o.emis, o.size_integrate != 0, st);
-        if (hs != HEAT_OK) return hs;
+    // fork: every slot stream starts after the work already queued on the caller's stream
+    if (nslots > 1) {
+        CKR(cudaEventRecord(ctx->ev_fork, st));
+        for (int k = 0; k < nslots; ++k) CKR(cudaStreamWaitEvent(ctx->slots[k].stream, ctx->ev_fork, 0));
     }
-    for (int c0 = 0; c0 < count; c0 += chunk) {
-        int cells = std::min(chunk, count - c0);
-        int cc_pad = (cells + 31) / 32 * 32;
+    for (int ci = 0; ci < n_chunks; ++ci) {
+        const int c0 = ci * chunk;
+        auto& sl = ctx->slots[ci % nslots];
+        cudaStream_t cs = nslots > 1 ? sl.stream : st;
+        const int cells = std::min(chunk, count - c0);
+        const int cc_pad = (cells + 31) / 32 * 32;
         ChunkDev ch;
         ch.cells = cells;
         ch.Cc = cc_pad;
         ch.NG = cc_pad / 32;
-        ch.tasks = ctx->s_tasks.as<int2>();
+        ch.tasks = (ch.NG == NG ? ctx->s_tasks : ctx->s_tasks_tail).as<int2>();
         ch.n_tasks = G * ch.NG;
-        if (ch.NG != NG) {
-            // last, shorter chunk: tasks list must only hold its groups
-            std::vector<int2> tasks;
-            for (int gi = 0; gi < G; ++gi)
-                for (int grp = 0; grp < ch.NG; ++grp) tasks.push_back(make_int2(ctx->grain_order[gi], grp));
-            CKR(cudaMemcpyAsync(ctx->s_tasks.p, tasks.data(), sizeof(int2) * tasks.size(), cudaMemcpyHostToDevice, st));
-            CKR(cudaStreamSynchronize(st));
-            ctx->tasks_NG = ch.NG;
-        }
-        ch.ua64 = ctx->s_ua64.as<double>();
-        ch.su64 = ctx->s_su64.as<double>();
-        ch.ua32 = ctx->s_ua32.as<float>();
-        ch.Bb64 = ctx->s_Bb64.as<double>();
-        ch.Bb32 = ctx->s_Bb32.as<float>();
-        ch.xs = ctx->s_xs.as<double>();
-        ch.ep = ctx->s_ep.as<unsigned short>();
-        ch.pabs = ctx->s_pabs.as<double>();
+        ch.ua64 = sl.ua64.as<double>();
+        ch.su64 = sl.su64.as<double>();
+        ch.ua32 = sl.ua32.as<float>();
+        ch.Bb64 = sl.Bb64.as<double>();
+        ch.Bb32 = sl.Bb32.as<float>();
+        ch.xs = sl.xs.as<double>();
+        ch.ep = sl.ep.as<unsigned short>();
+        ch.pabs = sl.pabs.as<double>();
         ch.status = ctx->d_status.as<int>();
         ch.ldP = nbt;
-        ch.P = internal_P ? ctx->s_P.as<double>() : P_out + (size_t)c0 * nbt;
+        ch.P = internal_P ? sl.P.as<double>() : P_out + (size_t)c0 * nbt;
         ch.ledger = !o.ledger_out ? nullptr
-                    : (o.host_io ? ctx->s_led.as<double>() : o.ledger_out + (size_t)c0 * G * 2);
+                    : (o.host_io ? sl.led.as<double>() : o.ledger_out + (size_t)c0 * G * 2);
         long long cell0 = (long long)c_begin + c0;
-        TIMED(HEAT_T_FIELD, launch_field(gd, ctx->u_dev, ctx->u_dtype, cell0, ch, build, st));
-        TIMED(HEAT_T_BUILD, launch_build(gd, ch, build, st));
-        TIMED(HEAT_T_RECUR, launch_recur(gd, ch, build, st));
+        TIMED(HEAT_T_FIELD, launch_field(gd, ctx->u_dev, ctx->u_dtype, cell0, ch, build, cs));
+        TIMED(HEAT_T_BUILD, launch_build(gd, ch, build, cs));
+        TIMED(HEAT_T_RECUR, launch_recur(gd, ch, build, cs));
         if (want_j) {
-            char* jdst = o.host_io ? ctx->s_j.as<char>() : (char*)j_out + (size_t)c0 * jrow * jel;
+            char* jdst = o.host_io ? sl.j.as<char>() : (char*)j_out + (size_t)c0 * jrow * jel;
             cudaEvent_t ta = nullptr;
             if (o.timing) {
                 ta = ctx->take_event();
-                CKR(cudaEventRecord(ta, st));
+                CKR(cudaEventRecord(ta, cs));
             }
-            if (o.emis > HEAT_EMIS_F64) {
-                heat_status hs =
-                    emis_tc_chunk(ctx, o.emis, o.size_integrate != 0, ch.P, cells, Cc, jdst, o.j_dtype == HEAT_F64, st);
+            if (tc) {
+                heat_status hs = emis_tc_chunk(ctx, o.emis, si, ch.P, cells, sl.A.p, sl.rowscale.as<float>(), jdst,
+                                               o.j_dtype == HEAT_F64, cs);
                 if (hs != HEAT_OK) return hs;
-            } else if (o.size_integrate)
+            } else if (si)
                 CKR(launch_gemm_f64(cells, N, 1, ctx->d_koff_all.as<int>(), ch.P, nbt, ctx->d_Kw.as<double>(), N, jdst,
-                                    N, 0, o.j_dtype == HEAT_F32, st));
+                                    N, 0, o.j_dtype == HEAT_F32, cs));
             else
                 CKR(launch_gemm_f64(cells, N, G, ctx->d_bin_off.as<int>(), ch.P, nbt, ctx->d_K.as<double>(), N, jdst,
-                                    (long long)G * N, N, o.j_dtype == HEAT_F32, st));
+                                    (long long)G * N, N, o.j_dtype == HEAT_F32, cs));
             if (o.timing) {
                 cudaEvent_t tb = ctx->take_event();
-                CKR(cudaEventRecord(tb, st));
+                CKR(cudaEventRecord(tb, cs));
                 ctx->timed.push_back({HEAT_T_EMIS, ta, tb});
             }
             if (o.host_io)
                 CKR(cudaMemcpyAsync((char*)j_out + (size_t)c0 * jrow * jel, jdst, (size_t)cells * jrow * jel,
-                                    cudaMemcpyDeviceToHost, st));
+                                    cudaMemcpyDeviceToHost, cs));
         }
         if (o.ledger_out && o.host_io)
             CKR(cudaMemcpyAsync(o.ledger_out + (size_t)c0 * G * 2, ch.ledger, sizeof(double) * 2 * (size_t)cells * G,
-                                cudaMemcpyDeviceToHost, st));
+                                cudaMemcpyDeviceToHost, cs));
         if (P_out && o.host_io)
             CKR(cudaMemcpyAsync(P_out + (size_t)c0 * nbt, ch.P, sizeof(double) * (size_t)cells * nbt,
-                                cudaMemcpyDeviceToHost, st));
-        if (o.host_io) CKR(cudaStreamSynchronize(st));
+                                cudaMemcpyDeviceToHost, cs));
     }
+    // join: the caller's stream continues after every chunk
+    if (nslots > 1)
+        for (int k = 0; k < nslots; ++k) {
+            CKR(cudaEventRecord(ctx->slots[k].done, ctx->slots[k].stream));
+            CKR(cudaStreamWaitEvent(st, ctx->slots[k].done, 0));
+        }
+    if (o.host_io) CKR(cudaStreamSynchronize(st));
+    return HEAT_OK;
+}
+
+heat_status heat_autotune(heat_ctx* ctx, const heat_opts* opts, double* P_out, void* j_out, void* stream,
+                          int* streams_out, int* chunk_out) {
+    if (!ctx || !opts) return HEAT_EINVAL;
+    if (opts->host_io) return ctx->fail(HEAT_EINVAL, "heat_autotune: device buffers only");
+    CKR(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int count = opts->cell_count > 0 ? opts->cell_count : ctx->n_cells - opts->cell_begin;
+    struct Cand {
+        int streams, chunk;
+    };
+    std::vector<Cand> cands;
+    for (int sN : {1, 2, 3})
+        for (int div : {1, 2, 4, 8}) {
+            int chunk = ((count + sN * div - 1) / (sN * div) + 31) / 32 * 32;
+            if (chunk < 256 && div > 1) continue;
+            if (sN > 1 && (count + chunk - 1) / chunk < sN) continue;
+            cands.push_back({sN, chunk});
+        }
+    cudaEvent_t e0, e1;
+    CKR(cudaEventCreate(&e0));
+    CKR(cudaEventCreate(&e1));
+    float best = 1e30f;
+    Cand pick{0, 0};
+    for (const Cand& c : cands) {
+        heat_opts o = *opts;
+        o.streams = c.streams;
+        o.chunk_cells = c.chunk;
+        o.timing = 0;
+        heat_status h = heat_solve(ctx, &o, P_out, j_out, stream);  // warm-up: allocations, uploads
+        if (h != HEAT_OK) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return h;
+        }
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+            CKR(cudaEventRecord(e0, st));
+            if ((h = heat_solve(ctx, &o, P_out, j_out, stream)) != HEAT_OK) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return h;
+            }
+            CKR(cudaEventRecord(e1, st));
+            CKR(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            CKR(cudaEventElapsedTime(&ms, e0, e1));
+            ms_min = std::min(ms_min, ms);
+        }
+        if (ms_min < best) {
+            best = ms_min;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->tuned_streams = pick.streams;
+    ctx->tuned_chunk = pick.chunk;
+    if (streams_out) *streams_out = pick.streams;
+    if (chunk_out) *chunk_out = pick.chunk;
     return HEAT_OK;
 }
 
@@ -747,11 +874,18 @@ void heat_destroy(heat_ctx* ctx) {
     cudaSetDevice(ctx->device);
     DevBuf* bufs[] = {&ctx->d_lam, &ctx->d_dln, &ctx->d_lam32, &ctx->d_dln32, &ctx->d_bin_off, &ctx->d_cabs,
                       &ctx->d_T, &ctx->d_E, &ctx->d_Cf, &ctx->d_invC, &ctx->d_invdE, &ctx->d_invdE32, &ctx->d_Cact,
-                      &ctx->d_sC, &ctx->d_ca32, &ctx->d_ce32, &ctx->d_sC32, &ctx->d_rowptr, &ctx->d_seg_ptr,
+                      &ctx->d_sC, &ctx->d_ca32, &ctx->d_ce32, &ctx->d_sC32, &ctx->d_rowptr, &ctx->d_wmax, &ctx->d_seg_ptr,
                       &ctx->d_pat64, &ctx->d_pat32, &ctx->d_soft, &ctx->d_soft_off, &ctx->d_K, &ctx->d_Kw, &ctx->d_w,
-                      &ctx->d_koff_all, &ctx->d_cde, &ctx->d_u_own, &ctx->s_tasks, &ctx->s_ua64, &ctx->s_su64, &ctx->s_ua32,
-                      &ctx->s_Bb64, &ctx->s_Bb32, &ctx->s_xs, &ctx->s_ep, &ctx->s_pabs, &ctx->s_P, &ctx->s_j, &ctx->s_led, &ctx->d_status};
+                      &ctx->d_koff_all, &ctx->d_cde, &ctx->d_u_own, &ctx->s_tasks, &ctx->s_tasks_tail, &ctx->d_status};
     for (DevBuf* b : bufs) b->release();
+    for (auto& sl : ctx->slots) {
+        DevBuf* sb[] = {&sl.ua64, &sl.su64, &sl.ua32, &sl.Bb64, &sl.Bb32, &sl.xs, &sl.ep,
+                        &sl.pabs, &sl.P, &sl.j, &sl.led, &sl.A, &sl.rowscale};
+        for (DevBuf* b : sb) b->release();
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+        if (sl.done) cudaEventDestroy(sl.done);
+    }
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     for (auto* modes : {ctx->tc, ctx->tc_si})
         for (int m = 0; m < 5; ++m) {
             modes[m].B.release();
@@ -760,8 +894,6 @@ void heat_destroy(heat_ctx* ctx) {
             modes[m].boff.release();
             modes[m].aoff.release();
         }
-    ctx->s_A.release();
-    ctx->s_rowscale.release();
     surrogate_free(ctx->sur);
     ctx->sur = nullptr;
     for (auto& t : ctx->timed) {
@@ -798,6 +930,7 @@ __attribute__((visibility("hidden"))) heat_status heat_internal_grain_view(heat_
     gd->invdE = ctx->d_invdE.as<double>();
     gd->cde = ctx->d_cde.as<double>();
     gd->rowptr = ctx->d_rowptr.as<int>();
+    gd->wmax = ctx->d_wmax.as<int>();
     gd->band_total = ctx->band_per_cell;
     gd->seg_ptr = ctx->d_seg_ptr.as<int>();
     gd->pat64 = ctx->d_pat64.as<PatF64>();

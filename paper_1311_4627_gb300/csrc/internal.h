@@ -40,6 +40,7 @@ struct GrainDev {
     const double* invdE;    // [nbt] 1/(E_{j+1}-E_j) (0 for the last bin)
     const int* rowptr;      // [nbt + G] per grain, rows f = 0..M: band elements of row f at
                             //   rowptr[off_g + g + f] .. rowptr[off_g + g + f + 1] (global indices)
+    const int* wmax;        // [G] widest band row of grain g (selects the recursion's window size)
     long long band_total;   // band elements of all grains (per cell)
     const int* seg_ptr;     // [G][N+1] pattern entries of grain g in segment n at
                             //   seg_ptr[g*(N+1)+n] .. seg_ptr[g*(N+1)+n+1]

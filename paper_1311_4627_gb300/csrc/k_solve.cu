@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(128) k_build(GrainDev gd, ChunkDev ch) {
     int task = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     int lane = threadIdx.x & 31;
     if (task >= ch.n_tasks) return;
-    const int N = gd.N, Cc = ch.Cc, nbt = gd.nbt;
+    const int N = gd.N, Cc = ch.Cc;
     int g = ch.tasks[task].x, grp = ch.tasks[task].y;
     int off = gd.bin_off[g];
     int cc = grp * 32 + lane;
@@ -230,21 +230,60 @@ __device__ __forceinline__ double band_b(const float* B32, const double* B64, in
     return __ldcs(B64 + (size_t)e * 32);
 }
 
+// B in its stored type (kept in registers ahead of use), and its FP64 value
 template <int BUILD>
-__global__ void __launch_bounds__(128) k_recur(GrainDev gd, ChunkDev ch) {
-    int task = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    int lane = threadIdx.x & 31;
-    if (task >= ch.n_tasks) return;
+struct BandRaw {
+    using T = double;
+    static __device__ __forceinline__ T load(const float*, const double* B64, int e) {
+        return __ldcs(B64 + (size_t)e * 32);
+    }
+    static __device__ __forceinline__ double wide(T v) { return v; }
+};
+template <>
+struct BandRaw<1> {
+    using T = float;
+    static __device__ __forceinline__ T load(const float* B32, const double*, int e) {
+        return __ldcs(B32 + (size_t)e * 32);
+    }
+    static __device__ __forceinline__ double wide(T v) { return widen_pos(v); }
+};
+
+// Window part of a row: element e1-1-k multiplies X_{f-1-k} = w[k] for k < nreg (<= W);
+// a jump into the unrolled tail, so no predicated-off FMA occupies the FP64 pipe.
+template <int BUILD, int W>
+__device__ __forceinline__ void window_tail(int nreg, const typename BandRaw<BUILD>::T (&br)[W],
+                                            const double (&w)[W], double& S, double& S1) {
+    using Raw = BandRaw<BUILD>;
+    switch (nreg) {
+        case 8: if constexpr (W > 7) S1 = fma(Raw::wide(br[7 % W]), w[7 % W], S1);  // fallthrough
+        case 7: if constexpr (W > 6) S = fma(Raw::wide(br[6 % W]), w[6 % W], S);    // fallthrough
+        case 6: if constexpr (W > 5) S1 = fma(Raw::wide(br[5 % W]), w[5 % W], S1);  // fallthrough
+        case 5: if constexpr (W > 4) S = fma(Raw::wide(br[4 % W]), w[4 % W], S);    // fallthrough
+        case 4: if constexpr (W > 3) S1 = fma(Raw::wide(br[3 % W]), w[3 % W], S1);  // fallthrough
+        case 3: if constexpr (W > 2) S = fma(Raw::wide(br[2 % W]), w[2 % W], S);    // fallthrough
+        case 2: if constexpr (W > 1) S1 = fma(Raw::wide(br[1 % W]), w[1 % W], S1);  // fallthrough
+        case 1: S = fma(Raw::wide(br[0]), w[0], S);                                 // fallthrough
+        default: break;
+    }
+}
+
+// One task: the recursion of grain g for the 32 cells of group grp (lane = cell).  W is
+// the register window: the last W values of X, and the window part of each row's band
+// (its last min(width, W) elements), prefetched one row ahead.  The row loop's fixed
+// cost grows with W, so grains whose rows are all narrow (the large grains: nearly a
+// chain) use a small W.
+template <int BUILD, int W>
+__device__ __forceinline__ void recur_task(const GrainDev& gd, const ChunkDev& ch, int g, int grp, int lane) {
+    using Raw = BandRaw<BUILD>;
     const int nbt = gd.nbt;
-    int g = ch.tasks[task].x, grp = ch.tasks[task].y;
-    int off = gd.bin_off[g];
-    int M = gd.bin_off[g + 1] - off - 1;
-    int cc = grp * 32 + lane;
-    size_t xb = ((size_t)grp * nbt + off) * 32 + lane;
+    const int off = gd.bin_off[g];
+    const int M = gd.bin_off[g + 1] - off - 1;
+    const int cc = grp * 32 + lane;
+    const size_t xb = ((size_t)grp * nbt + off) * 32 + lane;
     const int* rp = gd.rowptr + off + g;
     const double* ic_row = gd.invC + off;
     double* xl = ch.xs + xb;
-    size_t bb = (size_t)grp * gd.band_total * 32 + lane;
+    const size_t bb = (size_t)grp * gd.band_total * 32 + lane;
     const float* __restrict__ B32 = ch.Bb32 + (BUILD ? bb : 0);
     const double* __restrict__ B64 = ch.Bb64 + (BUILD ? 0 : bb);
     bool numeric_bad = false;
@@ -254,20 +293,38 @@ __global__ void __launch_bounds__(128) k_recur(GrainDev gd, ChunkDev ch) {
     xl[0] = 1.0;
     epl[0] = 0;
     double total = 1.0;  // running sum of X, rescaled with it
-    // register window of the last 8 X values: w[k] = X_{f-1-k}; the band's last (most
-    // recent) elements read it instead of reloading what this thread just stored
-    double w[8];
+    // register window: w[k] = X_{f-1-k}; the band's last elements read it instead of
+    // reloading what this thread just stored
+    double w[W];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) w[k] = 0.0;
+    for (int k = 0; k < W; ++k) w[k] = 0.0;
     w[0] = 1.0;
-    int e = rp[1];
+    // row pipeline: the band bounds, the cooling rate and the window-part B values of row
+    // f+1 are loaded while row f is computed
+    int e = rp[1];                       // band of row f: elements [e, e1)
+    int e1 = rp[2];
+    int e2 = M >= 2 ? rp[3] : e1;        // end of row f+1's band
+    double ic = ic_row[1];
+    typename Raw::T br[W];               // window part of row f: br[k] = B at element e1-1-k
+    {
+        const int nr = min(e1 - e, W);
+#pragma unroll
+        for (int k = 0; k < W; ++k) br[k] = (k < nr) ? Raw::load(B32, B64, e1 - 1 - k) : 0;
+    }
     const int e_end = rp[M + 1];
     // L2 prefetch of the B stream, kept 64..96 elements ahead: lane k fetches the
     // 128-byte line of element pf + k (lines of all 32 lanes of one element)
     const size_t lane_base = bb - lane;
     int pf = e;
     for (int f = 1; f <= M; ++f) {
-        const int e1 = rp[f + 1];
+        // next row's loads
+        const bool more = f < M;
+        const int e3 = f + 2 <= M ? rp[f + 3] : e2;
+        const double ic_n = more ? ic_row[f + 1] : 0.0;
+        const int nr_n = more ? min(e2 - e1, W) : 0;
+        typename Raw::T br_n[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) br_n[k] = (k < nr_n) ? Raw::load(B32, B64, e2 - 1 - k) : 0;
         while (pf < e1 + 64 && pf < e_end) {
             int q = pf + lane;
             if (q < e_end) {
@@ -278,41 +335,27 @@ __global__ void __launch_bounds__(128) k_recur(GrainDev gd, ChunkDev ch) {
             pf += 32;
         }
         const int width = e1 - e;          // band of row f: j in [f - width, f)
-        const int nreg = min(width, 8);    // its last nreg elements come from the window
+        const int nreg = min(width, W);    // its last nreg elements come from the window
         const int e_mem = e1 - nreg;       // elements before e_mem read X from memory
-        int j = f - width;
         double S = 0.0, S1 = 0.0;
-        for (; e + 8 <= e_mem; e += 8, j += 8) {
-            double b[8], x[8];
+        if (e < e_mem) {
+            int j = f - width;
+            for (; e + 8 <= e_mem; e += 8, j += 8) {
+                double b[8], x[8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) b[k] = band_b<BUILD>(B32, B64, e + k);
+                for (int k = 0; k < 8; ++k) b[k] = band_b<BUILD>(B32, B64, e + k);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) x[k] = xl[(j + k) * 32];
+                for (int k = 0; k < 8; ++k) x[k] = xl[(j + k) * 32];
 #pragma unroll
-            for (int k = 0; k < 8; k += 2) {
-                S = fma(b[k], x[k], S);
-                S1 = fma(b[k + 1], x[k + 1], S1);
+                for (int k = 0; k < 8; k += 2) {
+                    S = fma(b[k], x[k], S);
+                    S1 = fma(b[k + 1], x[k + 1], S1);
+                }
             }
+            for (; e < e_mem; ++e, ++j) S1 = fma(band_b<BUILD>(B32, B64, e), xl[j * 32], S1);
         }
-        for (; e < e_mem; ++e, ++j) S1 = fma(band_b<BUILD>(B32, B64, e), xl[j * 32], S1);
-        // window part: element e1-1-k multiplies X_{f-1-k} = w[k], k < nreg
-        double br[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) br[k] = (k < nreg) ? band_b<BUILD>(B32, B64, e1 - 1 - k) : 0.0;
-        switch (nreg) {  // no predicated-off FMAs: jump into the unrolled tail
-            case 8: S1 = fma(br[7], w[7], S1);
-            case 7: S = fma(br[6], w[6], S);
-            case 6: S1 = fma(br[5], w[5], S1);
-            case 5: S = fma(br[4], w[4], S);
-            case 4: S1 = fma(br[3], w[3], S1);
-            case 3: S = fma(br[2], w[2], S);
-            case 2: S1 = fma(br[1], w[1], S1);
-            case 1: S = fma(br[0], w[0], S);
-            default: break;
-        }
-        e = e1;
+        window_tail<BUILD, W>(nreg, br, w, S, S1);
         if (width > 1) S += S1;
-        const double ic = ic_row[f];
         double X = S * ic;
         if (__double2hiint(ic) == 0 && __double2loint(ic) == 0) {  // zero cooling rate
             X = 0.0;
@@ -322,19 +365,26 @@ __global__ void __launch_bounds__(128) k_recur(GrainDev gd, ChunkDev ch) {
         epl[f * 32] = (unsigned short)epoch;
         total += X;
 #pragma unroll
-        for (int k = 7; k > 0; --k) w[k] = w[k - 1];
+        for (int k = W - 1; k > 0; --k) w[k] = w[k - 1];
         w[0] = X;
         if (above_rescale(X)) {
             ++epoch;
-            const int lo = (f < M) ? (f + 1) - (rp[f + 2] - rp[f + 1]) : f + 1;  // next row's band start
+            const int lo = more ? (f + 1) - (e2 - e1) : f + 1;  // next row's band start
             for (int i = lo; i <= f; ++i) {
                 xl[i * 32] *= kRescaleSmall;
                 epl[i * 32] = (unsigned short)epoch;
             }
             total *= kRescaleSmall;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) w[k] *= kRescaleSmall;
+            for (int k = 0; k < W; ++k) w[k] *= kRescaleSmall;
         }
+        // rotate the row pipeline
+        e = e1;
+        e1 = e2;
+        e2 = e3;
+        ic = ic_n;
+#pragma unroll
+        for (int k = 0; k < W; ++k) br[k] = br_n[k];
     }
     if (cc < ch.cells) {
         const double inv = 1.0 / total;
@@ -357,6 +407,23 @@ __global__ void __launch_bounds__(128) k_recur(GrainDev gd, ChunkDev ch) {
         }
     }
     if (numeric_bad) atomicOr(ch.status, kStatNumeric);
+}
+
+template <int BUILD>
+__global__ void __launch_bounds__(128, 4) k_recur(GrainDev gd, ChunkDev ch) {
+    const int task = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (task >= ch.n_tasks) return;
+    const int g = ch.tasks[task].x, grp = ch.tasks[task].y;
+    const int wm = gd.wmax[g];  // warp-uniform
+    if (wm <= 1)
+        recur_task<BUILD, 1>(gd, ch, g, grp, lane);
+    else if (wm <= 2)
+        recur_task<BUILD, 2>(gd, ch, g, grp, lane);
+    else if (wm <= 4)
+        recur_task<BUILD, 4>(gd, ch, g, grp, lane);
+    else
+        recur_task<BUILD, 8>(gd, ch, g, grp, lane);
 }
 
 cudaError_t launch_field(const GrainDev& g, const void* u, int dtype, long long cell0, const ChunkDev& ch, int build,

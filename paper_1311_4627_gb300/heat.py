@@ -41,7 +41,7 @@ class heat_opts(ctypes.Structure):
     _fields_ = [("build", ctypes.c_int), ("emis", ctypes.c_int), ("j_dtype", ctypes.c_int),
                 ("size_integrate", ctypes.c_int), ("cell_begin", ctypes.c_int), ("cell_count", ctypes.c_int),
                 ("chunk_cells", ctypes.c_int), ("host_io", ctypes.c_int), ("timing", ctypes.c_int),
-                ("ledger_out", ctypes.c_void_p)]
+                ("ledger_out", ctypes.c_void_p), ("streams", ctypes.c_int)]
 
 
 _lib = None
@@ -78,6 +78,9 @@ def lib():
         L.heat_get_cooling.argtypes = [_vp, _vp]
         L.heat_band_elements.restype = ctypes.c_int
         L.heat_band_elements.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong)]
+        L.heat_autotune.restype = ctypes.c_int
+        L.heat_autotune.argtypes = [_vp, ctypes.POINTER(heat_opts), _vp, _vp, _vp, ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int)]
         L.heat_get_timing.restype = ctypes.c_int
         L.heat_get_timing.argtypes = [_vp, _vp, _vp, ctypes.c_int]
         L.heat_solve_noalloc.restype = ctypes.c_int
@@ -165,6 +168,15 @@ def heat_set_fields(ctx, n_cells, u, dtype, on_device, stream=None):
 
 def heat_solve(ctx, opts: heat_opts, P_out=None, j_out=None, stream=None):
     _check(ctx, lib().heat_solve(ctx, ctypes.byref(opts), _ptr(P_out), _ptr(j_out), stream))
+
+
+def heat_autotune(ctx, opts: heat_opts, P_out=None, j_out=None, stream=None):
+    """Time (streams, chunk_cells) candidates on the current fields, keep the fastest for
+    later solves that leave both at 0; returns (streams, chunk_cells)."""
+    s, c = ctypes.c_int(), ctypes.c_int()
+    _check(ctx, lib().heat_autotune(ctx, ctypes.byref(opts), _ptr(P_out), _ptr(j_out), stream, ctypes.byref(s),
+                                    ctypes.byref(c)))
+    return s.value, c.value
 
 
 def heat_sync(ctx):

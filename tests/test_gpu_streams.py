@@ -1,0 +1,90 @@
+"""Chunk pipelining over internal streams: every (streams, chunk_cells) choice gives the
+same bits, host staging works across several chunks in flight, and the autotuner's pick
+is used by later default solves."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1311_4627_gb300 import heat
+from paper_1311_4627_gb300 import workloads as W
+
+from .gpu_helpers import Lib, masked_relerr
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wl_lib():
+    """200 cells (ragged against 32 and against every chunk size below) x 6 grains."""
+    full = W.batched(cells=200)
+    wl = W.grain_subset(full, [0, 9, 22, 40, 55, 63])
+    lib = Lib(wl)
+    lib.set_fields(wl.u)
+    yield wl, lib
+    lib.close()
+
+
+CONFIGS = [(1, 0), (1, 64), (2, 32), (2, 96), (3, 64), (4, 32), (4, 128)]
+
+
+@pytest.mark.parametrize("build,emis", [(heat.HEAT_BUILD_F64, heat.HEAT_EMIS_F64),
+                                        (heat.HEAT_BUILD_F32, heat.HEAT_EMIS_BF16X3)])
+def test_streams_and_chunks_are_bitwise_identical(wl_lib, build, emis):
+    wl, lib = wl_lib
+    ref = lib.solve(build=build, emis=emis, j_dtype=heat.HEAT_F32, streams=1, chunk_cells=256)
+    for s, c in CONFIGS:
+        got = lib.solve(build=build, emis=emis, j_dtype=heat.HEAT_F32, streams=s, chunk_cells=c)
+        assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), (s, c)
+
+
+def test_size_integrated_across_streams(wl_lib):
+    wl, lib = wl_lib
+    a = lib.solve(want_P=False, build=heat.HEAT_BUILD_F32, emis=heat.HEAT_EMIS_BF16X3, j_dtype=heat.HEAT_F32,
+                  size_integrate=1, streams=1, chunk_cells=256)[1]
+    b = lib.solve(want_P=False, build=heat.HEAT_BUILD_F32, emis=heat.HEAT_EMIS_BF16X3, j_dtype=heat.HEAT_F32,
+                  size_integrate=1, streams=3, chunk_cells=64)[1]
+    assert np.array_equal(a, b)
+
+
+def test_host_io_with_chunks_in_flight(wl_lib):
+    import torch
+
+    wl, lib = wl_lib
+    Pd, jd = lib.solve(build=heat.HEAT_BUILD_F32, emis=heat.HEAT_EMIS_BF16X3, j_dtype=heat.HEAT_F32)
+    n = wl.n_cells
+    P = np.zeros((n, wl.total_bins))
+    j = np.zeros((n, wl.n_grains, wl.n_lambda), dtype=np.float32)
+    led = np.zeros((n, wl.n_grains, 2))
+    st = torch.cuda.current_stream().cuda_stream
+    heat.heat_solve(lib.ctx, heat.heat_default_opts(build=heat.HEAT_BUILD_F32, emis=heat.HEAT_EMIS_BF16X3,
+                                                    j_dtype=heat.HEAT_F32, host_io=1, streams=3, chunk_cells=32,
+                                                    ledger_out=led), P, j, st)
+    heat.heat_sync(lib.ctx)
+    assert np.array_equal(P, Pd) and np.array_equal(j.astype(np.float64), jd)
+    assert np.all(led[..., 0] > 0) and np.all(np.isfinite(led))
+
+
+def test_autotune_choice_is_used_and_exact(wl_lib):
+    import torch
+
+    wl, lib = wl_lib
+    st = torch.cuda.current_stream().cuda_stream
+    ref = lib.solve(build=heat.HEAT_BUILD_F32, emis=heat.HEAT_EMIS_BF16X3, j_dtype=heat.HEAT_F32, streams=1,
+                    chunk_cells=256)
+    j = torch.empty(wl.n_cells, wl.n_grains, wl.n_lambda, dtype=torch.float32, device="cuda")
+    s, c = heat.heat_autotune(lib.ctx, heat.heat_default_opts(build=heat.HEAT_BUILD_F32, emis=heat.HEAT_EMIS_BF16X3,
+                                                             j_dtype=heat.HEAT_F32), None, j, st)
+    heat.heat_sync(lib.ctx)
+    assert 1 <= s <= 4 and c > 0 and c % 32 == 0
+    got = lib.solve(build=heat.HEAT_BUILD_F32, emis=heat.HEAT_EMIS_BF16X3, j_dtype=heat.HEAT_F32)
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+
+
+def test_pipelined_mixed_path_against_oracle(wl_lib):
+    """Several chunks on three streams still meet the mixed-path bound against the oracle."""
+    wl, lib = wl_lib
+    sub = W.field_subset(wl, np.arange(40))
+    _, j_ref, _, _ = oracle.solve_batch(sub, oracle.grain_cooling(wl))
+    _, j = lib.solve(want_P=False, build=heat.HEAT_BUILD_F32, emis=heat.HEAT_EMIS_BF16X3, j_dtype=heat.HEAT_F64,
+                     cell_count=40, streams=3, chunk_cells=32)
+    assert masked_relerr(j, j_ref) <= 1e-3
