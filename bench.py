@@ -203,6 +203,59 @@ def workload_config(wl, path):
             "path": path}
 
 
+# ---------------------------------------------------------------------------- single-cell latency
+def single_cell_section(dev, stream):
+    """One cell x 8 carbonaceous grains x 128 bins x 256 wavelengths: microseconds per
+    heat_solve, launched eagerly and replayed from a CUDA graph, for the exact and the
+    mixed path (a latency-bound solve: the roofline does not apply)."""
+    import torch
+
+    from paper_1311_4627_gb300 import heat
+    from paper_1311_4627_gb300 import workloads as W
+
+    wl = W.single_cell()
+    ctx = heat.heat_create_grid(dev.index, wl.lam)
+    heat.heat_set_grains(ctx, wl.radius, wl.cabs, wl.bin_off, wl.T, wl.E, wl.size_weight)
+    s = torch.cuda.Stream(dev)
+    sh = s.cuda_stream
+    u = torch.from_numpy(wl.u).to(dev)
+    heat.heat_set_fields(ctx, 1, u, heat.HEAT_F64, 1, sh)
+    P = torch.empty(1, wl.total_bins, dtype=torch.float64, device=dev)
+    j = torch.empty(1, wl.n_grains, wl.n_lambda, dtype=torch.float32, device=dev)
+    out = {"workload": f"single cell x {wl.n_grains} grains, 128 bins, {wl.n_lambda} wavelengths", "paths": {}}
+    reps = 200
+    for name, b, e in (("exact", heat.HEAT_BUILD_F64, heat.HEAT_EMIS_F64),
+                       ("mixed", heat.HEAT_BUILD_F32, heat.HEAT_EMIS_BF16X3)):
+        o = heat.heat_default_opts(build=b, emis=e, j_dtype=heat.HEAT_F32)
+        for _ in range(5):
+            heat.heat_solve(ctx, o, P, j, sh)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(reps):
+            heat.heat_solve(ctx, o, P, j, sh)
+        e1.record(s)
+        torch.cuda.synchronize(dev)
+        eager_us = e0.elapsed_time(e1) * 1e3 / reps
+        g = heat.Graph(ctx, o, P, j, sh)
+        for _ in range(5):
+            g.launch(sh)
+        torch.cuda.synchronize(dev)
+        e0.record(s)
+        for _ in range(reps):
+            g.launch(sh)
+        e1.record(s)
+        torch.cuda.synchronize(dev)
+        graph_us = e0.elapsed_time(e1) * 1e3 / reps
+        out["paths"][name] = {"eager_us_per_solve": eager_us, "graph_us_per_solve": graph_us,
+                              "graph_kernel_nodes": g.kernel_nodes(),
+                              "spectra_per_s_graph": wl.n_grains / (graph_us * 1e-6)}
+        g.close()
+    heat.heat_sync(ctx)
+    heat.heat_destroy(ctx)
+    return out
+
+
 # ---------------------------------------------------------------------------- emissivity-heavy workload
 def emissivity_heavy_section(args, dev, stream, peaks, peaks_src):
     """65536 cells x 32 carbonaceous grains x 512 bins x 2048 wavelengths, per-grain FP32
@@ -559,6 +612,8 @@ def main():
                 "j_masked_1e-6_peak": float(np.max(np.abs(sur_j[mj] - j_ref[mj]) / j_ref[mj])),
                 "sample": f"{nsub} cells x {G} grains vs the FP64 oracle"}
     line["paths"] = paths
+    if rank == 0 and ws == 1:
+        line["single_cell"] = single_cell_section(dev, stream)
     if rank == 0 and ws == 1 and not args.no_emis_heavy:
         del j
         torch.cuda.empty_cache()

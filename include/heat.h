@@ -157,6 +157,28 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
 heat_status heat_autotune(heat_ctx* ctx, const heat_opts* opts, double* P_out, void* j_out, void* cuda_stream,
                           int* streams_out, int* chunk_out);
 
+/* ---- CUDA graphs ----------------------------------------------------------------------
+ * A solve captured once and replayed: the launch cost of a solve's kernels (field, build,
+ * recursion, packing, emissivity per chunk) is paid once, which matters for small solves
+ * (a single cell's grains) and for solves repeated over changing fields (an iterative
+ * radiative-transfer loop that updates u in place).
+ * heat_graph_create runs heat_solve(ctx, opts, P_out, j_out) once on cuda_stream (so that
+ * every allocation, upload and internal stream exists), waits for it, then captures the
+ * same solve into a graph.  The graph is bound to the buffers of that call: P_out, j_out,
+ * the fields pointer current at capture (heat_set_fields with on_device = 1: its contents
+ * may change between launches, the pointer may not) and the ctx's scratch.  A later
+ * heat_solve on the ctx with another configuration may reallocate that scratch: destroy
+ * and recreate the graph after one.  opts->timing and opts->host_io are not allowed.
+ * Errors: HEAT_EINVAL, HEAT_ESTATE, HEAT_ENOMEM, HEAT_ECUDA (capture refused). */
+typedef struct heat_graph heat_graph;
+heat_status heat_graph_create(heat_ctx* ctx, const heat_opts* opts, double* P_out, void* j_out, void* cuda_stream,
+                              heat_graph** out);
+/* Replay the captured solve on cuda_stream (asynchronous; errors surface at heat_sync). */
+heat_status heat_graph_launch(heat_graph* graph, void* cuda_stream);
+/* Kernel nodes in the graph (the solve's launches). */
+heat_status heat_graph_nodes(const heat_graph* graph, long long* kernel_nodes);
+void heat_graph_destroy(heat_graph* graph);
+
 /* Wait for all work of the ctx's last calls and return the device status:
  * HEAT_OK, HEAT_ENUMERIC, HEAT_EINVAL (bad field values) or HEAT_ECUDA.  Clears the status. */
 heat_status heat_sync(heat_ctx* ctx);

@@ -813,6 +813,88 @@ heat_status heat_autotune(heat_ctx* ctx, const heat_opts* opts, double* P_out, v
     return HEAT_OK;
 }
 
+struct heat_graph {
+    heat_ctx* ctx = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;
+};
+
+heat_status heat_graph_create(heat_ctx* ctx, const heat_opts* opts, double* P_out, void* j_out, void* stream,
+                              heat_graph** out) {
+    if (!out) return HEAT_EINVAL;
+    *out = nullptr;
+    if (!ctx || !opts) return HEAT_EINVAL;
+    if (opts->timing || opts->host_io) return ctx->fail(HEAT_EINVAL, "heat_graph_create: timing and host_io not allowed");
+    CKR(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (st == nullptr) return ctx->fail(HEAT_EINVAL, "heat_graph_create: capture needs a non-default stream");
+    heat_status h = heat_solve(ctx, opts, P_out, j_out, stream);  // allocations, uploads, streams
+    if (h != HEAT_OK) return h;
+    CKR(cudaStreamSynchronize(st));
+    CKR(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    h = heat_solve(ctx, opts, P_out, j_out, stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (h != HEAT_OK) {
+        if (g) cudaGraphDestroy(g);
+        return h;
+    }
+    if (e != cudaSuccess) return ctx->cuda_fail(e, "heat_graph_create: capture");
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return ctx->cuda_fail(e, "heat_graph_create: instantiate");
+    }
+    size_t n = 0;
+    CKR(cudaGraphGetNodes(g, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    long long kernels = 0;
+    if (n) {
+        CKR(cudaGraphGetNodes(g, nodes.data(), &n));
+        for (auto nd : nodes) {
+            cudaGraphNodeType t;
+            CKR(cudaGraphNodeGetType(nd, &t));
+            kernels += t == cudaGraphNodeTypeKernel;
+        }
+    }
+    heat_graph* gr = new (std::nothrow) heat_graph();
+    if (!gr) {
+        cudaGraphExecDestroy(x);
+        cudaGraphDestroy(g);
+        return HEAT_ENOMEM;
+    }
+    gr->ctx = ctx;
+    gr->graph = g;
+    gr->exec = x;
+    gr->kernels = kernels;
+    *out = gr;
+    return HEAT_OK;
+}
+
+heat_status heat_graph_launch(heat_graph* gr, void* stream) {
+    if (!gr || !gr->exec) return HEAT_EINVAL;
+    heat_ctx* ctx = gr->ctx;
+    CKR(cudaSetDevice(ctx->device));
+    cudaError_t e = cudaGraphLaunch(gr->exec, (cudaStream_t)stream);
+    return e == cudaSuccess ? HEAT_OK : ctx->cuda_fail(e, "heat_graph_launch");
+}
+
+heat_status heat_graph_nodes(const heat_graph* gr, long long* kernel_nodes) {
+    if (!gr || !kernel_nodes) return HEAT_EINVAL;
+    *kernel_nodes = gr->kernels;
+    return HEAT_OK;
+}
+
+void heat_graph_destroy(heat_graph* gr) {
+    if (!gr) return;
+    cudaSetDevice(gr->ctx->device);
+    if (gr->exec) cudaGraphExecDestroy(gr->exec);
+    if (gr->graph) cudaGraphDestroy(gr->graph);
+    delete gr;
+}
+
 heat_status heat_sync(heat_ctx* ctx) {
     if (!ctx) return HEAT_EINVAL;
     CKR(cudaSetDevice(ctx->device));

@@ -247,15 +247,23 @@ cudaError_t launch_emis_tc(const EmisTcParams& p, bool tf32, int sms, cudaStream
     if (total <= 0) return cudaSuccess;
     size_t smem = emis_tc_smem_bytes();
     int grid = total < sms ? total : sms;
-    if (tf32) {
-        cudaError_t e = cudaFuncSetAttribute(k_emis_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the shared-memory opt-in is set once per device (not a stream operation, but kept out
+    // of the launch path so that a solve can be captured into a CUDA graph)
+    static bool attr_set[2][64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr_set[tf32][dev]) {
+        e = tf32 ? cudaFuncSetAttribute(k_emis_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                 : cudaFuncSetAttribute(k_emis_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_emis_tc<true><<<grid, 192, smem, st>>>(p);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(k_emis_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_emis_tc<false><<<grid, 192, smem, st>>>(p);
+        attr_set[tf32][dev] = true;
     }
+    if (tf32)
+        k_emis_tc<true><<<grid, 192, smem, st>>>(p);
+    else
+        k_emis_tc<false><<<grid, 192, smem, st>>>(p);
     return cudaGetLastError();
 }
 

@@ -78,6 +78,14 @@ def lib():
         L.heat_get_cooling.argtypes = [_vp, _vp]
         L.heat_band_elements.restype = ctypes.c_int
         L.heat_band_elements.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong)]
+        L.heat_graph_create.restype = ctypes.c_int
+        L.heat_graph_create.argtypes = [_vp, ctypes.POINTER(heat_opts), _vp, _vp, _vp, ctypes.POINTER(_vp)]
+        L.heat_graph_launch.restype = ctypes.c_int
+        L.heat_graph_launch.argtypes = [_vp, _vp]
+        L.heat_graph_nodes.restype = ctypes.c_int
+        L.heat_graph_nodes.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong)]
+        L.heat_graph_destroy.restype = None
+        L.heat_graph_destroy.argtypes = [_vp]
         L.heat_autotune.restype = ctypes.c_int
         L.heat_autotune.argtypes = [_vp, ctypes.POINTER(heat_opts), _vp, _vp, _vp, ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int)]
@@ -168,6 +176,35 @@ def heat_set_fields(ctx, n_cells, u, dtype, on_device, stream=None):
 
 def heat_solve(ctx, opts: heat_opts, P_out=None, j_out=None, stream=None):
     _check(ctx, lib().heat_solve(ctx, ctypes.byref(opts), _ptr(P_out), _ptr(j_out), stream))
+
+
+class Graph:
+    """A heat_solve captured into a CUDA graph (heat_graph_create); launch() replays it."""
+
+    def __init__(self, ctx, opts: heat_opts, P_out=None, j_out=None, stream=None):
+        h = _vp()
+        _check(ctx, lib().heat_graph_create(ctx, ctypes.byref(opts), _ptr(P_out), _ptr(j_out), stream,
+                                            ctypes.byref(h)))
+        self.ctx, self.handle = ctx, h
+
+    def launch(self, stream=None):
+        _check(self.ctx, lib().heat_graph_launch(self.handle, stream))
+
+    def kernel_nodes(self) -> int:
+        v = ctypes.c_longlong()
+        _check(self.ctx, lib().heat_graph_nodes(self.handle, ctypes.byref(v)))
+        return v.value
+
+    def close(self):
+        if self.handle:
+            lib().heat_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def heat_autotune(ctx, opts: heat_opts, P_out=None, j_out=None, stream=None):
