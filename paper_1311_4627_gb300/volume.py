@@ -1,0 +1,240 @@
+"""Radiative-transfer volume run: every cell of a volume solved chunk by chunk through the
+C ABI (mixed path, size-integrated emissivity J_c = sum_g w_g j_{c,g}, Eq. convolution),
+an energy check per chunk, and a checkpoint manifest so that an interrupted run resumes
+where it stopped.
+
+The manifest (``manifest.json`` in the output directory) records the run's configuration
+and, per finished chunk, its output file, the file's SHA-256, the cell range and the
+energy check.  A resumed run must have the same configuration; a chunk whose file is
+missing or whose checksum does not match is computed again.  The manifest is replaced
+atomically (written to a temporary file, then renamed).
+
+    python -m paper_1311_4627_gb300.volume --out DIR [--shape 128 128 64] [--chunk 65536]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import tempfile
+import time
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+MANIFEST = "manifest.json"
+
+
+def sha256_file(path: str) -> str:
+    h = hashlib.sha256()
+    with open(path, "rb") as f:
+        for block in iter(lambda: f.read(1 << 22), b""):
+            h.update(block)
+    return h.hexdigest()
+
+
+def energy_summary(ledger: np.ndarray, weights: np.ndarray) -> dict:
+    """Energy check of one chunk from the solve's ledger [cells][grains][2] (absorbed power on
+    the grid, emitted power of the discrete model, erg/s per grain): the spread of the
+    per-spectrum ratio emitted / absorbed and the size-weighted totals."""
+    absorbed, emitted = ledger[..., 0], ledger[..., 1]
+    ok = absorbed > 0
+    r = emitted[ok] / absorbed[ok]
+    tot_a = float(np.sum(absorbed * weights[None, :]))
+    tot_e = float(np.sum(emitted * weights[None, :]))
+    return {"spectra": int(ok.sum()), "ratio_min": float(r.min()) if r.size else None,
+            "ratio_median": float(np.median(r)) if r.size else None, "ratio_max": float(r.max()) if r.size else None,
+            "weighted_absorbed": tot_a, "weighted_emitted": tot_e,
+            "weighted_ratio": tot_e / tot_a if tot_a > 0 else None}
+
+
+class ChunkManifest:
+    """Checkpoint state of a chunked run (host logic only)."""
+
+    def __init__(self, out_dir: str, config: dict):
+        self.out_dir = out_dir
+        self.config = config
+        self.path = os.path.join(out_dir, MANIFEST)
+        self.chunks: dict[str, dict] = {}
+
+    def load(self, resume: bool) -> None:
+        os.makedirs(self.out_dir, exist_ok=True)
+        if not resume or not os.path.exists(self.path):
+            self.chunks = {}
+            self.save()
+            return
+        with open(self.path) as f:
+            m = json.load(f)
+        if m.get("config") != self.config:
+            raise ValueError(f"{self.path}: written by a run with another configuration")
+        self.chunks = m.get("chunks", {})
+
+    def save(self) -> None:
+        fd, tmp = tempfile.mkstemp(dir=self.out_dir, prefix=".manifest.", suffix=".tmp")
+        with os.fdopen(fd, "w") as f:
+            json.dump({"version": 1, "config": self.config, "chunks": self.chunks}, f, indent=1, sort_keys=True)
+            f.flush()
+            os.fsync(f.fileno())
+        os.replace(tmp, self.path)
+
+    def done(self, k: int) -> bool:
+        """Chunk k finished and its file intact."""
+        e = self.chunks.get(str(k))
+        if not e:
+            return False
+        p = os.path.join(self.out_dir, e["file"])
+        return os.path.exists(p) and sha256_file(p) == e["sha256"]
+
+    def record(self, k: int, fname: str, info: dict) -> None:
+        p = os.path.join(self.out_dir, fname)
+        self.chunks[str(k)] = dict(info, file=fname, sha256=sha256_file(p))
+        self.save()
+
+
+def run_chunks(manifest: ChunkManifest, n_cells: int, chunk: int, solve_chunk, resume: bool = True,
+               stop_after: int | None = None, prepare=None, log=None) -> dict:
+    """Drive the chunks of [0, n_cells): skip the finished ones, solve the others with
+    solve_chunk(k, begin, end, prepared) -> (J float32 [cells][n_lambda], info dict), write
+    J_k.npy and record it.  prepare(begin, end), if given, runs one chunk ahead in a host
+    thread (e.g. making the next chunk's fields while the GPU works).  stop_after: return
+    after that many chunks were solved in this call (an interrupted run)."""
+    manifest.load(resume)
+    todo = [k for k in range((n_cells + chunk - 1) // chunk) if not manifest.done(k)]
+    solved = 0
+    with ThreadPoolExecutor(1) as pool:
+        nxt = None
+        if prepare and todo:
+            b = todo[0] * chunk
+            nxt = pool.submit(prepare, b, min(n_cells, b + chunk))
+        for i, k in enumerate(todo):
+            if stop_after is not None and solved >= stop_after:
+                break
+            b, e = k * chunk, min(n_cells, (k + 1) * chunk)
+            prepared = nxt.result() if nxt is not None else None
+            nxt = None
+            if prepare and i + 1 < len(todo):
+                b2 = todo[i + 1] * chunk
+                nxt = pool.submit(prepare, b2, min(n_cells, b2 + chunk))
+            J, info = solve_chunk(k, b, e, prepared)
+            fname = f"J_{k:05d}.npy"
+            np.save(os.path.join(manifest.out_dir, fname), np.ascontiguousarray(J, dtype=np.float32))
+            manifest.record(k, fname, dict(info, cells=[b, e]))
+            solved += 1
+            if log:
+                log(f"chunk {k}: cells [{b}, {e}) {json.dumps(info)}")
+    n_chunks = (n_cells + chunk - 1) // chunk
+    return {"chunks": n_chunks, "solved_now": solved,
+            "complete": all(manifest.done(k) for k in range(n_chunks))}
+
+
+def load_output(manifest_dir: str) -> np.ndarray:
+    """The volume's J [cells][n_lambda] assembled from the chunk files."""
+    with open(os.path.join(manifest_dir, MANIFEST)) as f:
+        m = json.load(f)
+    parts = sorted(m["chunks"].values(), key=lambda e: e["cells"][0])
+    return np.concatenate([np.load(os.path.join(manifest_dir, e["file"])) for e in parts])
+
+
+class VolumeSolver:
+    """GPU side of a volume run: one ctx with the volume's grains; per chunk the fields are
+    copied from pinned host memory, solved on the mixed path with size-integrated output
+    and the energy ledger, and J is read back."""
+
+    def __init__(self, vol, chunk: int, device: int = 0, emis: str = "bf16x3"):
+        import torch
+
+        from . import heat
+
+        self.torch, self.heat, self.vol = torch, heat, vol
+        g = vol.grains
+        self.dev = torch.device(f"cuda:{device}")
+        torch.cuda.set_device(self.dev)
+        self.stream = torch.cuda.Stream(self.dev)
+        self.ctx = heat.heat_create_grid(device, g.lam)
+        heat.heat_set_grains(self.ctx, g.radius, g.cabs, g.bin_off, g.T, g.E, g.size_weight)
+        self.emis = {"bf16x3": heat.HEAT_EMIS_BF16X3, "tf32x3": heat.HEAT_EMIS_TF32X3}[emis]
+        N, G = g.n_lambda, g.n_grains
+        self.u_dev = torch.empty(chunk, N, dtype=torch.float64, device=self.dev)
+        self.J_dev = torch.empty(chunk, N, dtype=torch.float32, device=self.dev)
+        self.led_dev = torch.empty(chunk, G, 2, dtype=torch.float64, device=self.dev)
+        self.u_pin = torch.empty(chunk, N, dtype=torch.float64).pin_memory()
+        self.J_pin = torch.empty(chunk, N, dtype=torch.float32).pin_memory()
+        self.led_pin = torch.empty(chunk, G, 2, dtype=torch.float64).pin_memory()
+
+    def prepare(self, begin: int, end: int) -> np.ndarray:
+        return self.vol.fields(begin, end)
+
+    def solve_chunk(self, k: int, begin: int, end: int, u: np.ndarray | None):
+        torch, heat = self.torch, self.heat
+        n = end - begin
+        if u is None:
+            u = self.prepare(begin, end)
+        sh = self.stream.cuda_stream
+        t0 = time.perf_counter()
+        self.u_pin[:n].copy_(torch.from_numpy(u))
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        with torch.cuda.stream(self.stream):
+            ev[0].record(self.stream)
+            self.u_dev[:n].copy_(self.u_pin[:n], non_blocking=True)
+            heat.heat_set_fields(self.ctx, n, self.u_dev, heat.HEAT_F64, 1, sh)
+            o = heat.heat_default_opts(build=heat.HEAT_BUILD_F32, emis=self.emis, j_dtype=heat.HEAT_F32,
+                                       size_integrate=1, cell_count=n, ledger_out=self.led_dev)
+            heat.heat_solve(self.ctx, o, None, self.J_dev, sh)
+            self.J_pin[:n].copy_(self.J_dev[:n], non_blocking=True)
+            self.led_pin[:n].copy_(self.led_dev[:n], non_blocking=True)
+            ev[1].record(self.stream)
+        self.stream.synchronize()
+        heat.heat_sync(self.ctx)
+        gpu_ms = ev[0].elapsed_time(ev[1])
+        J = self.J_pin[:n].numpy().copy()
+        info = {"gpu_ms": round(gpu_ms, 3), "wall_s": round(time.perf_counter() - t0, 3),
+                "spectra": n * self.vol.grains.n_grains,
+                "energy": energy_summary(self.led_pin[:n].numpy(), self.vol.grains.size_weight)}
+        return J, info
+
+    def close(self):
+        self.heat.heat_destroy(self.ctx)
+
+
+def volume_config(vol, chunk: int, emis: str) -> dict:
+    g = vol.grains
+    return {"shape": list(vol.shape), "seed": vol.seed, "grains": g.n_grains, "bins": int(g.total_bins),
+            "n_lambda": g.n_lambda, "chunk_cells": chunk, "path": f"mixed ({emis}), size-integrated"}
+
+
+def main(argv=None):
+    from . import workloads as W
+
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--out", required=True)
+    ap.add_argument("--shape", type=int, nargs=3, default=[128, 128, 64])
+    ap.add_argument("--chunk", type=int, default=65536)
+    ap.add_argument("--radii", type=int, default=40, help="radii per composition")
+    ap.add_argument("--bins", type=int, default=512)
+    ap.add_argument("--n-lambda", type=int, default=1024)
+    ap.add_argument("--emis", default="bf16x3", choices=["bf16x3", "tf32x3"])
+    ap.add_argument("--no-resume", action="store_true")
+    ap.add_argument("--stop-after", type=int, default=None)
+    args = ap.parse_args(argv)
+    t0 = time.perf_counter()
+    vol = W.rt_volume(tuple(args.shape), radii_per_composition=args.radii, nbins=args.bins, n_lambda=args.n_lambda)
+    solver = VolumeSolver(vol, args.chunk, emis=args.emis)
+    man = ChunkManifest(args.out, volume_config(vol, args.chunk, args.emis))
+    res = run_chunks(man, vol.n_cells, args.chunk, solver.solve_chunk, resume=not args.no_resume,
+                     stop_after=args.stop_after, prepare=solver.prepare, log=print)
+    solver.close()
+    ch = [man.chunks[k] for k in sorted(man.chunks, key=int)]
+    gpu_s = sum(c["gpu_ms"] for c in ch) / 1e3
+    spectra = sum(c["spectra"] for c in ch)
+    ratios = [c["energy"]["weighted_ratio"] for c in ch if c["energy"]["weighted_ratio"] is not None]
+    res.update({"cells": vol.n_cells, "spectra": spectra, "gpu_s": round(gpu_s, 3),
+                "spectra_per_s_gpu": spectra / gpu_s if gpu_s > 0 else None,
+                "wall_s": round(time.perf_counter() - t0, 2),
+                "energy_weighted_ratio_range": [min(ratios), max(ratios)] if ratios else None,
+                "config": man.config})
+    print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

@@ -247,3 +247,64 @@ def grain_subset(wl: Workload, grains) -> Workload:
     E = np.concatenate([wl.E[wl.grain_slice(g)] for g in grains])
     return Workload(wl.name + f" [grains {grains}]", wl.lam, wl.radius[grains], [wl.composition[g] for g in grains],
                     wl.cabs[grains], off, T, E, wl.size_weight[grains], u=wl.u, chi=wl.chi, hardness=wl.hardness)
+
+
+# ---------------------------------------------------------------------------- volume
+def gaussian_random_field(shape, corr_cells: float, rng: np.random.Generator) -> np.ndarray:
+    """Periodic Gaussian random field on a grid: white noise smoothed by a Gaussian kernel of
+    standard deviation corr_cells (in cells), through the FFT; normalised to zero mean and
+    unit variance.  Its autocorrelation at separation r is exp(-r^2 / (4 corr_cells^2))."""
+    noise = rng.standard_normal(shape)
+    k2 = np.zeros(shape)
+    for ax, n in enumerate(shape):
+        k = 2.0 * math.pi * np.fft.fftfreq(n)
+        sh = [1] * len(shape)
+        sh[ax] = n
+        k2 = k2 + (k**2).reshape(sh)
+    f = np.fft.ifftn(np.fft.fftn(noise) * np.exp(-0.5 * k2 * corr_cells**2)).real
+    return (f - f.mean()) / f.std()
+
+
+@dataclasses.dataclass
+class Volume:
+    """A radiative-transfer volume: grains, and per cell the field parameters (chi, hardness,
+    blackbody weights) from which u is made chunk by chunk (u of the whole volume is
+    n_cells x n_lambda FP64, too large to keep)."""
+    grains: Workload  # grid and grains (no fields)
+    shape: tuple
+    chi: np.ndarray  # [cells]
+    hardness: np.ndarray  # [cells]
+    wts: np.ndarray  # [cells, 3]
+    seed: int
+
+    @property
+    def n_cells(self) -> int:
+        return int(self.chi.size)
+
+    def fields(self, begin: int, end: int) -> np.ndarray:
+        """u of cells [begin, end) (x-fastest order of the grid)."""
+        return three_bb_fields(self.grains.lam, self.chi[begin:end], self.hardness[begin:end],
+                               self.wts[begin:end])
+
+
+def rt_volume(shape=(128, 128, 64), corr_cells: float = 8.0, radii_per_composition: int = 40, nbins: int = 512,
+              n_lambda: int = 1024, seed: int = 1005) -> Volume:
+    """Gaussian-random-field volume: log10 chi a GRF of mean 0 and standard deviation 1.5,
+    hardness a GRF of standard deviation 0.5 clipped to [-1, 1] (correlation length
+    corr_cells), blackbody weights 10^U(-2, 0); grains: carbonaceous and silicate at
+    radii_per_composition radii (3.5 A - 1 um), nbins bins each, n_lambda wavelengths."""
+    lam = wavelength_grid(n_lambda)
+    radii = np.geomspace(3.5e-8, 1e-4, radii_per_composition)
+    rs = np.concatenate([radii, radii])
+    comps = ["carbonaceous"] * radii_per_composition + ["silicate"] * radii_per_composition
+    grains = _workload(f"volume {shape} x {2 * radii_per_composition} grains x {nbins} bins x {n_lambda} wavelengths",
+                       lam, rs, comps, [nbins] * rs.size, 0, seed, 1.0, 1.0, 0.0, 0.0, fields=False)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    g1 = gaussian_random_field(shape, corr_cells, rng)
+    g2 = gaussian_random_field(shape, corr_cells, rng)
+    cells = int(np.prod(shape))
+    # x-fastest cell order: cell index = x + nx (y + ny z)
+    chi = 10.0 ** (1.5 * g1.transpose().reshape(cells))
+    hard = np.clip(0.5 * g2.transpose().reshape(cells), -1.0, 1.0)
+    wts = 10.0 ** rng.uniform(-2.0, 0.0, (cells, 3))
+    return Volume(grains, tuple(shape), chi, hard, wts, seed)
