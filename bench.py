@@ -416,9 +416,9 @@ def main():
     ms, step_ms, kt, clocks, wall = timed_run(args.path, args.steps, args.warmup, sample_clocks=True)
     total_ms = float(np.sum(step_ms))
     if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+        from paper_1311_4627_gb300 import shard
+
+        total_ms = shard.max_over_ranks(total_ms)
     value = ws * cells * G * args.steps / (total_ms / 1e3)
     gpu_launches = int(sum(n for _, n in kt.values()))
 

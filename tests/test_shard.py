@@ -1,0 +1,68 @@
+"""Sharding over ranks, on CPU with the gloo backend (world size 2): the ranges cover the
+cells exactly once, and spectra computed per rank (by the oracle) and gathered equal the
+single-process result bit for bit."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+from paper_1311_4627_gb300 import shard
+
+
+def test_ranges_partition_the_cells():
+    for n in (1, 31, 32, 33, 100, 4096, 4097):
+        for world in (1, 2, 3, 8):
+            rs = [shard.cell_range(r, world, n) for r in range(world)]
+            assert rs[0][0] == 0 and rs[-1][1] == n
+            for (b0, e0), (b1, e1) in zip(rs, rs[1:]):
+                assert e0 == b1
+            for b, e in rs[:-1]:
+                assert b % 32 == 0 and e % 32 == 0 or e == n
+    with pytest.raises(ValueError):
+        shard.cell_range(2, 2, 10)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out_dir):
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    from paper_1311_4627_gb300 import workloads as W
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    full = W.batched(cells=70, n_lambda=128)
+    wl = W.grain_subset(full, [0, 40])
+    b, e = shard.cell_range(rank, world, wl.n_cells)
+    _, j, _, st = oracle.solve_batch(W.field_subset(wl, np.arange(b, e)), oracle.grain_cooling(wl), n_threads=1)
+    assert st == oracle.OK
+    J = torch.from_numpy(oracle.size_integrate(wl.size_weight, j))
+    t = shard.max_over_ranks(float(rank + 1))
+    got = shard.gather_rows(J, wl.n_cells)
+    if rank == 0:
+        np.save(os.path.join(out_dir, "gathered.npy"), got.numpy())
+        np.save(os.path.join(out_dir, "tmax.npy"), np.array([t]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_gather_equals_one_process(tmp_path):
+    import oracle
+    from paper_1311_4627_gb300 import workloads as W
+
+    mp.spawn(_worker, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
+    full = W.batched(cells=70, n_lambda=128)
+    wl = W.grain_subset(full, [0, 40])
+    _, j, _, _ = oracle.solve_batch(wl, oracle.grain_cooling(wl), n_threads=1)
+    ref = oracle.size_integrate(wl.size_weight, j)
+    got = np.load(os.path.join(tmp_path, "gathered.npy"))
+    assert np.array_equal(got, ref)
+    assert float(np.load(os.path.join(tmp_path, "tmax.npy"))[0]) == 2.0
