@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--sur-epochs", type=int, default=30)
     ap.add_argument("--sur-tol", type=float, default=1e-2, help="ensemble spread (ln j) above which a cell falls back")
     ap.add_argument("--oracle-cells", type=int, default=24, help="cells in the oracle sample")
+    ap.add_argument("--no-single-cell", action="store_true", help="skip the single-cell latency section")
     ap.add_argument("--no-emis-heavy", action="store_true",
                     help="skip the emissivity-heavy workload (65536 cells x 32 grains x 512 bins x 2048 wavelengths)")
     ap.add_argument("--emis-heavy-oracle-cells", type=int, default=64,
@@ -612,7 +613,7 @@ def main():
                 "j_masked_1e-6_peak": float(np.max(np.abs(sur_j[mj] - j_ref[mj]) / j_ref[mj])),
                 "sample": f"{nsub} cells x {G} grains vs the FP64 oracle"}
     line["paths"] = paths
-    if rank == 0 and ws == 1:
+    if rank == 0 and ws == 1 and not args.no_single_cell:
         line["single_cell"] = single_cell_section(dev, stream)
     if rank == 0 and ws == 1 and not args.no_emis_heavy:
         del j

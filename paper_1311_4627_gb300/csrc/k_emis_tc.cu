@@ -300,8 +300,24 @@ __device__ __forceinline__ int scale_exp(double m) {
     return e;
 }
 
+// P * 2^-e rounded to FP32 (to nearest even) with integer operations only: P >= 0 is an
+// FP64 value and e its row's scale exponent; results below the FP32 normal range flush
+// to 0.  The FP64 pipe (one warp-wide instruction per 64 cycles on this part) stays out
+// of the packing, which is then bound by its memory traffic.
+__device__ __forceinline__ float scaled_to_f32(double p, int e) {
+    const unsigned hi = (unsigned)__double2hiint(p), lo = (unsigned)__double2loint(p);
+    const int fe = (int)(hi >> 20) - e - 896;  // FP32 biased exponent of p * 2^-e
+    if (fe <= 0) return 0.0f;
+    const unsigned m23 = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1FFFFFFFu;
+    unsigned fb = ((unsigned)fe << 23) | m23;
+    fb += (rest > 0x10000000u || (rest == 0x10000000u && (m23 & 1u))) ? 1u : 0u;
+    return __uint_as_float(fb);
+}
+
 // A' for one chunk: one warp per (cell, grain).  P [cells][nbt] FP64 in, per grain
-// A'_g [cells][Kp_g] (BF16 or TF32-in-FP32) out, and rowscale [cells][G] = 2^e.
+// A'_g [cells][Kp_g] (BF16 or TF32-in-FP32) out, and rowscale [cells][G] = 2^e with e
+// the smallest exponent for which the row's largest P divided by 2^e is below 1.
 __global__ void k_pack_p(int cells, int G, const int* __restrict__ bin_off, const double* __restrict__ P,
                          long long ldP, const long long* __restrict__ aoff, const int* __restrict__ kp, int split,
                          int tf32, void* __restrict__ A, float* __restrict__ rowscale) {
@@ -311,34 +327,35 @@ __global__ void k_pack_p(int cells, int G, const int* __restrict__ bin_off, cons
     int c = (int)(w / G), g = (int)(w % G);
     int off = bin_off[g], nb = bin_off[g + 1] - off;
     const double* pr = P + (size_t)c * ldP + off;
-    double m = 0.0;
-    for (int i = lane; i < nb; i += 32) m = fmax(m, pr[i]);
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    int e = scale_exp(m);
-    double inv = ldexp(1.0, -e);
+    // the largest high word has the largest exponent (P >= 0: bit patterns order as values)
+    unsigned mh = 0;
+    for (int i = lane; i < nb; i += 32) mh = max(mh, (unsigned)__double2hiint(pr[i]));
+    mh = __reduce_max_sync(0xffffffffu, mh);
+    // frexp exponent of the maximum: m = f 2^e, f in [0.5, 1); 0 for an all-zero row
+    const int e = mh >= 0x00100000u ? (int)(mh >> 20) - 1022 : 0;
     if (lane == 0) rowscale[(size_t)c * G + g] = ldexpf(1.0f, e);
     int K = kp[g];
     if (tf32) {
         float* row = (float*)A + aoff[g] + (size_t)c * K;
         for (int i = lane; i < nb; i += 32) {
-            float hi, lo;
-            split_tf32(pr[i] * inv, hi, lo);
+            const float v = scaled_to_f32(pr[i], e);
+            const float hi = tf32_rn(v);
             row[i] = hi;
             if (split) {
                 row[nb + i] = hi;
-                row[2 * nb + i] = lo;
+                row[2 * nb + i] = tf32_rn(v - hi);
             }
         }
         for (int i = (split ? 3 : 1) * nb + lane; i < K; i += 32) row[i] = 0.0f;
     } else {
         uint16_t* row = (uint16_t*)A + aoff[g] + (size_t)c * K;
         for (int i = lane; i < nb; i += 32) {
-            uint16_t hi, lo;
-            split_bf16(pr[i] * inv, hi, lo);
+            const float v = scaled_to_f32(pr[i], e);
+            const uint16_t hi = bf16_rn(v);
             row[i] = hi;
             if (split) {
                 row[nb + i] = hi;
-                row[2 * nb + i] = lo;
+                row[2 * nb + i] = bf16_rn(v - bf16_f(hi));
             }
         }
         for (int i = (split ? 3 : 1) * nb + lane; i < K; i += 32) row[i] = 0;
