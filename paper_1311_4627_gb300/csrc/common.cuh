@@ -23,7 +23,7 @@ constexpr double kRescaleSmall = 0x1p-800;
 // the segments in order and fills every element whose transition wavelength
 // hc/(Elo_f - E_j) lies in the current one).  e is the element's index in the band
 // storage (row-major over f, then j); t = ln(lambda_fj / lambda_n), 0 past the last node.
-struct PatF64 {
+struct __align__(16) PatF64 {
     int e;
     int pad;
     double t;
@@ -32,7 +32,7 @@ struct PatF64 {
 // FP32 build: with a_n = u_n ca_n and z = (su_n + sC_n + 2) t,
 //   B = Phi_n + u_n cat E1(fma(su_n, t, zt)),   cat = ca_n t,  zt = (sC_n + 2) t,
 // where ca_n = C_n lambda_n^2 / h (0 on an inactive C segment).
-struct PatF32 {
+struct __align__(16) PatF32 {  // one 128-bit load
     int e;
     float t;
     float cat;
