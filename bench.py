@@ -134,6 +134,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def recorded_traffic(kernel, cells, launches_per_step):
+    """DRAM bytes per launch of `kernel` from the committed ncu record (profiles/traffic.json),
+    or None when there is none for this kernel and size or the kernel's source changed since."""
+    import hashlib
+
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    name = {"recur": "k_recur"}.get(kernel)
+    if not name or not os.path.exists(p) or cells != 4096 or launches_per_step != 1:
+        return None
+    with open(p) as f:
+        rec = json.load(f).get(name)
+    if not rec:
+        return None
+    with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest()[:16] != rec["source_sha256_prefix"]:
+            return None
+    return rec["bytes_per_launch_4096_cells"]
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -458,6 +477,7 @@ def main():
         rooflines[name] = r
     dom = max(rooflines, key=lambda k: kt[k][0])
     roofline = dict(rooflines[dom])
+    roofline["traffic"] = recorded_traffic(dom, cells, kt[dom][1] / args.steps)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
