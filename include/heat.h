@@ -150,10 +150,12 @@ heat_status heat_set_fields(heat_ctx* ctx, int n_cells, const void* u_lambda, in
 heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void* j_out, void* cuda_stream);
 
 /* Time heat_solve on cells [opts->cell_begin, +opts->cell_count) of the current fields for
- * a set of (streams, chunk_cells) pairs and keep the fastest: later solves whose opts leave
- * both at 0 use it.  *streams_out / *chunk_out (or NULL) receive the choice.  Runs the
- * candidates on cuda_stream and synchronises; j_out / P_out as in heat_solve (device, with
- * room for the cells), overwritten.  Errors: as heat_solve. */
+ * a set of (streams, chunk_cells) pairs (the default first; each timed solve after a write
+ * larger than L2; the median of three) and keep the fastest: later solves whose opts leave
+ * both at 0 use it.  *streams_out / *chunk_out (or NULL) receive the choice (chunk 0 = the
+ * default size).  Runs the candidates on cuda_stream and synchronises; j_out / P_out as in
+ * heat_solve (device, with room for the cells), overwritten.  Allocates a temporary buffer
+ * of twice the L2 size.  Errors: as heat_solve. */
 heat_status heat_autotune(heat_ctx* ctx, const heat_opts* opts, double* P_out, void* j_out, void* cuda_stream,
                           int* streams_out, int* chunk_out);
 

@@ -78,6 +78,16 @@ __device__ __forceinline__ float e1f(float z) {
 }
 
 // E1(z) in FP64 (library expm1; exact at z = 0).
+// E1 for |z| <= 0.25: Taylor to z^5 (truncation < 5e-8 relative, below FP32 rounding).
+__device__ __forceinline__ float e1f_small(float z) {
+    float p = 1.0f / 720.0f;
+    p = fmaf(p, z, 1.0f / 120.0f);
+    p = fmaf(p, z, 1.0f / 24.0f);
+    p = fmaf(p, z, 1.0f / 6.0f);
+    p = fmaf(p, z, 0.5f);
+    return fmaf(p, z, 1.0f);
+}
+
 __device__ __forceinline__ double e1d(double z) {
     return z == 0.0 ? 1.0 : expm1(z) / z;
 }

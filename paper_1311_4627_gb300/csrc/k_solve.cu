@@ -157,10 +157,21 @@ __global__ void __launch_bounds__(128) k_build(GrainDev gd, ChunkDev ch) {
             float ua = us.x, su = us.y;
             float phi = __double2float_rn(Phi);
             int k = sp[n], k1 = sp[n + 1];
-            for (; k + 2 <= k1; k += 2) {
-                PatF32 a0 = gd.pat32[k], a1 = gd.pat32[k + 1];
-                __stcs(Bb + (size_t)a0.e * 32, fmaf(ua * a0.cat, e1f(fmaf(su, a0.t, a0.zt)), phi));
-                __stcs(Bb + (size_t)a1.e * 32, fmaf(ua * a1.cat, e1f(fmaf(su, a1.t, a1.zt)), phi));
+            // every element's argument is z = q t with t in [0, dln]: when |q| dln <= 1/4 the
+            // short series serves the whole segment.  The test is per lane (per cell), so a
+            // cell's values do not depend on the cells sharing its warp; lanes normally agree
+            if (fabsf(su + sC[n] + 2.0f) * gd.dln32[n] <= 0.25f) {
+                for (; k + 2 <= k1; k += 2) {
+                    PatF32 a0 = gd.pat32[k], a1 = gd.pat32[k + 1];
+                    __stcs(Bb + (size_t)a0.e * 32, fmaf(ua * a0.cat, e1f_small(fmaf(su, a0.t, a0.zt)), phi));
+                    __stcs(Bb + (size_t)a1.e * 32, fmaf(ua * a1.cat, e1f_small(fmaf(su, a1.t, a1.zt)), phi));
+                }
+            } else {
+                for (; k + 2 <= k1; k += 2) {
+                    PatF32 a0 = gd.pat32[k], a1 = gd.pat32[k + 1];
+                    __stcs(Bb + (size_t)a0.e * 32, fmaf(ua * a0.cat, e1f(fmaf(su, a0.t, a0.zt)), phi));
+                    __stcs(Bb + (size_t)a1.e * 32, fmaf(ua * a1.cat, e1f(fmaf(su, a1.t, a1.zt)), phi));
+                }
             }
             if (k < k1) {
                 PatF32 a0 = gd.pat32[k];
