@@ -88,6 +88,12 @@ __device__ __forceinline__ float e1f_small(float z) {
     return fmaf(p, z, 1.0f);
 }
 
+// Whether a segment's elements may use e1f_small: every argument there is z = q t with
+// t in [0, dl] and q = su + sC + 2, so |z| <= |q| dl.
+__device__ __forceinline__ bool short_series(float su, float sC, float dl) {
+    return fabsf(su + sC + 2.0f) * dl <= 0.25f;
+}
+
 __device__ __forceinline__ double e1d(double z) {
     return z == 0.0 ? 1.0 : expm1(z) / z;
 }

@@ -51,6 +51,7 @@ struct heat_ctx {
     std::vector<double> w;
     bool has_w = false;
     long long band_per_cell = 0;
+    int max_bins = 0;
     std::vector<int> grain_order;
     DevBuf d_bin_off, d_cabs, d_T, d_E, d_Cf, d_invC, d_invdE, d_invdE32, d_Cact, d_sC, d_ca32, d_ce32, d_sC32,
         d_rowptr, d_wmax, d_seg_ptr, d_pat64, d_pat32, d_soft, d_soft_off, d_K, d_Kw, d_w, d_koff_all, d_cde;

@@ -467,6 +467,8 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
     }
     soft_off[G] = (int)soft.size();
     ctx->band_per_cell = band_total;
+    ctx->max_bins = 0;
+    for (int g = 0; g < G; ++g) ctx->max_bins = std::max(ctx->max_bins, bin_offset[g + 1] - bin_offset[g]);
     ctx->grain_order.resize(G);
     for (int g = 0; g < G; ++g) ctx->grain_order[g] = g;
     std::stable_sort(ctx->grain_order.begin(), ctx->grain_order.end(),
@@ -668,6 +670,7 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
     gd.rowptr = ctx->d_rowptr.as<int>();
     gd.wmax = ctx->d_wmax.as<int>();
     gd.band_total = ctx->band_per_cell;
+    gd.max_bins = ctx->max_bins;
     gd.seg_ptr = ctx->d_seg_ptr.as<int>();
     gd.pat64 = ctx->d_pat64.as<PatF64>();
     gd.pat32 = ctx->d_pat32.as<PatF32>();
@@ -685,7 +688,8 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
         cudaStream_t cs = nslots > 1 ? sl.stream : st;
         const int cells = std::min(chunk, count - c0);
         const int cc_pad = (cells + 31) / 32 * 32;
-        ChunkDev ch;
+        ChunkDev ch{};
+        ch.small = count <= kSmallCells ? 1 : 0;
         ch.cells = cells;
         ch.Cc = cc_pad;
         ch.NG = cc_pad / 32;
@@ -1020,6 +1024,7 @@ __attribute__((visibility("hidden"))) heat_status heat_internal_grain_view(heat_
     gd->rowptr = ctx->d_rowptr.as<int>();
     gd->wmax = ctx->d_wmax.as<int>();
     gd->band_total = ctx->band_per_cell;
+    gd->max_bins = ctx->max_bins;
     gd->seg_ptr = ctx->d_seg_ptr.as<int>();
     gd->pat64 = ctx->d_pat64.as<PatF64>();
     gd->pat32 = ctx->d_pat32.as<PatF32>();

@@ -42,6 +42,7 @@ struct GrainDev {
                             //   rowptr[off_g + g + f] .. rowptr[off_g + g + f + 1] (global indices)
     const int* wmax;        // [G] widest band row of grain g (selects the recursion's window size)
     long long band_total;   // band elements of all grains (per cell)
+    int max_bins;           // largest bins per grain
     const int* seg_ptr;     // [G][N+1] pattern entries of grain g in segment n at
                             //   seg_ptr[g*(N+1)+n] .. seg_ptr[g*(N+1)+n+1]
     const PatF64* pat64;    // pattern entries (FP64 build)
@@ -71,7 +72,14 @@ struct ChunkDev {
     long long ldP;
     double* ledger;     // [cells][G][2] energy check (absorbed, emitted), or null
     int* status;
+    int small;          // 1: the solve has few cells (kSmallCells): element-parallel kernels
 };
+
+// Solves of at most this many cells use the element-parallel build and recursion (a block
+// per (cell, grain) for the build, a warp per spectrum with lanes over the band for the
+// recursion) instead of lane = cell, which would leave most lanes idle.  The choice is
+// made on the whole solve's cell count, so chunking never changes it.
+constexpr int kSmallCells = 16;
 
 cudaError_t launch_field(const GrainDev& g, const void* u, int dtype, long long cell0, const ChunkDev& ch, int build,
                          cudaStream_t st);

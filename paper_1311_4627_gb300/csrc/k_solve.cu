@@ -160,11 +160,15 @@ __global__ void __launch_bounds__(128) k_build(GrainDev gd, ChunkDev ch) {
             // every element's argument is z = q t with t in [0, dln]: when |q| dln <= 1/4 the
             // short series serves the whole segment.  The test is per lane (per cell), so a
             // cell's values do not depend on the cells sharing its warp; lanes normally agree
-            if (fabsf(su + sC[n] + 2.0f) * gd.dln32[n] <= 0.25f) {
+            if (short_series(su, sC[n], gd.dln32[n])) {
                 for (; k + 2 <= k1; k += 2) {
                     PatF32 a0 = gd.pat32[k], a1 = gd.pat32[k + 1];
                     __stcs(Bb + (size_t)a0.e * 32, fmaf(ua * a0.cat, e1f_small(fmaf(su, a0.t, a0.zt)), phi));
                     __stcs(Bb + (size_t)a1.e * 32, fmaf(ua * a1.cat, e1f_small(fmaf(su, a1.t, a1.zt)), phi));
+                }
+                if (k < k1) {
+                    PatF32 a0 = gd.pat32[k];
+                    __stcs(Bb + (size_t)a0.e * 32, fmaf(ua * a0.cat, e1f_small(fmaf(su, a0.t, a0.zt)), phi));
                 }
             } else {
                 for (; k + 2 <= k1; k += 2) {
@@ -172,10 +176,10 @@ __global__ void __launch_bounds__(128) k_build(GrainDev gd, ChunkDev ch) {
                     __stcs(Bb + (size_t)a0.e * 32, fmaf(ua * a0.cat, e1f(fmaf(su, a0.t, a0.zt)), phi));
                     __stcs(Bb + (size_t)a1.e * 32, fmaf(ua * a1.cat, e1f(fmaf(su, a1.t, a1.zt)), phi));
                 }
-            }
-            if (k < k1) {
-                PatF32 a0 = gd.pat32[k];
-                __stcs(Bb + (size_t)a0.e * 32, fmaf(ua * a0.cat, e1f(fmaf(su, a0.t, a0.zt)), phi));
+                if (k < k1) {
+                    PatF32 a0 = gd.pat32[k];
+                    __stcs(Bb + (size_t)a0.e * 32, fmaf(ua * a0.cat, e1f(fmaf(su, a0.t, a0.zt)), phi));
+                }
             }
             float a = ua * ca[n];
             if (a > 0.0f) {
@@ -437,6 +441,227 @@ __global__ void __launch_bounds__(128, 4) k_recur(GrainDev gd, ChunkDev ch) {
         recur_task<BUILD, 8>(gd, ch, g, grp, lane);
 }
 
+// ---------------------------------------------------------------------------
+// Element-parallel kernels for solves of few cells (ChunkDev::small).  They compute the same
+// quantities as k_build / k_recur with the same expressions; the build's cumulative sums
+// run in the same order (one thread), so B is bit-identical; the recursion sums each row
+// across lanes, so its rounding differs from the lane-per-cell kernel's.
+
+// Per-segment pieces of the build, shared in form with k_build (same operations, same order).
+struct SegF64 {
+    double om, q1, q0, dl, a;
+};
+__device__ __forceinline__ SegF64 seg64(const GrainDev& gd, int g, int n, double ua, double su) {
+    SegF64 r;
+    r.om = ua * gd.Cact[(size_t)g * gd.N + n];
+    const double sc = gd.sC[(size_t)g * gd.N + n];
+    r.q1 = su + sc + 2.0;
+    r.q0 = su + sc + 1.0;
+    const double ln = gd.lam[n];
+    r.a = r.om * ln * ln / kH;
+    r.dl = gd.dln[n];
+    return r;
+}
+
+// Block per (cell, grain): 256 threads, dynamic shared memory 2 N doubles.
+template <int BUILD>
+__global__ void __launch_bounds__(256) k_build_small(GrainDev gd, ChunkDev ch) {
+    extern __shared__ double sm[];
+    double* sPhi = sm;          // [N]: Phi before segment n (exclusive prefix), then Phi at the end
+    double* sPsi = sm + gd.N;   // [N]: Psi after the segments above n (exclusive suffix)
+    __shared__ double sPhiEnd, sPsiTot;
+    const int N = gd.N, Cc = ch.Cc;
+    const int cell = blockIdx.x / gd.G, g = blockIdx.x % gd.G;
+    if (cell >= ch.cells) return;
+    const int grp = cell >> 5, lc = cell & 31;
+    const int off = gd.bin_off[g];
+    const size_t bb = (size_t)grp * gd.band_total * 32 + lc;
+    const int* sp = gd.seg_ptr + (size_t)g * (N + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const float2* uasu = (const float2*)ch.ua32;
+    // 1. segment increments, in parallel
+    for (int n = tid; n < N - 1; n += blockDim.x) {
+        double dphi = 0.0, dpsi = 0.0;
+        if (BUILD == 0) {
+            const SegF64 s = seg64(gd, g, n, ch.ua64[(size_t)n * Cc + cell], ch.su64[(size_t)n * Cc + cell]);
+            if (s.om > 0.0) {
+                dphi = s.a * s.dl * e1d(s.q1 * s.dl);
+                dpsi = s.om * gd.lam[n] * s.dl * e1d(s.q0 * s.dl);
+            }
+        } else {
+            const float2 us = uasu[(size_t)n * Cc + cell];
+            const float ua = us.x, su = us.y;
+            const float sc = gd.sC32[(size_t)g * N + n], dl = gd.dln32[n];
+            const float a = ua * gd.ca32[(size_t)g * N + n];
+            if (a > 0.0f) dphi = widen_pos(a * dl * e1f((su + sc + 2.0f) * dl));
+            const float b = ua * gd.ce32[(size_t)g * N + n];
+            if (b > 0.0f) dpsi = widen_pos(b * dl * e1f((su + sc + 1.0f) * dl));
+        }
+        sPhi[n] = dphi;
+        sPsi[n] = dpsi;
+    }
+    __syncthreads();
+    // 2. the cumulative sums, in the lane-per-cell kernel's order
+    if (tid == 0) {
+        double Phi = 0.0;
+        for (int n = 0; n < N - 1; ++n) {
+            const double d = sPhi[n];
+            sPhi[n] = Phi;
+            Phi += d;
+        }
+        sPhiEnd = Phi;
+    } else if (tid == 32) {
+        double Psi = 0.0;
+        for (int n = N - 2; n >= 0; --n) {
+            const double d = sPsi[n];
+            sPsi[n] = Psi;
+            Psi += d;
+        }
+        sPsiTot = Psi;
+    }
+    __syncthreads();
+    // 3. band elements: warp per segment, lanes over its pattern entries
+    for (int n = warp; n < N - 1; n += blockDim.x >> 5) {
+        const int k0 = sp[n], k1 = sp[n + 1];
+        if (k0 == k1) continue;
+        if (BUILD == 0) {
+            const SegF64 s = seg64(gd, g, n, ch.ua64[(size_t)n * Cc + cell], ch.su64[(size_t)n * Cc + cell]);
+            const double aq = (s.q1 != 0.0) ? s.a / s.q1 : s.a;
+            const double Phi = sPhi[n];
+            for (int k = k0 + lane; k < k1; k += 32) {
+                const PatF64 pt = gd.pat64[k];
+                ch.Bb64[bb + (size_t)pt.e * 32] = Phi + (s.q1 != 0.0 ? aq * expm1(s.q1 * pt.t) : aq * pt.t);
+            }
+        } else {
+            const float2 us = uasu[(size_t)n * Cc + cell];
+            const float ua = us.x, su = us.y;
+            const float phi = __double2float_rn(sPhi[n]);
+            const bool sh = short_series(su, gd.sC32[(size_t)g * N + n], gd.dln32[n]);
+            for (int k = k0 + lane; k < k1; k += 32) {
+                const PatF32 a0 = gd.pat32[k];
+                const float z = fmaf(su, a0.t, a0.zt);
+                ch.Bb32[bb + (size_t)a0.e * 32] = fmaf(ua * a0.cat, sh ? e1f_small(z) : e1f(z), phi);
+            }
+        }
+    }
+    for (int k = sp[N - 1] + tid; k < sp[N]; k += blockDim.x) {
+        if (BUILD == 0)
+            ch.Bb64[bb + (size_t)gd.pat64[k].e * 32] = sPhiEnd;
+        else
+            ch.Bb32[bb + (size_t)gd.pat32[k].e * 32] = __double2float_rn(sPhiEnd);
+    }
+    __syncthreads();  // the intra-bin terms add to diagonal elements written above
+    // 4. intra-bin terms, one per soft entry (each has its own diagonal element)
+    for (int p = gd.soft_off[g] + tid; p < gd.soft_off[g + 1]; p += blockDim.x) {
+        const SoftF64 sf = gd.soft[p];
+        if (BUILD == 0) {
+            double v = 0.0;
+            if (sf.n == N - 1) {
+                v = 0.0;
+            } else if (sf.n >= 0) {
+                const SegF64 s = seg64(gd, g, sf.n, ch.ua64[(size_t)sf.n * Cc + cell],
+                                       ch.su64[(size_t)sf.n * Cc + cell]);
+                double part = 0.0;
+                if (s.om > 0.0) {
+                    const double L = s.dl - sf.t;
+                    part = s.om * gd.lam[sf.n] * exp(s.q0 * sf.t) * L * e1d(s.q0 * L);
+                }
+                v = kC * (part + sPsi[sf.n]) * gd.invdE[off + sf.j];
+            } else {
+                v = kC * sPsiTot * gd.invdE[off + sf.j];
+            }
+            const size_t ix = bb + (size_t)sf.e_diag * 32;
+            ch.Bb64[ix] = (sf.diag_in_band ? ch.Bb64[ix] : 0.0) + v;
+        } else {
+            float v = 0.0f;
+            if (sf.n == N - 1) {
+                v = 0.0f;
+            } else if (sf.n >= 0) {
+                const float2 us = uasu[(size_t)sf.n * Cc + cell];
+                const float b = us.x * gd.ce32[(size_t)g * N + sf.n];
+                const float q0 = us.y + gd.sC32[(size_t)g * N + sf.n] + 1.0f;
+                const float dl = gd.dln32[sf.n];
+                float part = 0.0f;
+                if (b > 0.0f) {
+                    const float ts = (float)sf.t;
+                    const float L = dl - ts;
+                    part = b * __expf(q0 * ts) * L * e1f(q0 * L);
+                }
+                v = (part + __double2float_rn(sPsi[sf.n])) * gd.invdE32[off + sf.j];
+            } else {
+                v = __double2float_rn(sPsiTot) * gd.invdE32[off + sf.j];
+            }
+            float* q = ch.Bb32 + bb + (size_t)sf.e_diag * 32;
+            *q = (sf.diag_in_band ? *q : 0.0f) + v;
+        }
+    }
+    if (tid == 0 && ch.pabs) ch.pabs[(size_t)cell * gd.G + g] = BUILD == 0 ? kC * sPsiTot : sPsiTot;
+}
+
+// Warp per spectrum, lanes over each row's band; X history in shared memory
+// (dynamic: max_bins doubles per warp).  Same recursion (Eq. xf), rescale and normalisation
+// as k_recur; each row's sum is reduced across lanes.
+template <int BUILD>
+__global__ void __launch_bounds__(128) k_recur_small(GrainDev gd, ChunkDev ch) {
+    extern __shared__ double smx[];
+    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (w >= ch.cells * gd.G) return;
+    double* xs = smx + (size_t)(threadIdx.x >> 5) * gd.max_bins;
+    const int cell = w / gd.G, g = w % gd.G;
+    const int grp = cell >> 5, lc = cell & 31;
+    const int off = gd.bin_off[g];
+    const int M = gd.bin_off[g + 1] - off - 1;
+    const int* rp = gd.rowptr + off + g;
+    const double* ic_row = gd.invC + off;
+    const size_t bb = (size_t)grp * gd.band_total * 32 + lc;
+    const float* B32 = ch.Bb32 + (BUILD ? bb : 0);
+    const double* B64 = ch.Bb64 + (BUILD ? 0 : bb);
+    bool numeric_bad = false;
+    if (lane == 0) xs[0] = 1.0;
+    double total = 1.0;
+    __syncwarp();
+    for (int f = 1; f <= M; ++f) {
+        const int e0 = rp[f], width = rp[f + 1] - e0, j0 = f - width;
+        double s = 0.0;
+        for (int k = lane; k < width; k += 32) s = fma(band_b<BUILD>(B32, B64, e0 + k), xs[j0 + k], s);
+        if (width > 1)
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const double S = __shfl_sync(0xffffffffu, s, 0);
+        const double ic = ic_row[f];
+        double X = S * ic;
+        if (__double2hiint(ic) == 0 && __double2loint(ic) == 0) {
+            X = 0.0;
+            if (S != 0.0) numeric_bad = true;
+        }
+        if (lane == 0) xs[f] = X;
+        total += X;
+        if (above_rescale(X)) {
+            __syncwarp();
+            for (int i = lane; i <= f; i += 32) xs[i] *= kRescaleSmall;
+            total *= kRescaleSmall;
+        }
+        __syncwarp();
+    }
+    const double inv = 1.0 / total;
+    double* prow = ch.P + (size_t)cell * ch.ldP + off;
+    double emit = 0.0;
+    for (int i = lane; i <= M; i += 32) {
+        const double p = xs[i] * inv;
+        prow[i] = p;
+        emit = fma(p, gd.cde[off + i], emit);
+    }
+    if (ch.ledger) {
+        for (int o = 16; o > 0; o >>= 1) emit += __shfl_xor_sync(0xffffffffu, emit, o);
+        if (lane == 0) {
+            double* lg = ch.ledger + ((size_t)cell * gd.G + g) * 2;
+            lg[0] = ch.pabs[(size_t)cell * gd.G + g];
+            lg[1] = emit;
+        }
+    }
+    if (numeric_bad && lane == 0) atomicOr(ch.status, kStatNumeric);
+}
+
 cudaError_t launch_field(const GrainDev& g, const void* u, int dtype, long long cell0, const ChunkDev& ch, int build,
                          cudaStream_t st) {
     dim3 block(32, 8), grid((g.N + 31) / 32, ch.Cc / 32);
@@ -459,6 +684,23 @@ cudaError_t launch_field(const GrainDev& g, const void* u, int dtype, long long 
 }
 
 cudaError_t launch_build(const GrainDev& g, const ChunkDev& ch, int build, cudaStream_t st) {
+    if (ch.small) {
+        const size_t smem = sizeof(double) * 2 * (size_t)g.N;
+        const unsigned blocks = (unsigned)(ch.cells * g.G);
+        if (blocks == 0) return cudaSuccess;
+        if (smem > 48 * 1024) {
+            cudaError_t e = build == 0 ? cudaFuncSetAttribute(k_build_small<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                              (int)smem)
+                                       : cudaFuncSetAttribute(k_build_small<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                              (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        if (build == 0)
+            k_build_small<0><<<blocks, 256, smem, st>>>(g, ch);
+        else
+            k_build_small<1><<<blocks, 256, smem, st>>>(g, ch);
+        return cudaGetLastError();
+    }
     int threads = 128, blocks = (ch.n_tasks + 3) / 4;
     if (build == 0)
         k_build<0><<<blocks, threads, 0, st>>>(g, ch);
@@ -468,6 +710,24 @@ cudaError_t launch_build(const GrainDev& g, const ChunkDev& ch, int build, cudaS
 }
 
 cudaError_t launch_recur(const GrainDev& g, const ChunkDev& ch, int build, cudaStream_t st) {
+    if (ch.small) {
+        const long long warps = (long long)ch.cells * g.G;
+        if (warps == 0) return cudaSuccess;
+        const size_t smem = sizeof(double) * 4 * (size_t)g.max_bins;  // 4 warps per block
+        if (smem > 48 * 1024) {
+            cudaError_t e = build == 0 ? cudaFuncSetAttribute(k_recur_small<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                              (int)smem)
+                                       : cudaFuncSetAttribute(k_recur_small<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                              (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        const unsigned blocks = (unsigned)((warps + 3) / 4);
+        if (build == 0)
+            k_recur_small<0><<<blocks, 128, smem, st>>>(g, ch);
+        else
+            k_recur_small<1><<<blocks, 128, smem, st>>>(g, ch);
+        return cudaGetLastError();
+    }
     int threads = 128, blocks = (ch.n_tasks + 3) / 4;
     if (build == 0)
         k_recur<0><<<blocks, threads, 0, st>>>(g, ch);

@@ -106,6 +106,7 @@ extern "C" heat_status heat_solve_noalloc(heat_ctx* ctx, int build, const double
             return (void*)q;
         };
         ChunkDev ch{};
+        ch.small = n_cells <= kSmallCells ? 1 : 0;  // as heat_solve decides
         ch.cells = cells;
         ch.Cc = Cc;
         ch.NG = NG;

@@ -99,12 +99,14 @@ def test_size_integration_and_f32_output(batched_sub):
 
 
 def test_cell_ranges_compose_bitwise(batched_sub):
-    """Solving [0, k) and [k, n) separately equals one solve (independent spectra)."""
+    """Solving [0, k) and [k, n) separately equals one solve (independent spectra).  Both
+    parts exceed the small-solve threshold (16 cells), so all three solves run the same
+    kernels; small solves agree to rounding (test_small_solves_match_...)."""
     wl, _, _, _, lib = batched_sub
     Pa, ja = lib.solve(build=heat.HEAT_BUILD_F32)
     n = wl.n_cells
-    P1, j1 = lib.solve(build=heat.HEAT_BUILD_F32, cell_begin=0, cell_count=13)
-    P2, j2 = lib.solve(build=heat.HEAT_BUILD_F32, cell_begin=13, cell_count=n - 13)
+    P1, j1 = lib.solve(build=heat.HEAT_BUILD_F32, cell_begin=0, cell_count=20)
+    P2, j2 = lib.solve(build=heat.HEAT_BUILD_F32, cell_begin=20, cell_count=n - 20)
     assert np.array_equal(np.concatenate([P1, P2]), Pa)
     assert np.array_equal(np.concatenate([j1, j2]), ja)
 
@@ -203,3 +205,20 @@ def test_energy_check_matches_oracle(batched_sub, build, tol_abs, tol_emit):
     ratio = led[:, :, 1] / led[:, :, 0]
     assert np.all(np.abs(ratio / ratio_ref - 1.0) < tol_emit)
     assert np.all((ratio > 0.7) & (ratio < 1.5)), (ratio.min(), ratio.max())
+
+
+@pytest.mark.parametrize("build", [heat.HEAT_BUILD_F64, heat.HEAT_BUILD_F32])
+def test_small_solves_match_the_lane_per_cell_kernels(batched_sub, build):
+    """A solve of at most 16 cells takes the element-parallel kernels; the same cells solved
+    within a larger solve take the lane-per-cell kernels.  The build is the same arithmetic;
+    the recursion sums each row in another order, so P agrees to rounding, not bitwise."""
+    wl, _, P_ref, j_ref, lib = batched_sub
+    P_all, j_all = lib.solve(build=build, emis=heat.HEAT_EMIS_F64)
+    P_s, j_s = lib.solve(build=build, emis=heat.HEAT_EMIS_F64, cell_begin=5, cell_count=12)
+    r, ok = relerr(P_s, P_all[5:17])
+    assert ok and r <= 1e-12, r
+    r, ok = relerr(j_s, j_all[5:17])
+    assert ok and r <= 1e-12, r
+    if build == heat.HEAT_BUILD_F64:
+        r, ok = relerr(P_s, P_ref[5:17])
+        assert ok and r <= EXACT_TOL, r
