@@ -9,7 +9,7 @@
 // tcgen05 GEMM, one persistent CTA per SM, warp-specialised:
 //   warp 0 lane 0 : TMA producer (2D tiled loads, 128B swizzle) into a 4-stage smem ring
 //   warp 1 lane 0 : MMA issuer (tcgen05.mma cta_group::1, M=128 N=256, FP32 in TMEM)
-//   warps 2..5    : epilogue (tcgen05.ld -> scale -> smem transpose -> coalesced stores)
+//   warps 2..5    : epilogue (tcgen05.ld -> scale -> 16-byte stores, one row per lane)
 // Two TMEM accumulators (2 x 256 columns) let the epilogue of one tile overlap the MMAs
 // of the next.  Every mbarrier wait is bounded; on timeout the kernel flags
 // kStatTimeout, drains its own copies and MMAs with bounded waits, frees TMEM and exits.
@@ -30,7 +30,6 @@ constexpr int kM = 128, kN = 256, kStages = 4;
 constexpr int kAStage = kM * 128;  // bytes: 128 rows x 128 B
 constexpr int kBStage = kN * 128;  // bytes: 256 rows x 128 B
 constexpr int kEpiWarps = 4;
-constexpr int kEpiTile = 32 * 33;  // floats per epilogue warp (32 x 32, padded)
 
 }  // namespace
 
@@ -56,8 +55,7 @@ __global__ void __launch_bounds__(192, 1) k_emis_tc(const __grid_constant__ Emis
     unsigned char* sB = smem + kStages * kAStage;
     uint64_t* bars = (uint64_t*)(sB + kStages * kBStage);
     // bars: full[kStages], empty[kStages], tfull[2], tempty[2], done
-    float* epi = (float*)(bars + 2 * kStages + 5);
-    uint32_t* tmem_slot = (uint32_t*)(epi + kEpiWarps * kEpiTile);
+    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * kStages + 5);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -178,9 +176,10 @@ __global__ void __launch_bounds__(192, 1) k_emis_tc(const __grid_constant__ Emis
                 if (mbar_try(b_done, 0)) break;
         }
     } else {
-        // ---------------- epilogue: warps 2..5 own TMEM lane quarters (warp % 4)
+        // ---------------- epilogue: warps 2..5 own TMEM lane quarters (warp % 4); lane = row
+        // of the tile.  Each lane scales its 32 columns of a chunk and writes them as eight
+        // 16-byte stores (one 128-byte run per row); the column scales are broadcast loads.
         const int q = warp & 3;
-        float* st = epi + (warp - 2) * kEpiTile;
         int acc = 0;
         uint32_t acc_phase = 0;
         for (int t = blockIdx.x; t < total; t += gridDim.x) {
@@ -196,30 +195,46 @@ __global__ void __launch_bounds__(192, 1) k_emis_tc(const __grid_constant__ Emis
             }
             tc_fence_after();
             const int g = p.grain[gi];
-            const int row0 = mt * kM + q * 32;
-            const int my_row = row0 + lane;
-            const float rs = my_row < p.cells ? p.rowscale[(size_t)my_row * p.G + g] : 0.0f;
+            const int row = mt * kM + q * 32 + lane;
+            const bool rok = row < p.cells;
+            const float rs = rok ? p.rowscale[(size_t)row * p.G + g] : 0.0f;
+            const size_t jrow = (size_t)(rok ? row : 0) * p.ldj + (size_t)g * p.N;
+            const float* csg = p.colscale + (size_t)g * p.N;
             for (int c = 0; c < kN / 32; ++c) {
                 uint32_t v[32];
                 tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kN + c * 32), v);
+                const int col0 = nt * kN + c * 32;
+                if (col0 >= p.N) continue;
+                float* dst = (float*)p.j + jrow + col0;
+                const bool fast = !p.j_f64 && col0 + 32 <= p.N &&
+                                  __all_sync(0xffffffffu, ((uintptr_t)dst & 15u) == 0 && ((uintptr_t)(csg + col0) & 15u) == 0);
+                if (fast) {
+                    const float4* cs4 = (const float4*)(csg + col0);
 #pragma unroll
-                for (int i = 0; i < 32; ++i) st[lane * 33 + i] = __uint_as_float(v[i]);
-                __syncwarp();
-                const int col = nt * kN + c * 32 + lane;
-                const float cs = col < p.N ? p.colscale[(size_t)g * p.N + col] : 0.0f;
-                for (int r = 0; r < 32; ++r) {
-                    const float rsr = __shfl_sync(0xffffffffu, rs, r);
-                    const int row = row0 + r;
-                    if (row < p.cells && col < p.N) {
-                        size_t o = (size_t)row * p.ldj + (size_t)g * p.N + col;
-                        float val = st[r * 33 + lane];
-                        if (p.j_f64)
-                            ((double*)p.j)[o] = (double)val * (double)rsr * (double)cs;
-                        else
-                            ((float*)p.j)[o] = val * rsr * cs;
+                    for (int k = 0; k < 8; ++k) {
+                        const float4 cs = cs4[k];
+                        float4 o;
+                        o.x = __uint_as_float(v[4 * k]) * rs * cs.x;
+                        o.y = __uint_as_float(v[4 * k + 1]) * rs * cs.y;
+                        o.z = __uint_as_float(v[4 * k + 2]) * rs * cs.z;
+                        o.w = __uint_as_float(v[4 * k + 3]) * rs * cs.w;
+                        if (rok) __stcs((float4*)dst + k, o);
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const int col = col0 + i;
+                        if (rok && col < p.N) {
+                            const float val = __uint_as_float(v[i]);
+                            const float cs = csg[col];
+                            const size_t o = jrow + col;
+                            if (p.j_f64)
+                                ((double*)p.j)[o] = (double)val * (double)rs * (double)cs;
+                            else
+                                ((float*)p.j)[o] = val * rs * cs;
+                        }
                     }
                 }
-                __syncwarp();
             }
             tc_fence_before();
             __syncwarp();
@@ -239,7 +254,7 @@ __global__ void __launch_bounds__(192, 1) k_emis_tc(const __grid_constant__ Emis
 }
 
 size_t emis_tc_smem_bytes() {
-    return 1024 + (size_t)kStages * (kAStage + kBStage) + (2 * kStages + 5) * 8 + kEpiWarps * kEpiTile * 4 + 16;
+    return 1024 + (size_t)kStages * (kAStage + kBStage) + (2 * kStages + 5) * 8 + 16;
 }
 
 cudaError_t launch_emis_tc(const EmisTcParams& p, bool tf32, int sms, cudaStream_t st) {
