@@ -79,7 +79,8 @@ typedef struct heat_opts {
                            in the accumulator)                                                    */
     int cell_begin;     /* first cell solved (0-based)                                             */
     int cell_count;     /* cells solved; <= 0 means all cells from cell_begin                      */
-    int chunk_cells;    /* cells per internal chunk (multiple of 32; 0 = library default)         */
+    int chunk_cells;    /* cells per internal chunk (multiple of 32; 0 = library default: as many
+                           as 45 % of the usable device memory holds)                             */
     int host_io;        /* 1: P_out and j_out are host pointers; the library stages through device
                            memory and the call returns after the results are on the host          */
     int timing;         /* 1: record CUDA events around every kernel launch (see heat_get_timing)  */

@@ -540,6 +540,26 @@ heat_status heat_set_fields(heat_ctx* ctx, int n_cells, const void* u, int dtype
     return HEAT_OK;
 }
 
+// Default cells per chunk: as many as 45 % of the device memory the library could use (free
+// memory plus the chunk scratch it already holds) allows for `nslots` chunks in flight (B band,
+// X history, field tables per 32-cell group), at least one group; with several slots the range
+// is also split evenly over them.  More cells per chunk means more warps in flight for the
+// latency-bound build and recursion kernels.
+static int default_chunk(heat_ctx* ctx, int build, int count, int nslots) {
+    const size_t per_group = (size_t)ctx->band_per_cell * 32 * (build == 0 ? 8 : 4) + (size_t)ctx->nbt * 32 * 10 +
+                             (size_t)ctx->N * 32 * 16;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = size_t(16) << 30;
+    size_t held = 0;
+    for (auto& sl : ctx->slots) held += sl.ua64.cap + sl.su64.cap + sl.ua32.cap + sl.Bb64.cap + sl.Bb32.cap + sl.xs.cap +
+                                        sl.ep.cap;
+    const size_t budget = std::max<size_t>(size_t(2) << 30, (size_t)(0.45 * (double)(free_b + held)));
+    size_t groups = std::max<size_t>(1, budget / (size_t)nslots / per_group);
+    size_t want = ((size_t)count + 31) / 32;
+    if (nslots > 1) want = (want + nslots - 1) / nslots;
+    return (int)(std::min(groups, std::max<size_t>(1, want)) * 32);
+}
+
 heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void* j_out, void* stream) {
     if (!ctx || !opts) return HEAT_EINVAL;
     if (ctx->G == 0) return ctx->fail(HEAT_ESTATE, "heat_solve: grains not set");
@@ -565,9 +585,9 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
     const size_t jrow = (size_t)(o.size_integrate ? 1 : G) * N;
 
     // chunks in flight and cells per chunk: the caller's, else heat_autotune's, else the
-    // default: one stream, chunks as large as ~16 GiB of scratch (B band, X history, field
-    // tables) allows, since a chunk's recursion time is bounded below by its longest tasks;
-    // with streams > 1 and no chunk size, the range is split evenly over the streams
+    // default: one stream, chunks as large as the memory budget allows (default_chunk),
+    // since a chunk's build and recursion run faster with more warps in flight and its
+    // recursion time is bounded below by its longest tasks
     int nslots = o.streams > 0 ? o.streams : 0;
     int chunk = o.chunk_cells;
     if (nslots == 0 && chunk == 0 && ctx->tuned_streams > 0) {
@@ -576,13 +596,7 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
     }
     if (nslots == 0) nslots = 1;
     nslots = std::min(nslots, (int)heat_ctx::kMaxSlots);
-    if (chunk == 0) {
-        size_t per_group = (size_t)ctx->band_per_cell * 32 * (build == 0 ? 8 : 4) + (size_t)nbt * 32 * 10 +
-                           (size_t)N * 32 * 16;
-        size_t groups = std::max<size_t>(1, (size_t(16) << 30) / nslots / per_group);
-        chunk = (int)std::min<size_t>(groups * 32, 16384);
-        if (nslots > 1) chunk = std::min(chunk, ((count + nslots - 1) / nslots + 31) / 32 * 32);
-    }
+    if (chunk == 0) chunk = default_chunk(ctx, build, count, nslots);
     const int n_chunks = (count + chunk - 1) / chunk;
     nslots = std::max(1, std::min(nslots, n_chunks));
     const int span = std::min(count, chunk);
@@ -839,11 +853,22 @@ heat_status heat_graph_create(heat_ctx* ctx, const heat_opts* opts, double* P_ou
     CKR(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
     if (st == nullptr) return ctx->fail(HEAT_EINVAL, "heat_graph_create: capture needs a non-default stream");
-    heat_status h = heat_solve(ctx, opts, P_out, j_out, stream);  // allocations, uploads, streams
+    // fix the chunking now: the default depends on free memory, which the warm-up changes
+    heat_opts o = *opts;
+    if (o.streams == 0 && o.chunk_cells == 0 && ctx->tuned_streams > 0) {
+        o.streams = ctx->tuned_streams;
+        o.chunk_cells = ctx->tuned_chunk;
+    }
+    if (o.streams == 0) o.streams = 1;
+    if (o.chunk_cells == 0) {
+        const int count = o.cell_count > 0 ? o.cell_count : ctx->n_cells - o.cell_begin;
+        o.chunk_cells = default_chunk(ctx, o.build, std::max(count, 1), std::min(o.streams, (int)heat_ctx::kMaxSlots));
+    }
+    heat_status h = heat_solve(ctx, &o, P_out, j_out, stream);  // allocations, uploads, streams
     if (h != HEAT_OK) return h;
     CKR(cudaStreamSynchronize(st));
     CKR(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    h = heat_solve(ctx, opts, P_out, j_out, stream);
+    h = heat_solve(ctx, &o, P_out, j_out, stream);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(st, &g);
     if (h != HEAT_OK) {
