@@ -52,7 +52,7 @@ struct heat_ctx {
     bool has_w = false;
     long long band_per_cell = 0;
     int max_bins = 0;
-    std::vector<int> grain_order;
+    std::vector<int> grain_order, grain_order_build;  // task orders of the recursion and the build
     DevBuf d_bin_off, d_cabs, d_T, d_E, d_Cf, d_invC, d_invdE, d_invdE32, d_Cact, d_sC, d_ca32, d_ce32, d_sC32,
         d_rowptr, d_wmax, d_seg_ptr, d_pat64, d_pat32, d_soft, d_soft_off, d_K, d_Kw, d_w, d_koff_all, d_cde;
     // fields
@@ -60,8 +60,9 @@ struct heat_ctx {
     const void* u_dev = nullptr;
     int u_dtype = 0;
     DevBuf d_u_own;
-    // chunk task lists: (grain, group) pairs, grains in LPT order; `full` for chunks of
-    // tasks_NG groups, `tail` for the last, shorter chunk (tail_NG groups)
+    // chunk task lists: (grain, group) pairs, the recursion's order then the build's (each
+    // longest first); `full` for chunks of tasks_NG groups, `tail` for the last, shorter
+    // chunk (tail_NG groups)
     DevBuf s_tasks, s_tasks_tail;
     int tasks_NG = -1, tail_NG = -1;
     // scratch of one chunk in flight; chunks go round-robin over the slots, each slot on

@@ -217,12 +217,15 @@ static heat_status emis_tc_chunk(heat_ctx* ctx, int m, bool si, const double* P,
     return HEAT_OK;
 }
 
-// (grain, group) task list of a chunk of NG groups, grains in LPT order.
+// (grain, group) task lists of a chunk of NG groups, longest first: the recursion's order
+// (grains by band + 30 x rows: a long chain of narrow rows takes its time whatever the
+// load, so it starts early) followed by the build's (band + 12 x rows).
 static std::vector<int2> make_tasks(const heat_ctx* ctx, int NG) {
     std::vector<int2> tasks;
-    tasks.reserve((size_t)ctx->G * NG);
-    for (int gi = 0; gi < ctx->G; ++gi)
-        for (int grp = 0; grp < NG; ++grp) tasks.push_back(make_int2(ctx->grain_order[gi], grp));
+    tasks.reserve(2 * (size_t)ctx->G * NG);
+    for (const auto* order : {&ctx->grain_order, &ctx->grain_order_build})
+        for (int gi = 0; gi < ctx->G; ++gi)
+            for (int grp = 0; grp < NG; ++grp) tasks.push_back(make_int2((*order)[gi], grp));
     return tasks;
 }
 
@@ -355,7 +358,7 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
     std::vector<int> soft_off(G + 1, 0);
     std::vector<int> wmax(G, 1);
     std::vector<int> bin_grain(nbt);
-    std::vector<long long> cost(G, 0);
+    std::vector<long long> cost(G, 0), cost_build(G, 0);
     long long band_total = 0;
     struct Ent {
         int n, e;
@@ -463,16 +466,20 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
             return ctx->fail(HEAT_EINVAL, "heat_set_grains: band of the grains too large (over 6.7e7 elements)");
         // task order (longest first): a row costs about as much as 12 band elements in
         // the recursion (its chain waits on dependent FP64 ops), so many-row grains start early
-        cost[g] = band + 12LL * nb;
+        cost[g] = band + 30LL * nb;
+        cost_build[g] = band + 12LL * nb;
     }
     soft_off[G] = (int)soft.size();
     ctx->band_per_cell = band_total;
     ctx->max_bins = 0;
     for (int g = 0; g < G; ++g) ctx->max_bins = std::max(ctx->max_bins, bin_offset[g + 1] - bin_offset[g]);
     ctx->grain_order.resize(G);
-    for (int g = 0; g < G; ++g) ctx->grain_order[g] = g;
+    ctx->grain_order_build.resize(G);
+    for (int g = 0; g < G; ++g) ctx->grain_order[g] = ctx->grain_order_build[g] = g;
     std::stable_sort(ctx->grain_order.begin(), ctx->grain_order.end(),
                      [&](int a, int b) { return cost[a] > cost[b]; });
+    std::stable_sort(ctx->grain_order_build.begin(), ctx->grain_order_build.end(),
+                     [&](int a, int b) { return cost_build[a] > cost_build[b]; });
 
     std::vector<double> cabs(c_abs_cm2, c_abs_cm2 + (size_t)G * N), T(T_bins_K, T_bins_K + nbt),
         E(H_bins_erg, H_bins_erg + nbt);
@@ -708,6 +715,7 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
         ch.Cc = cc_pad;
         ch.NG = cc_pad / 32;
         ch.tasks = (ch.NG == NG ? ctx->s_tasks : ctx->s_tasks_tail).as<int2>();
+        ch.btasks = ch.tasks + (size_t)G * ch.NG;
         ch.n_tasks = G * ch.NG;
         ch.ua64 = sl.ua64.as<double>();
         ch.su64 = sl.su64.as<double>();

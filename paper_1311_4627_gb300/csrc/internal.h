@@ -56,7 +56,8 @@ struct ChunkDev {
     int cells;          // valid cells in the chunk
     int Cc;             // padded cells (multiple of 32)
     int NG;             // Cc / 32 cell groups
-    const int2* tasks;  // [G * NG] (grain, group), largest work first
+    const int2* tasks;  // [G * NG] (grain, group), largest work first (recursion order)
+    const int2* btasks; // the same pairs in the build's order, or null (then `tasks`)
     int n_tasks;
     // field tables, transposed [N][Cc]
     double* ua64; double* su64;

@@ -86,7 +86,8 @@ __global__ void __launch_bounds__(128) k_build(GrainDev gd, ChunkDev ch) {
     int lane = threadIdx.x & 31;
     if (task >= ch.n_tasks) return;
     const int N = gd.N, Cc = ch.Cc;
-    int g = ch.tasks[task].x, grp = ch.tasks[task].y;
+    const int2 tk = (ch.btasks ? ch.btasks : ch.tasks)[task];
+    int g = tk.x, grp = tk.y;
     int off = gd.bin_off[g];
     int cc = grp * 32 + lane;
     size_t bb = (size_t)grp * gd.band_total * 32 + lane;  // + e * 32
