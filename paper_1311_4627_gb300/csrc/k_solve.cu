@@ -264,21 +264,22 @@ struct BandRaw<1> {
     static __device__ __forceinline__ double wide(T v) { return widen_pos(v); }
 };
 
-// Window part of a row: element e1-1-k multiplies X_{f-1-k} = w[k] for k < nreg (<= W);
-// a jump into the unrolled tail, so no predicated-off FMA occupies the FP64 pipe.
+// Window part of a row: element e1-1-k multiplies X_{f-1-k} = w[k] for k < nreg (<= W),
+// accumulated into S in element order; a jump into the unrolled tail, so no predicated-off
+// FMA occupies the FP64 pipe.
 template <int BUILD, int W>
 __device__ __forceinline__ void window_tail(int nreg, const typename BandRaw<BUILD>::T (&br)[W],
-                                            const double (&w)[W], double& S, double& S1) {
+                                            const double (&w)[W], double& S) {
     using Raw = BandRaw<BUILD>;
     switch (nreg) {
-        case 8: if constexpr (W > 7) S1 = fma(Raw::wide(br[7 % W]), w[7 % W], S1);  // fallthrough
-        case 7: if constexpr (W > 6) S = fma(Raw::wide(br[6 % W]), w[6 % W], S);    // fallthrough
-        case 6: if constexpr (W > 5) S1 = fma(Raw::wide(br[5 % W]), w[5 % W], S1);  // fallthrough
-        case 5: if constexpr (W > 4) S = fma(Raw::wide(br[4 % W]), w[4 % W], S);    // fallthrough
-        case 4: if constexpr (W > 3) S1 = fma(Raw::wide(br[3 % W]), w[3 % W], S1);  // fallthrough
-        case 3: if constexpr (W > 2) S = fma(Raw::wide(br[2 % W]), w[2 % W], S);    // fallthrough
-        case 2: if constexpr (W > 1) S1 = fma(Raw::wide(br[1 % W]), w[1 % W], S1);  // fallthrough
-        case 1: S = fma(Raw::wide(br[0]), w[0], S);                                 // fallthrough
+        case 8: if constexpr (W > 7) S = fma(Raw::wide(br[7 % W]), w[7 % W], S);  // fallthrough
+        case 7: if constexpr (W > 6) S = fma(Raw::wide(br[6 % W]), w[6 % W], S);  // fallthrough
+        case 6: if constexpr (W > 5) S = fma(Raw::wide(br[5 % W]), w[5 % W], S);  // fallthrough
+        case 5: if constexpr (W > 4) S = fma(Raw::wide(br[4 % W]), w[4 % W], S);  // fallthrough
+        case 4: if constexpr (W > 3) S = fma(Raw::wide(br[3 % W]), w[3 % W], S);  // fallthrough
+        case 3: if constexpr (W > 2) S = fma(Raw::wide(br[2 % W]), w[2 % W], S);  // fallthrough
+        case 2: if constexpr (W > 1) S = fma(Raw::wide(br[1 % W]), w[1 % W], S);  // fallthrough
+        case 1: S = fma(Raw::wide(br[0]), w[0], S);                               // fallthrough
         default: break;
     }
 }
@@ -353,7 +354,9 @@ __device__ __forceinline__ void recur_task(const GrainDev& gd, const ChunkDev& c
         const int width = e1 - e;          // band of row f: j in [f - width, f)
         const int nreg = min(width, W);    // its last nreg elements come from the window
         const int e_mem = e1 - nreg;       // elements before e_mem read X from memory
-        double S = 0.0, S1 = 0.0;
+        // one accumulator, in element order: the SM sub-partition's FP64 unit, shared by the
+        // warps on it, is the bound, not this warp's dependent FMA chain
+        double S = 0.0;
         if (e < e_mem) {
             int j = f - width;
             for (; e + 8 <= e_mem; e += 8, j += 8) {
@@ -363,15 +366,11 @@ __device__ __forceinline__ void recur_task(const GrainDev& gd, const ChunkDev& c
 #pragma unroll
                 for (int k = 0; k < 8; ++k) x[k] = xl[(j + k) * 32];
 #pragma unroll
-                for (int k = 0; k < 8; k += 2) {
-                    S = fma(b[k], x[k], S);
-                    S1 = fma(b[k + 1], x[k + 1], S1);
-                }
+                for (int k = 0; k < 8; ++k) S = fma(b[k], x[k], S);
             }
-            for (; e < e_mem; ++e, ++j) S1 = fma(band_b<BUILD>(B32, B64, e), xl[j * 32], S1);
+            for (; e < e_mem; ++e, ++j) S = fma(band_b<BUILD>(B32, B64, e), xl[j * 32], S);
         }
-        window_tail<BUILD, W>(nreg, br, w, S, S1);
-        if (width > 1) S += S1;
+        window_tail<BUILD, W>(nreg, br, w, S);
         double X = S * ic;
         if (__double2hiint(ic) == 0 && __double2loint(ic) == 0) {  // zero cooling rate
             X = 0.0;
