@@ -137,3 +137,68 @@ def test_checkpoint_round_trip(trained, tmp_path):
             heat.heat_surrogate_save(lib.ctx, path)
             heat.heat_surrogate_load(lib.ctx, path)
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_what_training_gains(small):
+    """What the trained network adds: on held-out cells its error is far below the same
+    network's before training, and evaluating it costs less GPU time than solving the same
+    spectra on the plain exact path.  (Its accuracy does not reach the 1e-2 fallback bound;
+    the fallback keeps the combined result within it.)"""
+    import torch
+
+    wl, lib = small
+    st = torch.cuda.current_stream().cuda_stream
+    held = (224, 32)
+    ns = held[1] * wl.n_grains
+    X = torch.empty(ns, heat.SURROGATE_INPUTS, dtype=torch.float32, device="cuda")
+    lnp = torch.empty(ns, dtype=torch.float32, device="cuda")
+    ref = torch.empty(held[1], wl.n_grains, wl.n_lambda, dtype=torch.float32, device="cuda")
+    heat.heat_solve(lib.ctx, heat.heat_default_opts(build=heat.HEAT_BUILD_F64, emis=heat.HEAT_EMIS_F64,
+                                                    j_dtype=heat.HEAT_F32, cell_begin=held[0], cell_count=held[1]),
+                    None, ref, st)
+
+    def err_of_network():
+        heat.heat_surrogate_samples(lib.ctx, held[0], held[1], None, X, None, lnp, st)
+        lnj = torch.empty(ns, wl.n_lambda, dtype=torch.float32, device="cuda")
+        sp = torch.empty(ns, dtype=torch.float32, device="cuda")
+        heat.heat_surrogate_predict(lib.ctx, X, lnp, ns, lnj, sp, st)
+        heat.heat_sync(lib.ctx)
+        r = ref.reshape(ns, wl.n_lambda).double()
+        m = r > 1e-6 * r.max(dim=1, keepdim=True).values
+        e = (torch.exp(lnj.double()) - r).abs() / r.clamp_min(1e-300)
+        return float(torch.median(torch.where(m, e, torch.zeros_like(e)).max(dim=1).values))
+
+    # untrained network with the same normalisation, then trained
+    j = torch.empty(192, wl.n_grains, wl.n_lambda, dtype=torch.float32, device="cuda")
+    heat.heat_solve(lib.ctx, heat.heat_default_opts(build=heat.HEAT_BUILD_F32, emis=heat.HEAT_EMIS_BF16X3,
+                                                    j_dtype=heat.HEAT_F32, cell_count=192), None, j, st)
+    n_tr = 192 * wl.n_grains
+    Xt = torch.empty(n_tr, heat.SURROGATE_INPUTS, dtype=torch.float32, device="cuda")
+    Yt = torch.empty(n_tr, wl.n_lambda, dtype=torch.float32, device="cuda")
+    heat.heat_surrogate_init(lib.ctx, 4, np.zeros(wl.n_grains), seed=21)
+    heat.heat_surrogate_samples(lib.ctx, 0, 192, j, Xt, Yt, None, st)
+    heat.heat_surrogate_fit_norm(lib.ctx, Xt, Yt, n_tr, st)
+    e_untrained = err_of_network()
+    heat.heat_surrogate_train(lib.ctx, Xt, Yt, n_tr, 256, 60, 1e-3, seed=5, stream=st)
+    e_trained = err_of_network()
+    assert e_trained < 0.5 * e_untrained, (e_trained, e_untrained)
+
+    # GPU time: network inference vs the exact path on the same spectra
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    for _ in range(5):
+        heat.heat_solve(lib.ctx, heat.heat_default_opts(build=heat.HEAT_BUILD_F64, emis=heat.HEAT_EMIS_F64,
+                                                        j_dtype=heat.HEAT_F32, cell_begin=held[0],
+                                                        cell_count=held[1]), None, ref, st)
+    ev[1].record()
+    lnj = torch.empty(ns, wl.n_lambda, dtype=torch.float32, device="cuda")
+    sp = torch.empty(ns, dtype=torch.float32, device="cuda")
+    ev[2].record()
+    for _ in range(5):
+        heat.heat_surrogate_samples(lib.ctx, held[0], held[1], None, X, None, lnp, st)
+        heat.heat_surrogate_predict(lib.ctx, X, lnp, ns, lnj, sp, st)
+    ev[3].record()
+    torch.cuda.synchronize()
+    t_exact, t_net = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+    assert t_net < t_exact, (t_net, t_exact)
