@@ -359,14 +359,41 @@ __device__ __forceinline__ void recur_task(const GrainDev& gd, const ChunkDev& c
         double S = 0.0;
         if (e < e_mem) {
             int j = f - width;
-            for (; e + 8 <= e_mem; e += 8, j += 8) {
-                double b[8], x[8];
+            // batches of 8 elements, two register sets: the loads of the next batch are in
+            // flight while this batch's FMAs run (no register copy waits on a load)
+            const int nb = (e_mem - e) >> 3;
+            if (nb > 0) {
+                typename Raw::T bA[8], bB[8];
+                double xA[8], xB[8];
 #pragma unroll
-                for (int k = 0; k < 8; ++k) b[k] = band_b<BUILD>(B32, B64, e + k);
+                for (int k = 0; k < 8; ++k) bA[k] = Raw::load(B32, B64, e + k);
 #pragma unroll
-                for (int k = 0; k < 8; ++k) x[k] = xl[(j + k) * 32];
+                for (int k = 0; k < 8; ++k) xA[k] = xl[(j + k) * 32];
+                int i = 0;
+                for (; i + 2 <= nb; i += 2) {
 #pragma unroll
-                for (int k = 0; k < 8; ++k) S = fma(b[k], x[k], S);
+                    for (int k = 0; k < 8; ++k) bB[k] = Raw::load(B32, B64, e + 8 + k);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) xB[k] = xl[(j + 8 + k) * 32];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) S = fma(Raw::wide(bA[k]), xA[k], S);
+                    if (i + 2 < nb) {
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) bA[k] = Raw::load(B32, B64, e + 16 + k);
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) xA[k] = xl[(j + 16 + k) * 32];
+                    }
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) S = fma(Raw::wide(bB[k]), xB[k], S);
+                    e += 16;
+                    j += 16;
+                }
+                if (i < nb) {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) S = fma(Raw::wide(bA[k]), xA[k], S);
+                    e += 8;
+                    j += 8;
+                }
             }
             for (; e < e_mem; ++e, ++j) S = fma(band_b<BUILD>(B32, B64, e), xl[j * 32], S);
         }
