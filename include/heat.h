@@ -92,8 +92,11 @@ typedef struct heat_opts {
     int streams;        /* chunks in flight (1..4), each on an internal stream forked from and
                            joined back into cuda_stream, so that the recursion of one chunk
                            overlaps the matrix build and emissivity of the next; 0 = the
-                           library default (or heat_autotune's choice).  Results do not depend
-                           on it or on chunk_cells (every spectrum is computed the same way)   */
+                           library default (heat_autotune's choice, else 1 on device buffers and
+                           2 with host_io, whose copies then overlap the other chunk's kernels).
+                           Results do not depend on it or on chunk_cells, except that solves of
+                           at most 16 cells take element-parallel kernels (same bounds against
+                           the oracle, rounding differs in the last bits)                      */
 } heat_opts;
 
 /* kernel classes reported by heat_get_timing */
