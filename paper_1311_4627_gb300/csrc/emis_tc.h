@@ -10,7 +10,7 @@ constexpr int kMaxTcGrains = 96;  // grains per launch (tensor maps travel as ke
 struct EmisTcParams {
     CUtensorMap ta[kMaxTcGrains];  // A'_g: [cells][Kp_g] operand, 128B swizzle, box 128 rows
     CUtensorMap tb[kMaxTcGrains];  // B'_g: [N][Kp_g] operand, box 256 rows
-    int ksteps[kMaxTcGrains];      // Kp_g / elements per 128-byte slice
+    int ksteps[kMaxTcGrains];      // k blocks: (split ? Kp_g / 2 : Kp_g) / elements per 128-byte slice
     int grain[kMaxTcGrains];       // grain index of slot i
     int ng;                        // grains in this launch
     int cells, N, G;
@@ -24,7 +24,7 @@ struct EmisTcParams {
 };
 
 size_t emis_tc_smem_bytes();
-cudaError_t launch_emis_tc(const EmisTcParams& p, bool tf32, int sms, cudaStream_t st);
+cudaError_t launch_emis_tc(const EmisTcParams& p, bool tf32, bool split, int sms, cudaStream_t st);
 cudaError_t launch_pack_p(int cells, int G, const int* bin_off, const double* P, long long ldP, const long long* aoff,
                           const int* kp, int split, int tf32, void* A, float* rowscale, cudaStream_t st);
 cudaError_t launch_pack_k(int N, int G, const int* bin_off, const double* K, const long long* boff, const int* kp,

@@ -143,8 +143,7 @@ static heat_status ensure_tc_mode(heat_ctx* ctx, int m, bool si, cudaStream_t st
     t.boff_h[0] = 0;
     for (int g = 0; g < G; ++g) {
         int nb = si ? ctx->nbt : ctx->bin_off[g + 1] - ctx->bin_off[g];
-        int k = (split ? 3 : 1) * nb;
-        t.kp_h[g] = (k + ke - 1) / ke * ke;
+        t.kp_h[g] = (split ? 2 : 1) * ((nb + ke - 1) / ke * ke);  // [hi | lo] parts of whole k blocks
         t.boff_h[g + 1] = t.boff_h[g] + (long long)N * t.kp_h[g];
     }
     t.order.resize(G);
@@ -197,7 +196,7 @@ static heat_status emis_tc_chunk(heat_ctx* ctx, int m, bool si, const double* P,
             if (!encode_operand(&prm.ta[i], abase, tf32, t.kp_h[g], cells, 128) ||
                 !encode_operand(&prm.tb[i], bbase, tf32, t.kp_h[g], N, 256))
                 return ctx->fail(HEAT_ECUDA, "heat_solve: cuTensorMapEncodeTiled failed");
-            prm.ksteps[i] = t.kp_h[g] / (tf32 ? 32 : 64);
+            prm.ksteps[i] = (split ? t.kp_h[g] / 2 : t.kp_h[g]) / (tf32 ? 32 : 64);
             prm.grain[i] = g;
         }
         prm.ng = ng;
@@ -212,7 +211,7 @@ static heat_status emis_tc_chunk(heat_ctx* ctx, int m, bool si, const double* P,
         prm.ldj = (long long)G * N;
         prm.j_f64 = j_f64 ? 1 : 0;
         prm.status = ctx->d_status.as<int>();
-        CKR(launch_emis_tc(prm, tf32, ctx->sms, st));
+        CKR(launch_emis_tc(prm, tf32, split, ctx->sms, st));
     }
     return HEAT_OK;
 }

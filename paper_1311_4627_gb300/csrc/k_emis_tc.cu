@@ -2,12 +2,13 @@
 //   j[c][g][n] = 2^{eP[c,g]} 2^{eK[g,n]} sum_k A'_g[c][k] B'_g[n][k]
 // with A' = the cell's P of grain g divided by its power-of-two row scale and B' = the
 // grain's Planck kernel C_abs B_lambda(T_i) [E_i >= hc/lambda] divided by its power-of-two
-// column scale, both rounded to BF16 or TF32.  In the split modes the k axis holds three
-// copies of the bins, [P_hi | P_hi | P_lo] against [K_hi | K_lo | K_hi], so one GEMM sums
-// P_hi K_hi + P_hi K_lo + P_lo K_hi with FP32 accumulation.
+// column scale, both rounded to BF16 or TF32.  In the split modes the operands hold the
+// bins twice, [P_hi | P_lo] and [K_hi | K_lo]; each stage loads the four tiles of one k block
+// once and issues P_hi K_hi + P_hi K_lo + P_lo K_hi into the FP32 accumulator.
 //
 // tcgen05 GEMM, one persistent CTA per SM, warp-specialised:
-//   warp 0 lane 0 : TMA producer (2D tiled loads, 128B swizzle) into a 4-stage smem ring
+//   warp 0 lane 0 : TMA producer (2D tiled loads, 128B swizzle) into a 192 KB smem ring
+//                   (4 stages of one A and one B tile, or 2 stages of two each when split)
 //   warp 1 lane 0 : MMA issuer (tcgen05.mma cta_group::1, M=128 N=256, FP32 in TMEM)
 //   warps 2..5    : epilogue (tcgen05.ld -> scale -> 16-byte stores, one row per lane)
 // Two TMEM accumulators (2 x 256 columns) let the epilogue of one tile overlap the MMAs
@@ -26,9 +27,11 @@ namespace heat {
 
 namespace {
 
-constexpr int kM = 128, kN = 256, kStages = 4;
-constexpr int kAStage = kM * 128;  // bytes: 128 rows x 128 B
-constexpr int kBStage = kN * 128;  // bytes: 256 rows x 128 B
+constexpr int kM = 128, kN = 256;
+constexpr int kAStage = kM * 128;  // bytes of one A tile: 128 rows x 128 B
+constexpr int kBStage = kN * 128;  // bytes of one B tile: 256 rows x 128 B
+constexpr int kRingBytes = 4 * (kAStage + kBStage);
+constexpr int kMaxStages = 4;
 constexpr int kEpiWarps = 4;
 
 }  // namespace
@@ -47,13 +50,15 @@ __device__ __forceinline__ void tile_of(const EmisTcParams& p, int t, int& gi, i
 
 }  // namespace
 
-template <bool TF32>
+template <bool TF32, bool SPLIT>
 __global__ void __launch_bounds__(192, 1) k_emis_tc(const __grid_constant__ EmisTcParams p) {
+    constexpr int NP = SPLIT ? 2 : 1;                        // operand parts (hi, lo)
+    constexpr int kStages = kMaxStages / NP;
+    constexpr int kStageBytes = NP * (kAStage + kBStage);
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* sA = smem;
-    unsigned char* sB = smem + kStages * kAStage;
-    uint64_t* bars = (uint64_t*)(sB + kStages * kBStage);
+    // stage s: A parts at s * kStageBytes + q * kAStage, B parts after the NP A tiles
+    uint64_t* bars = (uint64_t*)(smem + kRingBytes);
     // bars: full[kStages], empty[kStages], tfull[2], tempty[2], done
     uint32_t* tmem_slot = (uint32_t*)(bars + 2 * kStages + 5);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
@@ -100,14 +105,21 @@ __global__ void __launch_bounds__(192, 1) k_emis_tc(const __grid_constant__ Emis
             for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
                 int gi, mt, nt;
                 tile_of(p, t, gi, mt, nt);
+                const int khalf = p.ksteps[gi] * KE;  // elements of one operand part
                 for (int ks = 0; ks < p.ksteps[gi]; ++ks) {
                     if (!mbar_wait(b_empty + 8 * stage, phase ^ 1, abort_flag)) {
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(b_full + 8 * stage, kAStage + kBStage);
-                    tma_load_2d(smem_u32(sA + stage * kAStage), &p.ta[gi], ks * KE, mt * kM, b_full + 8 * stage);
-                    tma_load_2d(smem_u32(sB + stage * kBStage), &p.tb[gi], ks * KE, nt * kN, b_full + 8 * stage);
+                    mbar_expect_tx(b_full + 8 * stage, kStageBytes);
+                    unsigned char* sb = smem + stage * kStageBytes;
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) {
+                        tma_load_2d(smem_u32(sb + q * kAStage), &p.ta[gi], q * khalf + ks * KE, mt * kM,
+                                    b_full + 8 * stage);
+                        tma_load_2d(smem_u32(sb + NP * kAStage + q * kBStage), &p.tb[gi], q * khalf + ks * KE,
+                                    nt * kN, b_full + 8 * stage);
+                    }
                     last_phase[stage] = (int)phase;
                     if (++stage == kStages) {
                         stage = 0;
@@ -148,11 +160,20 @@ __global__ void __launch_bounds__(192, 1) k_emis_tc(const __grid_constant__ Emis
                         break;
                     }
                     tc_fence_after();
-                    const uint64_t a0 = sdesc(smem_u32(sA + stage * kAStage));
-                    const uint64_t b0 = sdesc(smem_u32(sB + stage * kBStage));
+                    unsigned char* sb = smem + stage * kStageBytes;
+                    const uint64_t a_hi = sdesc(smem_u32(sb));
+                    const uint64_t b_hi = sdesc(smem_u32(sb + NP * kAStage));
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk)
-                        umma<TF32>(d, a0 + 2 * kk, b0 + 2 * kk, id, (ks | kk) != 0 ? 1u : 0u);
+                        umma<TF32>(d, a_hi + 2 * kk, b_hi + 2 * kk, id, (ks | kk) != 0 ? 1u : 0u);
+                    if constexpr (SPLIT) {
+                        const uint64_t a_lo = sdesc(smem_u32(sb + kAStage));
+                        const uint64_t b_lo = sdesc(smem_u32(sb + NP * kAStage + kBStage));
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) umma<TF32>(d, a_hi + 2 * kk, b_lo + 2 * kk, id, 1u);
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) umma<TF32>(d, a_lo + 2 * kk, b_hi + 2 * kk, id, 1u);
+                    }
                     umma_commit(b_empty + 8 * stage);
                     if (++stage == kStages) {
                         stage = 0;
@@ -253,33 +274,33 @@ __global__ void __launch_bounds__(192, 1) k_emis_tc(const __grid_constant__ Emis
     }
 }
 
-size_t emis_tc_smem_bytes() {
-    return 1024 + (size_t)kStages * (kAStage + kBStage) + (2 * kStages + 5) * 8 + 16;
-}
+size_t emis_tc_smem_bytes() { return 1024 + (size_t)kRingBytes + (2 * kMaxStages + 5) * 8 + 16; }
 
-cudaError_t launch_emis_tc(const EmisTcParams& p, bool tf32, int sms, cudaStream_t st) {
-    int total = p.ng * p.mtiles * p.ntiles;
-    if (total <= 0) return cudaSuccess;
-    size_t smem = emis_tc_smem_bytes();
-    int grid = total < sms ? total : sms;
+template <bool TF32, bool SPLIT>
+static cudaError_t launch_emis_tc_t(const EmisTcParams& p, int grid, size_t smem, cudaStream_t st) {
     // the shared-memory opt-in is set once per device (not a stream operation, but kept out
     // of the launch path so that a solve can be captured into a CUDA graph)
-    static bool attr_set[2][64] = {};
+    static bool attr_set[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!attr_set[tf32][dev]) {
-        e = tf32 ? cudaFuncSetAttribute(k_emis_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                 : cudaFuncSetAttribute(k_emis_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (!attr_set[dev]) {
+        e = cudaFuncSetAttribute(k_emis_tc<TF32, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr_set[tf32][dev] = true;
+        attr_set[dev] = true;
     }
-    if (tf32)
-        k_emis_tc<true><<<grid, 192, smem, st>>>(p);
-    else
-        k_emis_tc<false><<<grid, 192, smem, st>>>(p);
+    k_emis_tc<TF32, SPLIT><<<grid, 192, smem, st>>>(p);
     return cudaGetLastError();
+}
+
+cudaError_t launch_emis_tc(const EmisTcParams& p, bool tf32, bool split, int sms, cudaStream_t st) {
+    int total = p.ng * p.mtiles * p.ntiles;
+    if (total <= 0) return cudaSuccess;
+    size_t smem = emis_tc_smem_bytes();
+    int grid = total < sms ? total : sms;
+    if (tf32) return split ? launch_emis_tc_t<true, true>(p, grid, smem, st) : launch_emis_tc_t<true, false>(p, grid, smem, st);
+    return split ? launch_emis_tc_t<false, true>(p, grid, smem, st) : launch_emis_tc_t<false, false>(p, grid, smem, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -331,7 +352,7 @@ __device__ __forceinline__ float scaled_to_f32(double p, int e) {
 }
 
 // A' for one chunk: one warp per (cell, grain).  P [cells][nbt] FP64 in, per grain
-// A'_g [cells][Kp_g] (BF16 or TF32-in-FP32) out, and rowscale [cells][G] = 2^e with e
+// A'_g [cells][Kp_g] (BF16 or TF32-in-FP32; [P_hi | P_lo] when split) out, and rowscale [cells][G] = 2^e with e
 // the smallest exponent for which the row's largest P divided by 2^e is below 1.
 __global__ void k_pack_p(int cells, int G, const int* __restrict__ bin_off, const double* __restrict__ P,
                          long long ldP, const long long* __restrict__ aoff, const int* __restrict__ kp, int split,
@@ -349,36 +370,28 @@ __global__ void k_pack_p(int cells, int G, const int* __restrict__ bin_off, cons
     // frexp exponent of the maximum: m = f 2^e, f in [0.5, 1); 0 for an all-zero row
     const int e = mh >= 0x00100000u ? (int)(mh >> 20) - 1022 : 0;
     if (lane == 0) rowscale[(size_t)c * G + g] = ldexpf(1.0f, e);
-    int K = kp[g];
+    const int K = kp[g], half = split ? K / 2 : K;  // [hi | lo], each part half wide
     if (tf32) {
         float* row = (float*)A + aoff[g] + (size_t)c * K;
-        for (int i = lane; i < nb; i += 32) {
-            const float v = scaled_to_f32(pr[i], e);
+        for (int i = lane; i < half; i += 32) {
+            const float v = i < nb ? scaled_to_f32(pr[i], e) : 0.0f;
             const float hi = tf32_rn(v);
             row[i] = hi;
-            if (split) {
-                row[nb + i] = hi;
-                row[2 * nb + i] = tf32_rn(v - hi);
-            }
+            if (split) row[half + i] = tf32_rn(v - hi);
         }
-        for (int i = (split ? 3 : 1) * nb + lane; i < K; i += 32) row[i] = 0.0f;
     } else {
         uint16_t* row = (uint16_t*)A + aoff[g] + (size_t)c * K;
-        for (int i = lane; i < nb; i += 32) {
-            const float v = scaled_to_f32(pr[i], e);
+        for (int i = lane; i < half; i += 32) {
+            const float v = i < nb ? scaled_to_f32(pr[i], e) : 0.0f;
             const uint16_t hi = bf16_rn(v);
             row[i] = hi;
-            if (split) {
-                row[nb + i] = hi;
-                row[2 * nb + i] = bf16_rn(v - bf16_f(hi));
-            }
+            if (split) row[half + i] = bf16_rn(v - bf16_f(hi));
         }
-        for (int i = (split ? 3 : 1) * nb + lane; i < K; i += 32) row[i] = 0;
     }
 }
 
 // B' of every grain: one thread per (grain, wavelength).  K [nbt][N] FP64 in, per grain
-// B'_g [N][Kp_g] with parts [K_hi | K_lo | K_hi] (split) or [K_hi], and colscale [G][N].
+// B'_g [N][Kp_g] with parts [K_hi | K_lo] (split) or [K_hi], and colscale [G][N].
 __global__ void k_pack_k(int N, int G, const int* __restrict__ bin_off, const double* __restrict__ K,
                          const long long* __restrict__ boff, const int* __restrict__ kp, int split, int tf32,
                          void* __restrict__ B, float* __restrict__ colscale) {
@@ -391,31 +404,23 @@ __global__ void k_pack_k(int N, int G, const int* __restrict__ bin_off, const do
     int e = scale_exp(m);
     double inv = ldexp(1.0, -e);
     colscale[(size_t)g * N + n] = ldexpf(1.0f, e);
-    int Kp = kp[g];
+    const int Kp = kp[g], half = split ? Kp / 2 : Kp;  // [K_hi | K_lo], each part half wide
     if (tf32) {
         float* row = (float*)B + boff[g] + (size_t)n * Kp;
-        for (int i = 0; i < nb; ++i) {
-            float hi, lo;
-            split_tf32(K[(size_t)(off + i) * N + n] * inv, hi, lo);
+        for (int i = 0; i < half; ++i) {
+            float hi = 0.0f, lo = 0.0f;
+            if (i < nb) split_tf32(K[(size_t)(off + i) * N + n] * inv, hi, lo);
             row[i] = hi;
-            if (split) {
-                row[nb + i] = lo;
-                row[2 * nb + i] = hi;
-            }
+            if (split) row[half + i] = lo;
         }
-        for (int i = (split ? 3 : 1) * nb; i < Kp; ++i) row[i] = 0.0f;
     } else {
         uint16_t* row = (uint16_t*)B + boff[g] + (size_t)n * Kp;
-        for (int i = 0; i < nb; ++i) {
-            uint16_t hi, lo;
-            split_bf16(K[(size_t)(off + i) * N + n] * inv, hi, lo);
+        for (int i = 0; i < half; ++i) {
+            uint16_t hi = 0, lo = 0;
+            if (i < nb) split_bf16(K[(size_t)(off + i) * N + n] * inv, hi, lo);
             row[i] = hi;
-            if (split) {
-                row[nb + i] = lo;
-                row[2 * nb + i] = hi;
-            }
+            if (split) row[half + i] = lo;
         }
-        for (int i = (split ? 3 : 1) * nb; i < Kp; ++i) row[i] = 0;
     }
 }
 
