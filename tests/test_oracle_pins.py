@@ -380,12 +380,13 @@ def test_emissivity_integrates_to_cooling_power():
         assert abs(integ / want - 1.0) < 2e-4, (i, integ, want)
 
 
-def test_large_grain_reaches_thermal_equilibrium():
+@pytest.mark.parametrize("radius", [0.25e-4, 1.0e-4])
+def test_large_grain_reaches_thermal_equilibrium(radius):
     """Undiluted blackbody at T_rad heats a large grain to T_rad (Kirchhoff):
     mode of P within one bin of T_rad, and j near the peak ~ C B_lambda(T_rad)."""
     lam = W.wavelength_grid(512)
     T_rad = 120.0
-    wl = W.custom(lam, [1.0e-4], ["carbonaceous"], [512], W.blackbody_field(lam, T_rad)[None, :])
+    wl = W.custom(lam, [radius], ["carbonaceous"], [512], W.blackbody_field(lam, T_rad)[None, :])
     Cf = oracle.grain_cooling(wl)
     P, j, led, st = oracle.solve_batch(wl, Cf, want_ledger=True)
     assert st == oracle.OK
@@ -400,6 +401,37 @@ def test_large_grain_reaches_thermal_equilibrium():
     npk = int(np.argmax(bb))
     assert abs(j[0, 0, npk] / bb[npk] - 1.0) < 0.02
     assert abs(led[0, 0, 0] / led[0, 0, 1] - 1.0) < 1e-10
+
+
+@pytest.mark.parametrize("radius", [0.25e-4, 1.0e-4])
+def test_large_grain_in_a_diluted_field_sits_at_the_balance_temperature(radius):
+    """A large grain in a diluted 5000 K blackbody: T_eq from c int u C dlambda =
+    4 pi int C B_lambda(T_eq) dlambda (trapezoid sums on the grid, root by brentq, written
+    here independently of the oracle); the distribution's mean log T lies within one bin of
+    T_eq and j at its peak is C B_lambda(T_eq) within 2 %."""
+    from scipy import optimize
+
+    lam = W.wavelength_grid(512)
+    u = 1e-13 * W.blackbody_field(lam, 5000.0)
+    wl = W.custom(lam, [radius], ["carbonaceous"], [512], u[None, :])
+    C = wl.cabs[0]
+    c, h, k = 2.99792458e10, 6.62607015e-27, 1.380649e-16
+
+    def bl(T):
+        with np.errstate(over="ignore"):
+            return 2 * h * c * c / lam**5 / np.expm1(h * c / (lam * k * T))
+
+    absorbed = c * np.trapezoid(u * C, lam)
+    T_eq = optimize.brentq(lambda T: 4 * math.pi * np.trapezoid(C * bl(T), lam) - absorbed, 3.0, 2000.0, xtol=1e-10)
+    P, j, _, st = oracle.solve_batch(wl, oracle.grain_cooling(wl))
+    assert st == oracle.OK
+    Tg = wl.T
+    dlnT = math.log(Tg[1] / Tg[0])
+    Tmean = math.exp(float(np.sum(P[0] * np.log(Tg))))
+    assert abs(math.log(Tmean / T_eq)) <= dlnT, (Tmean, T_eq)
+    bb = C * bl(T_eq)
+    npk = int(np.argmax(bb))
+    assert abs(j[0, 0, npk] / bb[npk] - 1.0) < 0.02, (j[0, 0, npk], bb[npk])
 
 
 def test_size_integration_is_weighted_sum(c1):
