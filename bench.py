@@ -176,9 +176,16 @@ def oracle_sample(wl, n_cells, Cf=None):
     P, j, _, st = oracle.solve_batch(sub, Cf)
     dt = time.perf_counter() - t0
     spectra = n_cells * wl.n_grains
+    # one core: the first cell's spectra on a single thread
+    sub1 = W.field_subset(wl, np.arange(1))
+    t1 = time.perf_counter()
+    oracle.solve_batch(sub1, Cf, n_threads=1)
+    dt1 = time.perf_counter() - t1
     return {"value": spectra / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{n_cells} cells x {wl.n_grains} grains of the workload ({spectra} spectra, "
                       f"{dt:.1f} s, OpenMP over spectra; cooling set-up untimed)",
+            "one_core": {"value": wl.n_grains / dt1, "unit": UNIT,
+                         "sample": f"1 cell x {wl.n_grains} grains on one thread ({dt1:.1f} s)"},
             "status": st}, P, j, Cf
 
 
@@ -546,7 +553,19 @@ def main():
         heat.heat_surrogate_fit_norm(ctx, Xt, Yt, ns, sh)
         hist = heat.heat_surrogate_train(ctx, Xt, Yt, ns, 8192, args.sur_epochs, 1e-3, seed=9, stream=sh)
         train_s = time.perf_counter() - t0
-        del Xt, Yt, ut
+        # inference on the ns training samples (2^20 by default: one (field, grain) each)
+        lnp_t = torch.zeros(ns, dtype=torch.float32, device=dev)
+        lnj_t = torch.empty(ns, N, dtype=torch.float32, device=dev)
+        sp_t = torch.empty(ns, dtype=torch.float32, device=dev)
+        heat.heat_surrogate_predict(ctx, Xt[:8192], lnp_t[:8192], 8192, lnj_t[:8192], sp_t[:8192], sh)
+        e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e_a.record(stream)
+        heat.heat_surrogate_predict(ctx, Xt, lnp_t, ns, lnj_t, sp_t, sh)
+        e_b.record(stream)
+        torch.cuda.synchronize(dev)
+        infer_ms = e_a.elapsed_time(e_b)
+        del Xt, Yt, ut, lnp_t, lnj_t, sp_t
         heat.heat_set_fields(ctx, cells, u, heat.HEAT_F64, 1, sh)
         fo = opts_for("mixed")
         for _ in range(2):
@@ -598,6 +617,9 @@ def main():
                               "precision": "MLP ensemble (4 x 128-512x4-1024, BF16 tensor cores) + mixed-path fallback",
                               "fallback_cells": nfb, "fallback_fraction": nfb / cells, "tol_spread": args.sur_tol,
                               "network_alone": raw,
+                              "inference_samples": {"samples": ns, "ms": infer_ms,
+                                                    "samples_per_s": ns / (infer_ms / 1e3),
+                                                    "flop_per_sample": 4 * 2 * (128 * 512 + 3 * 512 * 512 + 512 * N)},
                               "training": {"samples": ns, "epochs": args.sur_epochs, "data_s": round(gen_s, 2),
                                            "train_s": round(train_s, 2), "loss_first": float(hist[0]),
                                            "loss_last": float(hist[-1])}}
@@ -607,7 +629,7 @@ def main():
     # oracle on the host cores (rank 0, N = 1), its outputs double as the error reference
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb, P_ref, j_ref, Cf = oracle_sample(wl, args.oracle_cells)
-        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "one_core")}
         nsub = args.oracle_cells
         for path in [q for q in paths if q in PATHS]:
             P_sub = torch.empty(nsub, nbt, dtype=torch.float64, device=dev)

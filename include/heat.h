@@ -252,7 +252,10 @@ heat_status heat_surrogate_predict(heat_ctx* ctx, const float* X, const float* l
  * j_out FP32 device [cells][n_grains][n_lambda] = exp(ln j) of the ensemble; every cell with
  * a grain whose spread exceeds tol is solved again by heat_solve with fallback_opts (its
  * exact/mixed precision choices; per-grain FP32 device j required) and overwritten.
- * *n_fallback = cells solved exactly.  Synchronous. */
+ * fallback_opts->ledger_out (device FP64 [cells][n_grains][2], or NULL) receives the energy
+ * check of every spectrum returned: for the surrogate's, [absorbed power c int u C dlambda,
+ * 4 pi int j dlambda on the grid (trapezoid)]; for the cells solved exactly, heat_solve's
+ * ledger.  *n_fallback = cells solved exactly.  Synchronous. */
 heat_status heat_solve_surrogate(heat_ctx* ctx, const heat_opts* fallback_opts, float tol, float* j_out,
                                  int* n_fallback, void* cuda_stream);
 

@@ -1,6 +1,7 @@
 // Kernels of the learned surrogate (an MLP ensemble over the binned field):
 //   k_gemm_bf16   tcgen05 GEMM  C[z] = A[z] . B[z]^T (+ bias), BF16 operands K-major,
-//                 FP32 accumulation in TMEM, FP32 and/or BF16 outputs; z = ensemble member
+//                 FP32 accumulation in TMEM, FP32 and/or BF16 (optionally GELU) outputs;
+//                 z = ensemble member
 //   elementwise   GELU forward/backward, transposes, column sums, masked MSE, Adam
 // The GEMM reuses the warp-specialised layout of the emissivity kernel: warp 0 issues
 // TMA loads into a 6-stage ring, warp 1 issues tcgen05.mma (M = 128, N = 128), warps 2..5
@@ -23,7 +24,6 @@ namespace {
 constexpr int gM = 128, gN = 128, gStages = 6;
 constexpr int gAStage = gM * 128, gBStage = gN * 128;
 constexpr int gEpiWarps = 4;
-constexpr int gEpiTile = 32 * 33;
 
 __device__ __forceinline__ void gtile(const GemmTcParams& p, int t, int& z, int& mt, int& nt) {
     int per = p.mtiles * p.ntiles;
@@ -35,14 +35,15 @@ __device__ __forceinline__ void gtile(const GemmTcParams& p, int t, int& z, int&
 
 }  // namespace
 
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+
 __global__ void __launch_bounds__(192, 1) k_gemm_bf16(const __grid_constant__ GemmTcParams p) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* sA = smem;
     unsigned char* sB = smem + gStages * gAStage;
     uint64_t* bars = (uint64_t*)(sB + gStages * gBStage);
-    float* epi = (float*)(bars + 2 * gStages + 5);
-    uint32_t* tmem_slot = (uint32_t*)(epi + gEpiWarps * gEpiTile);
+    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * gStages + 5);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -155,8 +156,9 @@ __global__ void __launch_bounds__(192, 1) k_gemm_bf16(const __grid_constant__ Ge
                 if (mbar_try(b_done, 0)) break;
         }
     } else {
+        // epilogue: lane = row of the tile; each chunk of 32 columns gets its bias (broadcast
+        // loads), optional GELU for the BF16 output, and 16-byte stores of the row's run
         const int q = warp & 3;
-        float* st = epi + (warp - 2) * gEpiTile;
         int acc = 0;
         uint32_t acc_phase = 0;
         for (int t = blockIdx.x; t < total; t += gridDim.x) {
@@ -171,30 +173,77 @@ __global__ void __launch_bounds__(192, 1) k_gemm_bf16(const __grid_constant__ Ge
                 break;
             }
             tc_fence_after();
-            const int row0 = mt * gM + q * 32;
+            const int row = mt * gM + q * 32 + lane;
+            const bool rok = row < p.M;
             float* C = p.c[z];
             __nv_bfloat16* Cb = p.cb[z];
             const float* bias = p.bias[z];
             for (int c = 0; c < gN / 32; ++c) {
                 uint32_t v[32];
                 tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * gN + c * 32), v);
+                const int col0 = nt * gN + c * 32;
+                if (col0 >= p.N) continue;
+                float* crow = C ? C + (size_t)(rok ? row : 0) * p.ldc + col0 : nullptr;
+                __nv_bfloat16* brow = Cb ? Cb + (size_t)(rok ? row : 0) * p.ldcb + col0 : nullptr;
+                const bool fast =
+                    col0 + 32 <= p.N &&
+                    __all_sync(0xffffffffu, ((uintptr_t)crow & 15u) == 0 && ((uintptr_t)brow & 15u) == 0 &&
+                                                (!bias || ((uintptr_t)(bias + col0) & 15u) == 0));
+                if (fast) {
+                    float val[32];
 #pragma unroll
-                for (int i = 0; i < 32; ++i) st[lane * 33 + i] = __uint_as_float(v[i]);
-                __syncwarp();
-                const int col = nt * gN + c * 32 + lane;
-                const float bv = (bias && col < p.N) ? bias[col] : 0.0f;
-                for (int r = 0; r < 32; ++r) {
-                    const int row = row0 + r;
-                    if (row < p.M && col < p.N) {
-                        float val = st[r * 33 + lane] + bv;
-                        if (C) {
-                            float* o = C + (size_t)row * p.ldc + col;
-                            *o = p.accumulate ? *o + val : val;
+                    for (int k = 0; k < 8; ++k) {
+                        const float4 b4 = bias ? ((const float4*)(bias + col0))[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        val[4 * k] = __uint_as_float(v[4 * k]) + b4.x;
+                        val[4 * k + 1] = __uint_as_float(v[4 * k + 1]) + b4.y;
+                        val[4 * k + 2] = __uint_as_float(v[4 * k + 2]) + b4.z;
+                        val[4 * k + 3] = __uint_as_float(v[4 * k + 3]) + b4.w;
+                    }
+                    if (rok && crow) {
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            float4 o = make_float4(val[4 * k], val[4 * k + 1], val[4 * k + 2], val[4 * k + 3]);
+                            if (p.accumulate) {
+                                const float4 old = ((const float4*)crow)[k];
+                                o.x += old.x;
+                                o.y += old.y;
+                                o.z += old.z;
+                                o.w += old.w;
+                            }
+                            ((float4*)crow)[k] = o;
                         }
-                        if (Cb) Cb[(size_t)row * p.ldcb + col] = __float2bfloat16_rn(val);
+                    }
+                    if (rok && brow) {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            uint32_t w[4];
+#pragma unroll
+                            for (int h = 0; h < 4; ++h) {
+                                float x0 = val[8 * k + 2 * h], x1 = val[8 * k + 2 * h + 1];
+                                if (p.act) {
+                                    x0 = gelu(x0);
+                                    x1 = gelu(x1);
+                                }
+                                const __nv_bfloat162 pr = __floats2bfloat162_rn(x0, x1);
+                                w[h] = *(const uint32_t*)&pr;
+                            }
+                            ((uint4*)brow)[k] = make_uint4(w[0], w[1], w[2], w[3]);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const int col = col0 + i;
+                        if (rok && col < p.N) {
+                            const float val = __uint_as_float(v[i]) + (bias ? bias[col] : 0.0f);
+                            if (C) {
+                                float* o = C + (size_t)row * p.ldc + col;
+                                *o = p.accumulate ? *o + val : val;
+                            }
+                            if (Cb) Cb[(size_t)row * p.ldcb + col] = __float2bfloat16_rn(p.act ? gelu(val) : val);
+                        }
                     }
                 }
-                __syncwarp();
             }
             tc_fence_before();
             __syncwarp();
@@ -214,7 +263,7 @@ __global__ void __launch_bounds__(192, 1) k_gemm_bf16(const __grid_constant__ Ge
 }
 
 size_t gemm_bf16_smem_bytes() {
-    return 1024 + (size_t)gStages * (gAStage + gBStage) + (2 * gStages + 5) * 8 + gEpiWarps * gEpiTile * 4 + 16;
+    return 1024 + (size_t)gStages * (gAStage + gBStage) + (2 * gStages + 5) * 8 + 16;
 }
 
 cudaError_t launch_gemm_bf16(const GemmTcParams& p, int sms, cudaStream_t st) {
@@ -230,7 +279,6 @@ cudaError_t launch_gemm_bf16(const GemmTcParams& p, int sms, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // elementwise kernels
 
-__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float x) {
     const float cdf = 0.5f * (1.0f + erff(x * 0.70710678118654752f));
     const float pdf = 0.39894228040143268f * __expf(-0.5f * x * x);

@@ -18,6 +18,7 @@ struct GemmTcParams {
     int M, N, K, nz;               // K a multiple of 64
     int mtiles, ntiles;
     int accumulate;                // 1: c += result
+    int act;                       // 1: the BF16 output is GELU of the result (the FP32 output is not)
     int* status;
 };
 

@@ -51,6 +51,9 @@ struct Surrogate {
     // work buffers for one member and a batch of B rows
     int B = 0;
     DevBuf Xn, Tn, Z[kLayers], Act[kLayers], dYb, dXf, dZb, T1, T2, loss, ens_mean, ens_m2, tb, cnt;
+    // inference of all members at once: hidden activations (ping-pong) and outputs per member
+    int IB = 0;
+    DevBuf H[8][2], Zo[8];
 };
 
 void surrogate_free(Surrogate* s) {
@@ -62,6 +65,11 @@ void surrogate_free(Surrogate* s) {
     for (int l = 0; l < kLayers; ++l) {
         s->Z[l].release();
         s->Act[l].release();
+    }
+    for (int m = 0; m < 8; ++m) {
+        s->H[m][0].release();
+        s->H[m][1].release();
+        s->Zo[m].release();
     }
     delete s;
 }
@@ -255,6 +263,59 @@ __global__ void k_ens_final(int rows, int N, int members, const float* __restric
     if (threadIdx.x == 0) spread[s] = red[0];
 }
 
+// Ensemble statistics of one sample per block from the members' standardised outputs
+// Zo[m][s][n]: ln j = mean over members + ln P_abs; spread = the largest standard deviation
+// (members - 1 in the denominator) of ln j over the predicted emission (mean within 1e-6 of
+// its peak).
+struct ZoPtrs {
+    const float* z[8];
+};
+__global__ void k_ens_stats(int rows, int N, int members, ZoPtrs zo, const float* __restrict__ ym,
+                            const float* __restrict__ ys, const float* __restrict__ lnp, float* __restrict__ lnj,
+                            float* __restrict__ spread) {
+    __shared__ float red[256];
+    const int s = blockIdx.x;
+    if (s >= rows) return;
+    float* out = lnj + (size_t)s * N;
+    float mx = -INFINITY;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        float sum = 0.0f;
+        for (int m = 0; m < members; ++m) sum += zo.z[m][(size_t)s * N + n] * ys[n] + ym[n];
+        const float mu = sum / (float)members;
+        out[n] = mu;  // the mean for now; ln P_abs is added below
+        mx = fmaxf(mx, mu);
+    }
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + k]);
+        __syncthreads();
+    }
+    const float thr = red[0] + logf(kMaskRel);
+    __syncthreads();
+    const float lp = lnp[s];
+    float sp = 0.0f;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        const float mu = out[n];
+        if (mu > thr && members > 1) {
+            float ss = 0.0f;
+            for (int m = 0; m < members; ++m) {
+                const float d = zo.z[m][(size_t)s * N + n] * ys[n] + ym[n] - mu;
+                ss += d * d;
+            }
+            sp = fmaxf(sp, sqrtf(ss / (float)(members - 1)));
+        }
+        out[n] = mu + lp;
+    }
+    red[threadIdx.x] = sp;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + k]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) spread[s] = red[0];
+}
+
 // j = exp(ln j) for the surrogate output; flags the cells with any grain above tol.
 __global__ void k_sur_output(long long n, int N, int G, const float* __restrict__ lnj, const float* __restrict__ spread,
                              float tol, float* __restrict__ j, int* __restrict__ cell_flag) {
@@ -263,6 +324,32 @@ __global__ void k_sur_output(long long n, int N, int G, const float* __restrict_
     j[i] = __expf(lnj[i]);
     long long s = i / N;
     if (i % N == 0 && spread[s] > tol) cell_flag[s / G] = 1;
+}
+
+// Energy check of surrogate spectra, one warp per (cell, grain) sample: [absorbed power
+// P_abs = exp(lnp), emitted power 4 pi int j dlambda by the trapezoid rule on the grid].
+__global__ void k_sur_energy(long long samples, int N, const double* __restrict__ lam, const float* __restrict__ j,
+                             const float* __restrict__ lnp, double* __restrict__ ledger) {
+    const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= samples) return;
+    const float* js = j + (size_t)w * N;
+    double acc = 0.0;
+    for (int n = lane; n < N - 1; n += 32) acc += 0.5 * ((double)js[n] + (double)js[n + 1]) * (lam[n + 1] - lam[n]);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+        ledger[2 * w] = exp((double)lnp[w]);
+        ledger[2 * w + 1] = 4.0 * 3.14159265358979323846 * acc;
+    }
+}
+
+// Ledger rows of the cells solved exactly, back to their places.
+__global__ void k_fallback_ledger(int n, int row, const int* __restrict__ list, const double* __restrict__ src,
+                                  double* __restrict__ dst) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)n * row) return;
+    int r = (int)(i / row), k = (int)(i % row);
+    dst[(size_t)list[r] * row + k] = src[i];
 }
 
 // Compact flagged cells into a list (order-independent: positions by atomic counter,
@@ -326,7 +413,7 @@ bool encode_bf16(CUtensorMap* m, const void* base, long long rows, long long k) 
 
 // C[M x N] = A[M x K] . B[N x K]^T (+ bias): both operands BF16 row-major (K contiguous).
 heat_status gemm(heat_ctx* ctx, int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* B, float* C,
-                 __nv_bfloat16* Cb, const float* bias, int accumulate, cudaStream_t st) {
+                 __nv_bfloat16* Cb, const float* bias, int accumulate, cudaStream_t st, int act = 0) {
     GemmTcParams p;
     std::memset(&p, 0, sizeof(p));
     if (!encode_bf16(&p.ta[0], A, M, K) || !encode_bf16(&p.tb[0], B, N, K))
@@ -343,10 +430,15 @@ heat_status gemm(heat_ctx* ctx, int M, int N, int K, const __nv_bfloat16* A, con
     p.mtiles = (M + 127) / 128;
     p.ntiles = (N + 127) / 128;
     p.accumulate = accumulate;
+    p.act = act;
     p.status = ctx->d_status.as<int>();
     SCK(launch_gemm_bf16(p, ctx->sms, st));
     return HEAT_OK;
 }
+
+// One layer of every member in one launch (problem z = member): C[z] = A[z] W[z]^T + b[z].
+heat_status gemm_members(heat_ctx* ctx, Surrogate* s, int l, int M, const __nv_bfloat16* const* A, float* const* C,
+                         __nv_bfloat16* const* Cb, int act, cudaStream_t st);
 
 heat_status ensure_batch(heat_ctx* ctx, Surrogate* s, int B) {
     if (s->B >= B) return HEAT_OK;
@@ -372,15 +464,43 @@ __nv_bfloat16* WTb(Surrogate* s, int m, int l) { return s->wtb.as<__nv_bfloat16>
 float* Pm(Surrogate* s, int m) { return s->params.as<float>() + (size_t)m * s->nparams; }
 float* Gm(Surrogate* s, int m) { return s->grads.as<float>() + (size_t)m * s->nparams; }
 
+heat_status gemm_members(heat_ctx* ctx, Surrogate* s, int l, int M, const __nv_bfloat16* const* A, float* const* C,
+                         __nv_bfloat16* const* Cb, int act, cudaStream_t st) {
+    const int N = s->Nout[l], K = s->Kin[l];
+    GemmTcParams p;
+    std::memset(&p, 0, sizeof(p));
+    for (int m = 0; m < s->members; ++m) {
+        if (!encode_bf16(&p.ta[m], A[m], M, K) || !encode_bf16(&p.tb[m], Wb(s, m, l), N, K))
+            return ctx->fail(HEAT_ECUDA, "surrogate: cuTensorMapEncodeTiled failed");
+        p.c[m] = C[m];
+        p.cb[m] = Cb[m];
+        p.bias[m] = Pm(s, m) + s->boff[l];
+    }
+    p.ldc = N;
+    p.ldcb = N;
+    p.M = M;
+    p.N = N;
+    p.K = K;
+    p.nz = s->members;
+    p.mtiles = (M + 127) / 128;
+    p.ntiles = (N + 127) / 128;
+    p.act = act;
+    p.status = ctx->d_status.as<int>();
+    SCK(launch_gemm_bf16(p, ctx->sms, st));
+    return HEAT_OK;
+}
+
 // Forward of member m on the normalised batch in s->Act[0] (rows B): Z[l] FP32, Act[l+1] BF16;
 // the output Z[kLayers-1] is the standardised prediction.
 heat_status forward(heat_ctx* ctx, Surrogate* s, int m, int B, cudaStream_t st) {
+    // hidden layers keep Z (FP32, for the backward pass) and write GELU(Z) as the next BF16
+    // input from the GEMM epilogue
     for (int l = 0; l < kLayers; ++l) {
+        const bool hidden = l + 1 < kLayers;
         heat_status h = gemm(ctx, B, s->Nout[l], s->Kin[l], s->Act[l].as<__nv_bfloat16>(), Wb(s, m, l),
-                             s->Z[l].as<float>(), nullptr, Pm(s, m) + s->boff[l], 0, st);
+                             s->Z[l].as<float>(), hidden ? s->Act[l + 1].as<__nv_bfloat16>() : nullptr,
+                             Pm(s, m) + s->boff[l], 0, st, hidden ? 1 : 0);
         if (h != HEAT_OK) return h;
-        if (l + 1 < kLayers)
-            SCK(launch_gelu_fwd((long long)B * s->Nout[l], s->Z[l].as<float>(), s->Act[l + 1].as<__nv_bfloat16>(), st));
     }
     return HEAT_OK;
 }
@@ -610,20 +730,37 @@ heat_status heat_surrogate_predict(heat_ctx* ctx, const float* X, const float* l
     const int B = 16384;
     heat_status h = ensure_batch(ctx, s, B);
     if (h != HEAT_OK) return h;
+    // all members at once: per-member hidden activations (ping-pong) and standardised outputs
+    if (s->IB < B) {
+        bool ok = true;
+        for (int m = 0; m < s->members; ++m) {
+            ok = ok && !s->H[m][0].ensure(2 * (size_t)B * kHidden) && !s->H[m][1].ensure(2 * (size_t)B * kHidden);
+            ok = ok && !s->Zo[m].ensure(4 * (size_t)B * s->N);
+        }
+        if (!ok) return ctx->fail(HEAT_ENOMEM, "surrogate: inference buffers");
+        s->IB = B;
+    }
     for (long long b0 = 0; b0 < n; b0 += B) {
         int cnt = (int)std::min<long long>(B, n - b0);
         k_gather_norm<<<cnt, 128, 0, st>>>(cnt, cnt, s->N, nullptr, X + (size_t)b0 * kFeat, nullptr,
                                            s->xmean.as<float>(), s->xstd.as<float>(), s->ymean.as<float>(),
                                            s->ystd.as<float>(), s->Act[0].as<__nv_bfloat16>(), nullptr, nullptr);
         int rows = (cnt + 63) / 64 * 64;  // GEMM rows in whole tiles of 64 (extra rows are ignored)
-        for (int m = 0; m < s->members; ++m) {
-            if ((h = forward(ctx, s, m, rows, st)) != HEAT_OK) return h;
-            long long ne = (long long)cnt * s->N;
-            k_ens_acc<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(ne, s->N, m, s->Z[kLayers - 1].as<float>(),
-                                                                     s->ymean.as<float>(), s->ystd.as<float>(),
-                                                                     s->ens_mean.as<float>(), s->ens_m2.as<float>());
+        const __nv_bfloat16* A[8];
+        __nv_bfloat16* Hb[8];
+        float* Zo[8];
+        for (int l = 0; l < kLayers; ++l) {
+            const bool hidden = l + 1 < kLayers;
+            for (int m = 0; m < s->members; ++m) {
+                A[m] = l == 0 ? s->Act[0].as<__nv_bfloat16>() : s->H[m][(l - 1) & 1].as<__nv_bfloat16>();
+                Hb[m] = hidden ? s->H[m][l & 1].as<__nv_bfloat16>() : nullptr;
+                Zo[m] = hidden ? nullptr : s->Zo[m].as<float>();
+            }
+            if ((h = gemm_members(ctx, s, l, rows, A, Zo, Hb, hidden ? 1 : 0, st)) != HEAT_OK) return h;
         }
-        k_ens_final<<<cnt, 256, 0, st>>>(cnt, s->N, s->members, s->ens_mean.as<float>(), s->ens_m2.as<float>(),
+        ZoPtrs zp{};
+        for (int m = 0; m < s->members; ++m) zp.z[m] = s->Zo[m].as<float>();
+        k_ens_stats<<<cnt, 256, 0, st>>>(cnt, s->N, s->members, zp, s->ymean.as<float>(), s->ystd.as<float>(),
                                          lnp + b0, lnj + (size_t)b0 * s->N, spread + b0);
         SCK(cudaGetLastError());
     }
@@ -774,6 +911,9 @@ heat_status heat_solve_surrogate(heat_ctx* ctx, const heat_opts* fallback_opts, 
     k_sur_output<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(ne, N, G, lnj.as<float>(), spread.as<float>(), tol, j_out,
                                                               flag.as<int>());
     k_compact<<<(count + 255) / 256, 256, 0, st>>>(count, flag.as<int>(), list.as<int>(), cnt.as<int>());
+    if (o.ledger_out)
+        k_sur_energy<<<(unsigned)((samples * 32 + 255) / 256), 256, 0, st>>>(
+            samples, N, ctx->d_lam.as<double>(), j_out, lnp.as<float>(), o.ledger_out);
     SCK(cudaGetLastError());
     int nfb = 0;
     SCK(cudaMemcpyAsync(&nfb, cnt.p, 4, cudaMemcpyDeviceToHost, st));
@@ -785,7 +925,9 @@ heat_status heat_solve_surrogate(heat_ctx* ctx, const heat_opts* fallback_opts, 
     SCK(cudaMemcpy(hl.data(), list.p, 4 * (size_t)nfb, cudaMemcpyDeviceToHost));
     std::sort(hl.begin(), hl.end());
     SCK(cudaMemcpy(list.p, hl.data(), 4 * (size_t)nfb, cudaMemcpyHostToDevice));
-    if (ufb.ensure(8 * (size_t)nfb * N) || jfb.ensure(4 * (size_t)nfb * G * N))
+    DevBuf lfb;
+    if (ufb.ensure(8 * (size_t)nfb * N) || jfb.ensure(4 * (size_t)nfb * G * N) ||
+        (o.ledger_out && lfb.ensure(sizeof(double) * 2 * (size_t)nfb * G)))
         return ctx->fail(HEAT_ENOMEM, "heat_solve_surrogate: allocation");
     long long nu = (long long)nfb * N;
     k_fallback_gather<<<(unsigned)((nu + 255) / 256), 256, 0, st>>>(nfb, N, list.as<int>(), (const double*)ctx->u_dev,
@@ -799,7 +941,7 @@ heat_status heat_solve_surrogate(heat_ctx* ctx, const heat_opts* fallback_opts, 
     heat_opts fo = o;
     fo.cell_begin = 0;
     fo.cell_count = nfb;
-    fo.ledger_out = nullptr;
+    fo.ledger_out = o.ledger_out ? lfb.as<double>() : nullptr;
     h = heat_solve(ctx, &fo, nullptr, jfb.p, stream);
     ctx->u_dev = u_save;
     ctx->n_cells = n_save;
@@ -808,6 +950,9 @@ heat_status heat_solve_surrogate(heat_ctx* ctx, const heat_opts* fallback_opts, 
     long long row = (long long)G * N;
     k_fallback_scatter<<<(unsigned)((nfb * row + 255) / 256), 256, 0, st>>>(nfb, row, list.as<int>(), jfb.as<float>(),
                                                                            j_out);
+    if (o.ledger_out)
+        k_fallback_ledger<<<(unsigned)((nfb * 2 * G + 255) / 256), 256, 0, st>>>(nfb, 2 * G, list.as<int>(),
+                                                                                lfb.as<double>(), o.ledger_out);
     SCK(cudaGetLastError());
     SCK(cudaStreamSynchronize(st));  // temporaries are released on return
     return HEAT_OK;

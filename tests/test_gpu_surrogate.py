@@ -202,3 +202,39 @@ def test_what_training_gains(small):
     torch.cuda.synchronize()
     t_exact, t_net = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
     assert t_net < t_exact, (t_net, t_exact)
+
+
+def test_energy_check_of_surrogate_and_fallback_spectra(trained):
+    """ledger_out of heat_solve_surrogate: with everything answered by the network, each
+    spectrum's [absorbed power, 4 pi int j dlambda]; with everything falling back, exactly the
+    ledger of the solve it falls back to."""
+    import torch
+
+    wl, lib, _ = trained
+    st = torch.cuda.current_stream().cuda_stream
+    cells = (200, 40)
+    j = torch.empty(cells[1], wl.n_grains, wl.n_lambda, dtype=torch.float32, device="cuda")
+    led = torch.zeros(cells[1], wl.n_grains, 2, dtype=torch.float64, device="cuda")
+    o = heat.heat_default_opts(build=heat.HEAT_BUILD_F32, emis=heat.HEAT_EMIS_BF16X3, j_dtype=heat.HEAT_F32,
+                               cell_begin=cells[0], cell_count=cells[1], ledger_out=led)
+    nfb = heat.heat_solve_surrogate(lib.ctx, o, 1e9, j, st)
+    heat.heat_sync(lib.ctx)
+    assert nfb == 0
+    jl = j.double().cpu().numpy()
+    trap = 4 * np.pi * np.sum(0.5 * (jl[..., 1:] + jl[..., :-1]) * np.diff(wl.lam), axis=-1)
+    L = led.cpu().numpy()
+    assert np.allclose(L[..., 1], trap, rtol=1e-9, atol=0)
+    assert np.all(L[..., 0] > 0)
+    # all cells fall back: the exact path's ledger, bit for bit
+    led2 = torch.zeros_like(led)
+    o.ledger_out = led2.data_ptr()
+    nfb = heat.heat_solve_surrogate(lib.ctx, o, 1e-30, j, st)
+    heat.heat_sync(lib.ctx)
+    assert nfb == cells[1]
+    led3 = torch.zeros_like(led)
+    j3 = torch.empty_like(j)
+    heat.heat_solve(lib.ctx, heat.heat_default_opts(build=heat.HEAT_BUILD_F32, emis=heat.HEAT_EMIS_BF16X3,
+                                                    j_dtype=heat.HEAT_F32, cell_begin=cells[0], cell_count=cells[1],
+                                                    ledger_out=led3), None, j3, st)
+    heat.heat_sync(lib.ctx)
+    assert torch.equal(led2, led3) and torch.equal(j, j3)
