@@ -9,12 +9,13 @@ marshals numpy arrays through ctypes.  Functions and the passages they follow:
 
 * ``range_integral``      -- log-log interpolant of Omega (Eq. interpolation) integrated in closed form
 * ``heating_matrix``      -- T_ul for u > l (Eq. heating, wavelength-integral form, plus intra-bin term)
+* ``heating_matrix_point`` -- T_ul by the paper's point rule (Eq. heating at lambda_ul, Eq. interpolation)
 * ``b_matrix``            -- B_fj suffix sums (Eq. bmatrix via Eq. brecurrence)
 * ``recursion``           -- X recursion and renormalisation (Eq. xf, Eq. renormalization)
 * ``cooling``, ``emitted_power`` -- T_{f-1,f} (Eq. cooling)
 * ``emissivity``          -- j_lambda (Eq. emission, Eq. emission-lambda)
 * ``ledger``              -- absorbed vs emitted power of the discrete model (follows from Eq. bequation)
-* ``solve_batch``         -- all of the above over cells x grains
+* ``solve_batch``         -- all of the above over cells x grains (either heating form)
 * ``size_integrate``      -- Eq. convolution, discretised
 """
 from __future__ import annotations
@@ -59,10 +60,13 @@ def lib():
         L.orc_ledger.restype = None
         L.orc_ledger.argtypes = [ctypes.c_int, _D, _D, _D, _D, _D]
         L.orc_solve_spectrum.restype = ctypes.c_int
-        L.orc_solve_spectrum.argtypes = [ctypes.c_int, _D, _D, ctypes.c_int, _D, _D, _D, _D, _D, _D, _D]
+        L.orc_solve_spectrum.argtypes = [ctypes.c_int, _D, _D, ctypes.c_int, _D, _D, _D, _D, _D, _D, _D,
+                                         ctypes.c_int]
         L.orc_solve_batch.restype = ctypes.c_int
         L.orc_solve_batch.argtypes = [ctypes.c_int, _D, ctypes.c_int, _D, _I, _D, _D, _D, ctypes.c_int, _D, _D,
-                                      _D, _D, ctypes.c_int]
+                                      _D, _D, ctypes.c_int, ctypes.c_int]
+        L.orc_heating_matrix_point.restype = ctypes.c_int
+        L.orc_heating_matrix_point.argtypes = [ctypes.c_int, _D, _D, ctypes.c_int, _D, _D]
         L.orc_size_integrate.restype = None
         L.orc_size_integrate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D]
         L.orc_max_threads.restype = ctypes.c_int
@@ -95,6 +99,19 @@ def range_integral(lam, om, p, a, b):
     lam, pl = _d(lam)
     om, po = _d(om)
     return lib().orc_range_integral(lam.size, pl, po, int(p), float(a), float(b))
+
+
+def heating_matrix_point(lam, om, E):
+    """Explicit T of the paper's point rule (Eq. heating)."""
+    lam, pl = _d(lam)
+    om, po = _d(om)
+    E, pe = _d(E)
+    nb = E.size
+    A = np.zeros((nb, nb))
+    st = lib().orc_heating_matrix_point(lam.size, pl, po, nb, pe, A.ctypes.data_as(_D))
+    if st != OK:
+        raise RuntimeError(f"orc_heating_matrix_point status {st}")
+    return A
 
 
 def heating_matrix(lam, om, E):
@@ -178,8 +195,13 @@ def grain_cooling(wl):
     return Cf
 
 
-def solve_batch(wl, Cf=None, want_j=True, want_ledger=False, n_threads=0, u=None):
-    """P [cells, total_bins], j [cells, G, N] (or None), ledger [cells, G, 2] (or None)."""
+HEATING_INTEGRAL, HEATING_POINT = 0, 1
+
+
+def solve_batch(wl, Cf=None, want_j=True, want_ledger=False, n_threads=0, u=None, heating=HEATING_INTEGRAL):
+    """P [cells, total_bins], j [cells, G, N] (or None), ledger [cells, G, 2] (or None).
+    heating: HEATING_INTEGRAL (elements integrated over the bin edges) or HEATING_POINT
+    (the paper's point rule, Eq. heating)."""
     if Cf is None:
         Cf = grain_cooling(wl)
     u = wl.u if u is None else u
@@ -196,7 +218,7 @@ def solve_batch(wl, Cf=None, want_j=True, want_ledger=False, n_threads=0, u=None
     j, pj = _dnull(np.zeros((cells, G, N)) if want_j else None)
     led, pld = _dnull(np.zeros((cells, G, 2)) if want_ledger else None)
     st = lib().orc_solve_batch(N, pl, G, pc, off.ctypes.data_as(_I), pt, pe, pcf, cells, pu,
-                               P.ctypes.data_as(_D), pj, pld, int(n_threads))
+                               P.ctypes.data_as(_D), pj, pld, int(n_threads), int(heating))
     return P, j, led, st
 
 

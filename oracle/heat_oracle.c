@@ -151,6 +151,28 @@ int orc_heating_matrix(int N, const double* lam, const double* om, int nb, const
     return ORC_OK;
 }
 
+/* The paper's point rule (Eq. heating): T_ul = Omega(lambda_ul) lambda_ul^3 dE_u / (h^2 c)
+ * with lambda_ul = hc / (E_u - E_l) (bin centres), Omega from the log-log interpolant (zero
+ * outside the grid) and dE_u the width of the upper bin, E^hi_u - E^lo_u; the top bin, whose
+ * upper edge is open, takes E_M - E_{M-1}.  The constant: photons absorbed per unit
+ * wavelength at Omega lambda / h, times the wavelength window lambda^2 dE / (h c) that a bin
+ * of width dE covers.  No intra-bin term: the paper's rule has none.                    */
+int orc_heating_matrix_point(int N, const double* lam, const double* om, int nb, const double* E, double* A)
+{
+    if (N < 2 || nb < 2) return ORC_EINVAL;
+    const int M = nb - 1;
+    memset(A, 0, sizeof(double) * (size_t)nb * (size_t)nb);
+    for (int u = 1; u <= M; ++u) {
+        const double lo = 0.5 * (E[u - 1] + E[u]);
+        const double dE = (u < M) ? 0.5 * (E[u] + E[u + 1]) - lo : E[M] - E[M - 1];
+        for (int l = 0; l < u; ++l) {
+            const double x = hc() / (E[u] - E[l]);
+            A[(size_t)u * nb + l] = orc_omega_at(N, lam, om, x) * x * x * x * dE / (H_PL * H_PL * C_LI);
+        }
+    }
+    return ORC_OK;
+}
+
 /* B_fj = sum_{k >= f} T_kj for f > j (Eq. bmatrix), built with the suffix
  * recurrence B_{f,j} = B_{f+1,j} + T_{f,j}, B_{M,j} = T_{M,j} (Eq. brecurrence).
  * B is row-major nb x nb; entries with f <= j are zero.                        */
@@ -380,7 +402,7 @@ void orc_ledger(int nb, const double* A, const double* E, const double* Cf, cons
 /* One (cell, grain) spectrum end to end.  P[nb], j[N] (may be NULL),
  * ledger[2] (may be NULL).  Work buffers are allocated here.                 */
 int orc_solve_spectrum(int N, const double* lam, const double* cabs, int nb, const double* T, const double* E,
-                       const double* Cf, const double* u, double* P, double* j, double* ledger)
+                       const double* Cf, const double* u, double* P, double* j, double* ledger, int heating)
 {
     size_t nn = (size_t)nb * (size_t)nb;
     double* om = (double*)malloc(sizeof(double) * (size_t)N);
@@ -388,7 +410,7 @@ int orc_solve_spectrum(int N, const double* lam, const double* cabs, int nb, con
     double* B = (double*)malloc(sizeof(double) * nn);
     if (!om || !A || !B) { free(om); free(A); free(B); return ORC_ENOMEM; }
     for (int n = 0; n < N; ++n) om[n] = u[n] * cabs[n];
-    int st = orc_heating_matrix(N, lam, om, nb, E, A);
+    int st = heating == 1 ? orc_heating_matrix_point(N, lam, om, nb, E, A) : orc_heating_matrix(N, lam, om, nb, E, A);
     if (st == ORC_OK) {
         orc_b_matrix(nb, A, B);
         st = orc_recursion(nb, B, Cf, P);
@@ -406,7 +428,7 @@ int orc_solve_spectrum(int N, const double* lam, const double* cabs, int nb, con
  * Returns the first non-OK status seen (all spectra are still computed).     */
 int orc_solve_batch(int N, const double* lam, int G, const double* cabs, const int* bin_off, const double* T,
                     const double* E, const double* Cf, int cells, const double* u, double* P, double* j,
-                    double* ledger, int n_threads)
+                    double* ledger, int n_threads, int heating)
 {
     int status = ORC_OK;
     const long total = (long)cells * G;
@@ -421,7 +443,7 @@ int orc_solve_batch(int N, const double* lam, int G, const double* cabs, const i
         int st = orc_solve_spectrum(N, lam, cabs + (size_t)g * N, nb, T + off, E + off, Cf + off,
                                     u + (size_t)c * N, P + (size_t)c * nbt + off,
                                     j ? j + ((size_t)c * G + g) * N : NULL,
-                                    ledger ? ledger + ((size_t)c * G + g) * 2 : NULL);
+                                    ledger ? ledger + ((size_t)c * G + g) * 2 : NULL, heating);
         if (st != ORC_OK) {
 #ifdef _OPENMP
 #pragma omp critical
