@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--sur-tol", type=float, default=1e-2, help="ensemble spread (ln j) above which a cell falls back")
     ap.add_argument("--oracle-cells", type=int, default=24, help="cells in the oracle sample")
     ap.add_argument("--no-single-cell", action="store_true", help="skip the single-cell latency section")
+    ap.add_argument("--no-point", action="store_true", help="skip the point-rule heating section")
     ap.add_argument("--no-emis-heavy", action="store_true",
                     help="skip the emissivity-heavy workload (65536 cells x 32 grains x 512 bins x 2048 wavelengths)")
     ap.add_argument("--emis-heavy-oracle-cells", type=int, default=64,
@@ -231,6 +232,51 @@ def workload_config(wl, path):
 
 
 # ---------------------------------------------------------------------------- single-cell latency
+def point_rule_section(args, wl, ctx, heat, timed_run, opts_for, dev, sh, Cf_oracle):
+    """The paper's point-rule heating (Eq. heating at the bin centres) against the integral
+    form on the same workload: exact path timing, error against the oracle's point mode on a
+    small sample, and the energy check (model emitted / physical absorbed power) by grain
+    size, which shows the heating the point rule drops for grains whose bins are wider than
+    the photons."""
+    import torch
+
+    import oracle
+
+    cells, G, nbt = wl.n_cells, wl.n_grains, wl.total_bins
+    k2 = max(2, args.steps // 2)
+    ms_p, _, kt_p, _, _ = timed_run("exact", k2, 1, heating=heat.HEAT_HEATING_POINT)
+    out = {"spectra_per_s": cells * G / (ms_p / 1e3), "ms_per_step": ms_p,
+           "kernels_ms_per_step": {k: v[0] / k2 for k, v in kt_p.items()},
+           "precision": "FP64 point-rule build, FP64 recursion, FP64 emissivity"}
+    led = {}
+    for name, h in (("point", heat.HEAT_HEATING_POINT), ("integral", heat.HEAT_HEATING_INTEGRAL)):
+        lg = torch.zeros(cells, G, 2, dtype=torch.float64, device=dev)
+        heat.heat_solve(ctx, heat.heat_default_opts(emis=heat.HEAT_EMIS_NONE, heating=h, ledger_out=lg), None, None, sh)
+        heat.heat_sync(ctx)
+        led[name] = lg.cpu().numpy()
+    classes = {"a<25A": wl.radius < 25e-8, "25A<=a<100A": (wl.radius >= 25e-8) & (wl.radius < 100e-8),
+               "a>=100A": wl.radius >= 100e-8}
+    ratio = {}
+    for name, lg in led.items():
+        r = lg[..., 1] / lg[..., 0]
+        ratio[name] = {c: float(np.median(r[:, m])) for c, m in classes.items() if m.any()}
+    out["median_emitted_over_absorbed"] = ratio
+    if args.no_cpu_baseline:  # the oracle runs only in the CPU-baseline leg
+        return out
+    nsub = min(4, cells)
+    sub_P = torch.empty(nsub, nbt, dtype=torch.float64, device=dev)
+    o = opts_for("exact", cell_count=nsub, heating=heat.HEAT_HEATING_POINT)
+    o.emis = heat.HEAT_EMIS_NONE
+    heat.heat_solve(ctx, o, sub_P, None, sh)
+    heat.heat_sync(ctx)
+    P_ref, _, _, st = oracle.solve_batch(wl, Cf_oracle, want_j=False, u=wl.u[:nsub], heating=oracle.HEATING_POINT)
+    Pg = sub_P.cpu().numpy()
+    m = np.abs(P_ref) > 1e-280
+    out["max_rel_err"] = {"P": float(np.max(np.abs(Pg[m] - P_ref[m]) / np.abs(P_ref[m]))), "oracle_status": int(st),
+                          "sample": f"{nsub} cells x {G} grains vs the FP64 oracle's point mode"}
+    return out
+
+
 def single_cell_section(dev, stream):
     """One cell x 8 carbonaceous grains x 128 bins x 256 wavelengths: microseconds per
     heat_solve, launched eagerly and replayed from a CUDA graph, for the exact and the
@@ -411,9 +457,9 @@ def main():
         return heat.heat_default_opts(build=heat.HEAT_BUILD_F32 if b == "f32" else heat.HEAT_BUILD_F64,
                                       emis=emis_code[e], j_dtype=heat.HEAT_F32, timing=timing, host_io=host_io, **kw)
 
-    def timed_run(path, steps, warmup, sample_clocks=False):
+    def timed_run(path, steps, warmup, sample_clocks=False, **kw):
         for _ in range(warmup):
-            heat.heat_solve(ctx, opts_for(path), None, j, sh)
+            heat.heat_solve(ctx, opts_for(path, **kw), None, j, sh)
         heat.heat_sync(ctx)
         heat.heat_get_timing(ctx, reset=True)
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -428,7 +474,7 @@ def main():
         for s in range(steps):
             flush.zero_()  # evict L2 between steps (outside the per-step events)
             evs[s][0].record(stream)
-            heat.heat_solve(ctx, opts_for(path, timing=1), None, j, sh)
+            heat.heat_solve(ctx, opts_for(path, timing=1, **kw), None, j, sh)
             evs[s][1].record(stream)
         torch.cuda.synchronize(dev)
         if ws > 1:
@@ -534,6 +580,7 @@ def main():
 
     # the learned surrogate with exact fallback (trained untimed on other cells)
     sur_j = None
+    Cf_oracle = None
     if not args.no_surrogate:
         tw = W.batched(cells=args.sur_cells, seed=2002)
         t0 = time.perf_counter()
@@ -629,6 +676,7 @@ def main():
     # oracle on the host cores (rank 0, N = 1), its outputs double as the error reference
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb, P_ref, j_ref, Cf = oracle_sample(wl, args.oracle_cells)
+        Cf_oracle = Cf
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "one_core")}
         nsub = args.oracle_cells
         for path in [q for q in paths if q in PATHS]:
@@ -655,6 +703,8 @@ def main():
                 "j_masked_1e-6_peak": float(np.max(np.abs(sur_j[mj] - j_ref[mj]) / j_ref[mj])),
                 "sample": f"{nsub} cells x {G} grains vs the FP64 oracle"}
     line["paths"] = paths
+    if rank == 0 and ws == 1 and not args.no_point:
+        line["point_rule"] = point_rule_section(args, wl, ctx, heat, timed_run, opts_for, dev, sh, Cf_oracle)
     if rank == 0 and ws == 1 and not args.no_single_cell:
         line["single_cell"] = single_cell_section(dev, stream)
     if rank == 0 and ws == 1 and not args.no_emis_heavy:

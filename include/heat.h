@@ -58,6 +58,18 @@ enum { HEAT_F64 = 0, HEAT_F32 = 1 };
  * the recursion (Eq. xf) always accumulates in FP64 */
 enum { HEAT_BUILD_F64 = 0, HEAT_BUILD_F32 = 1 };
 
+/* heating matrix (Eq. heating) */
+enum {
+    HEAT_HEATING_INTEGRAL = 0, /* each element integrates the photon rate over the upper bin's edges
+                                  (plus the intra-bin term of sub-bin photons); B telescopes to
+                                  one cumulative integral per element                             */
+    HEAT_HEATING_POINT = 1     /* the paper's point rule: T_ul = Omega(lambda_ul) lambda_ul^3 dE_u
+                                  / (h^2 c) at lambda_ul = hc / (E_u - E_l), Omega on the log-log
+                                  interpolant (Eq. interpolation), dE_u the upper bin's width (the
+                                  top bin takes E_M - E_{M-1}), no intra-bin term; B by suffix sums
+                                  down each column (Eq. brecurrence).  Exact build only          */
+};
+
 /* emissivity contraction (Eq. emission) */
 enum {
     HEAT_EMIS_NONE = -1,  /* no emissivity */
@@ -97,6 +109,9 @@ typedef struct heat_opts {
                            Results do not depend on it or on chunk_cells, except that solves of
                            at most 16 cells take element-parallel kernels (same bounds against
                            the oracle, rounding differs in the last bits)                      */
+    int heating;        /* HEAT_HEATING_INTEGRAL (default) or HEAT_HEATING_POINT (needs
+                           HEAT_BUILD_F64).  The ledger's absorbed power [0] is the physical one
+                           either way, so with the point rule [1]/[0] shows what the rule loses */
 } heat_opts;
 
 /* kernel classes reported by heat_get_timing */
@@ -255,7 +270,8 @@ heat_status heat_surrogate_predict(heat_ctx* ctx, const float* X, const float* l
  * fallback_opts->ledger_out (device FP64 [cells][n_grains][2], or NULL) receives the energy
  * check of every spectrum returned: for the surrogate's, [absorbed power c int u C dlambda,
  * 4 pi int j dlambda on the grid (trapezoid)]; for the cells solved exactly, heat_solve's
- * ledger.  *n_fallback = cells solved exactly.  Synchronous. */
+ * ledger.  *n_fallback = cells solved exactly.  fallback_opts->heating must be
+ * HEAT_HEATING_INTEGRAL (the form the network is trained on), else HEAT_EINVAL.  Synchronous. */
 heat_status heat_solve_surrogate(heat_ctx* ctx, const heat_opts* fallback_opts, float tol, float* j_out,
                                  int* n_fallback, void* cuda_stream);
 

@@ -39,6 +39,18 @@ struct __align__(16) PatF32 {  // one 128-bit load
     float zt;
 };
 
+// Point-rule element (Eq. heating at the bin centres) of band element e = (u, j):
+// T_uj = Omega(lambda_uj) fac with lambda_uj = hc / (E_u - E_j) in segment n at offset
+// t = ln(lambda_uj / lambda_n), fac = lambda_uj^3 dE_u / (h^2 c); n = -1 where lambda_uj is
+// off the grid (T = 0).  Entries run down each column j (u descending), so a column's
+// suffix sums B_uj = B_{u+1,j} + T_uj come out in order.
+struct __align__(8) PointEnt {
+    int e;
+    int n;
+    double t;
+    double fac;
+};
+
 // Soft-photon abscissa for the intra-bin term of row j+1:
 // lambda_s = hc / (Elo_{j+1} - E_j) in segment n with offset t; n = -1 below the
 // grid (all absorbed power counts), n = N-1 at or above the last node (none).

@@ -243,6 +243,7 @@ void heat_default_opts(heat_opts* o) {
     o->timing = 0;
     o->ledger_out = nullptr;
     o->streams = 0;
+    o->heating = HEAT_HEATING_INTEGRAL;
 }
 
 heat_status heat_create_grid(heat_ctx** out, int device, int n_lambda, const double* lambda_cm) {
@@ -364,6 +365,8 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
         double t;
     };
     std::vector<int> diag_e(nbt, 0), diag_ok(nbt, 0);
+    std::vector<PointEnt> pent;  // point-rule entries (Eq. heating), column by column
+    std::vector<int> pcol(nbt + 1, 0);
     for (int g = 0; g < G; ++g) {
         const int off = bin_offset[g], nb = bin_offset[g + 1] - off, M = nb - 1;
         const double* E = H_bins_erg + off;
@@ -377,6 +380,7 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
         }
         long long band = 0;
         std::vector<Ent> ents;
+        std::vector<int> row_e(nb, 0), row_jlo(nb, 0);  // band index of (f, jlo(f)) and jlo(f)
         // row 0 has no elements
         rowptr.push_back((int)band_total);
         for (int f = 1; f <= M; ++f) {
@@ -390,6 +394,8 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
             // term even when no photon on the grid reaches bin f from bin f-1
             const bool diag_in_band = jlo < f;
             if (!diag_in_band) jlo = f - 1;
+            row_e[f] = (int)(band_total + band);
+            row_jlo[f] = jlo;
             wmax[g] = std::max(wmax[g], f - jlo);
             diag_e[off + f - 1] = (int)(band_total + band + (f - 1 - jlo));
             diag_ok[off + f - 1] = diag_in_band ? 1 : 0;
@@ -413,6 +419,31 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
             }
         }
         rowptr.push_back((int)(band_total + band));
+        // point-rule entries: column j holds rows j+1 .. F(j), a contiguous range since
+        // jlo(f) does not decrease with f; every element the point rule can make non-zero
+        // (E_u - E_j <= hc/lambda_0) lies in the band, and the band's other elements take the
+        // column's suffix sum with T = 0
+        for (int j = 0; j < nb; ++j) {
+            pcol[off + j] = (int)pent.size();
+            int F = j;
+            while (F + 1 <= M && row_jlo[F + 1] <= j) ++F;
+            for (int u = F; u > j; --u) {
+                PointEnt pe;
+                pe.e = row_e[u] + (j - row_jlo[u]);
+                const double x = kHChost / (E[u] - E[j]);
+                const double dE = u < M ? Elo[u + 1] - Elo[u] : E[M] - E[M - 1];  // upper bin's width
+                if (x >= lam[0] && x <= lam[N - 1]) {
+                    pe.n = segment_of(lam, x);
+                    pe.t = std::log(x / lam[pe.n]);
+                    pe.fac = x * x * x * dE / (kHhost * kHhost * kChost);
+                } else {
+                    pe.n = -1;
+                    pe.t = 0.0;
+                    pe.fac = 0.0;
+                }
+                pent.push_back(pe);
+            }
+        }
         // pattern: the grain's elements grouped by segment
         std::stable_sort(ents.begin(), ents.end(), [](const Ent& a, const Ent& b) { return a.n < b.n; });
         size_t base = pat64.size();
@@ -469,6 +500,9 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
         cost_build[g] = band + 12LL * nb;
     }
     soft_off[G] = (int)soft.size();
+    pcol[nbt] = (int)pent.size();
+    if ((long long)pent.size() != band_total)
+        return ctx->fail(HEAT_EINVAL, "heat_set_grains: point-rule table does not cover the band");
     ctx->band_per_cell = band_total;
     ctx->max_bins = 0;
     for (int g = 0; g < G; ++g) ctx->max_bins = std::max(ctx->max_bins, bin_offset[g + 1] - bin_offset[g]);
@@ -488,7 +522,7 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
         upload(ctx->d_sC, sC) || upload(ctx->d_ca32, ca32) || upload(ctx->d_ce32, ce32) ||
         upload(ctx->d_sC32, sC32) || upload(ctx->d_rowptr, rowptr) || upload(ctx->d_wmax, wmax) || upload(ctx->d_pat64, pat64) ||
         upload(ctx->d_pat32, pat32) || upload(ctx->d_seg_ptr, seg_ptr) || upload(ctx->d_soft, soft) || upload(ctx->d_soft_off, soft_off) ||
-        upload(ctx->d_w, ctx->w))
+        upload(ctx->d_w, ctx->w) || upload(ctx->d_pent, pent) || upload(ctx->d_pcol, pcol))
         return ctx->fail(HEAT_ENOMEM, "heat_set_grains: device allocation failed");
     std::vector<int> koff_all = {0, nbt};
     if (upload(ctx->d_koff_all, koff_all)) return ctx->fail(HEAT_ENOMEM, "heat_set_grains: device allocation failed");
@@ -577,6 +611,10 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
     if ((o.build != HEAT_BUILD_F64 && o.build != HEAT_BUILD_F32) || o.emis < HEAT_EMIS_NONE || o.emis > HEAT_EMIS_TF32 ||
         (o.j_dtype != HEAT_F64 && o.j_dtype != HEAT_F32))
         return ctx->fail(HEAT_EINVAL, "heat_solve: bad precision option");
+    if (o.heating != HEAT_HEATING_INTEGRAL && o.heating != HEAT_HEATING_POINT)
+        return ctx->fail(HEAT_EINVAL, "heat_solve: bad heating option");
+    if (o.heating == HEAT_HEATING_POINT && o.build != HEAT_BUILD_F64)
+        return ctx->fail(HEAT_EINVAL, "heat_solve: the point rule needs the FP64 build");
     if (o.size_integrate && !ctx->has_w) return ctx->fail(HEAT_EINVAL, "heat_solve: size integration needs weights");
     if (o.chunk_cells < 0 || (o.chunk_cells % 32) != 0)
         return ctx->fail(HEAT_EINVAL, "heat_solve: chunk_cells must be a non-negative multiple of 32");
@@ -702,6 +740,8 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
     gd.pat32 = ctx->d_pat32.as<PatF32>();
     gd.soft = ctx->d_soft.as<SoftF64>();
     gd.soft_off = ctx->d_soft_off.as<int>();
+    gd.pent = ctx->d_pent.as<PointEnt>();
+    gd.pcol = ctx->d_pcol.as<int>();
 
     // fork: every slot stream starts after the work already queued on the caller's stream
     if (nslots > 1) {
@@ -716,6 +756,7 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
         const int cc_pad = (cells + 31) / 32 * 32;
         ChunkDev ch{};
         ch.small = count <= kSmallCells ? 1 : 0;
+        ch.point = o.heating == HEAT_HEATING_POINT ? 1 : 0;
         ch.cells = cells;
         ch.Cc = cc_pad;
         ch.NG = cc_pad / 32;
@@ -1006,7 +1047,7 @@ void heat_destroy(heat_ctx* ctx) {
                       &ctx->d_T, &ctx->d_E, &ctx->d_Cf, &ctx->d_invC, &ctx->d_invdE, &ctx->d_invdE32, &ctx->d_Cact,
                       &ctx->d_sC, &ctx->d_ca32, &ctx->d_ce32, &ctx->d_sC32, &ctx->d_rowptr, &ctx->d_wmax, &ctx->d_seg_ptr,
                       &ctx->d_pat64, &ctx->d_pat32, &ctx->d_soft, &ctx->d_soft_off, &ctx->d_K, &ctx->d_Kw, &ctx->d_w,
-                      &ctx->d_koff_all, &ctx->d_cde, &ctx->d_u_own, &ctx->s_tasks, &ctx->s_tasks_tail, &ctx->d_status};
+                      &ctx->d_koff_all, &ctx->d_cde, &ctx->d_pent, &ctx->d_pcol, &ctx->d_u_own, &ctx->s_tasks, &ctx->s_tasks_tail, &ctx->d_status};
     for (DevBuf* b : bufs) b->release();
     for (auto& sl : ctx->slots) {
         DevBuf* sb[] = {&sl.ua64, &sl.su64, &sl.ua32, &sl.Bb64, &sl.Bb32, &sl.xs, &sl.ep,
@@ -1068,6 +1109,8 @@ __attribute__((visibility("hidden"))) heat_status heat_internal_grain_view(heat_
     gd->pat32 = ctx->d_pat32.as<PatF32>();
     gd->soft = ctx->d_soft.as<SoftF64>();
     gd->soft_off = ctx->d_soft_off.as<int>();
+    gd->pent = ctx->d_pent.as<PointEnt>();
+    gd->pcol = ctx->d_pcol.as<int>();
     *device = ctx->device;
     *status = ctx->d_status.as<int>();
     return HEAT_OK;

@@ -49,6 +49,8 @@ struct GrainDev {
     const PatF32* pat32;    // pattern entries (FP32 build)
     const SoftF64* soft;    // [nbt - G] per grain, sorted by segment (descending)
     const int* soft_off;    // [G+1] start of each grain's soft list
+    const PointEnt* pent;   // point-rule entries, column by column (u descending within a column)
+    const int* pcol;        // [nbt + 1] entries of column j of grain g at pcol[off_g + j] .. pcol[off_g + j + 1]
 };
 
 // Per-chunk scratch.
@@ -74,6 +76,7 @@ struct ChunkDev {
     double* ledger;     // [cells][G][2] energy check (absorbed, emitted), or null
     int* status;
     int small;          // 1: the solve has few cells (kSmallCells): element-parallel kernels
+    int point;          // 1: point-rule heating (HEAT_HEATING_POINT, FP64 build only)
 };
 
 // Solves of at most this many cells use the element-parallel build and recursion (a block

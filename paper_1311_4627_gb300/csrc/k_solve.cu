@@ -689,6 +689,78 @@ __global__ void __launch_bounds__(128) k_recur_small(GrainDev gd, ChunkDev ch) {
     if (numeric_bad && lane == 0) atomicOr(ch.status, kStatNumeric);
 }
 
+// ---------------------------------------------------------------------------
+// Point-rule build (HEAT_HEATING_POINT; Eq. heating at the bin centres, Eq. brecurrence):
+//   T_uj = Omega(lambda_uj) lambda_uj^3 dE_u / (h^2 c),  Omega(lambda) = u_n C_n e^{(su_n + sC_n) t}
+// on the log-log interpolant (the slope of the product u C is the sum of the slopes), and
+// B_uj = B_{u+1,j} + T_uj down each column from its last band row, in the order of the
+// suffix recurrence.  Every band element is written (elements the rule leaves at zero
+// carry the column's sum).  Also the absorbed power c int Omega on the grid, summed in
+// k_build's order, for the energy check.
+__device__ __forceinline__ double point_column(const GrainDev& gd, const ChunkDev& ch, int g, int cell, int j,
+                                               double* Bb) {
+    const int N = gd.N, Cc = ch.Cc;
+    const double* Cact = gd.Cact + (size_t)g * N;
+    const double* sC = gd.sC + (size_t)g * N;
+    const int off = gd.bin_off[g];
+    const int k1 = gd.pcol[off + j + 1];
+    double acc = 0.0, om = 0.0, s = 0.0;
+    int ncur = -1;
+    for (int k = gd.pcol[off + j]; k < k1; ++k) {
+        const PointEnt pe = gd.pent[k];
+        if (pe.n >= 0) {
+            if (pe.n != ncur) {  // entries move up the wavelength grid along a column
+                ncur = pe.n;
+                om = ch.ua64[(size_t)pe.n * Cc + cell] * Cact[pe.n];
+                s = ch.su64[(size_t)pe.n * Cc + cell] + sC[pe.n];
+            }
+            acc += om * exp(s * pe.t) * pe.fac;
+        }
+        Bb[(size_t)pe.e * 32] = acc;
+    }
+    return acc;
+}
+
+__device__ __forceinline__ double absorbed_power(const GrainDev& gd, const ChunkDev& ch, int g, int cell) {
+    const int N = gd.N, Cc = ch.Cc;
+    const double* Cact = gd.Cact + (size_t)g * N;
+    const double* sC = gd.sC + (size_t)g * N;
+    double Psi = 0.0;
+    for (int n = N - 2; n >= 0; --n) {
+        const double om = ch.ua64[(size_t)n * Cc + cell] * Cact[n];
+        const double q0 = ch.su64[(size_t)n * Cc + cell] + sC[n] + 1.0;
+        const double b = om * gd.lam[n];
+        const double dl = gd.dln[n];
+        if (om > 0.0) Psi += b * dl * e1d(q0 * dl);
+    }
+    return kC * Psi;
+}
+
+// Lane per cell, warp per task (grain x 32 cells), columns in turn.
+__global__ void __launch_bounds__(128) k_build_point(GrainDev gd, ChunkDev ch) {
+    const int task = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (task >= ch.n_tasks) return;
+    const int2 tk = (ch.btasks ? ch.btasks : ch.tasks)[task];
+    const int g = tk.x, grp = tk.y;
+    const int cell = grp * 32 + lane;
+    const int M = gd.bin_off[g + 1] - gd.bin_off[g] - 1;
+    double* Bb = ch.Bb64 + (size_t)grp * gd.band_total * 32 + lane;
+    for (int j = 0; j < M; ++j) point_column(gd, ch, g, cell, j, Bb);
+    if (ch.pabs) ch.pabs[(size_t)cell * gd.G + g] = absorbed_power(gd, ch, g, cell);
+}
+
+// Few cells: block per (cell, grain), threads over the columns (each column's sum is the
+// same sequence as in k_build_point, so B is bit-identical).
+__global__ void __launch_bounds__(128) k_build_point_small(GrainDev gd, ChunkDev ch) {
+    const int cell = blockIdx.x / gd.G, g = blockIdx.x % gd.G;
+    if (cell >= ch.cells) return;
+    const int M = gd.bin_off[g + 1] - gd.bin_off[g] - 1;
+    double* Bb = ch.Bb64 + (size_t)(cell >> 5) * gd.band_total * 32 + (cell & 31);
+    for (int j = threadIdx.x; j < M; j += blockDim.x) point_column(gd, ch, g, cell, j, Bb);
+    if (threadIdx.x == 0 && ch.pabs) ch.pabs[(size_t)cell * gd.G + g] = absorbed_power(gd, ch, g, cell);
+}
+
 cudaError_t launch_field(const GrainDev& g, const void* u, int dtype, long long cell0, const ChunkDev& ch, int build,
                          cudaStream_t st) {
     dim3 block(32, 8), grid((g.N + 31) / 32, ch.Cc / 32);
@@ -711,6 +783,16 @@ cudaError_t launch_field(const GrainDev& g, const void* u, int dtype, long long 
 }
 
 cudaError_t launch_build(const GrainDev& g, const ChunkDev& ch, int build, cudaStream_t st) {
+    if (ch.point) {  // the point rule (FP64 build only; checked by the caller)
+        if (build != 0) return cudaErrorInvalidValue;
+        if (ch.small) {
+            const unsigned blocks = (unsigned)(ch.cells * g.G);
+            if (blocks) k_build_point_small<<<blocks, 128, 0, st>>>(g, ch);
+        } else {
+            k_build_point<<<(ch.n_tasks + 3) / 4, 128, 0, st>>>(g, ch);
+        }
+        return cudaGetLastError();
+    }
     if (ch.small) {
         const size_t smem = sizeof(double) * 2 * (size_t)g.N;
         const unsigned blocks = (unsigned)(ch.cells * g.G);

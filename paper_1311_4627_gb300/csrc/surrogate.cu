@@ -888,6 +888,8 @@ heat_status heat_solve_surrogate(heat_ctx* ctx, const heat_opts* fallback_opts, 
     if (fallback_opts->size_integrate || fallback_opts->host_io || fallback_opts->j_dtype != HEAT_F32 ||
         fallback_opts->emis == HEAT_EMIS_NONE)
         return ctx->fail(HEAT_EINVAL, "heat_solve_surrogate: fallback needs per-grain FP32 device j");
+    if (fallback_opts->heating != HEAT_HEATING_INTEGRAL)  // the network learns the integral form
+        return ctx->fail(HEAT_EINVAL, "heat_solve_surrogate: the surrogate is trained on the integral heating form");
     cudaStream_t st = (cudaStream_t)stream;
     const heat_opts& o = *fallback_opts;
     const int N = ctx->N, G = ctx->G;

@@ -21,6 +21,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "heat.h")
 HEAT_OK, HEAT_EINVAL, HEAT_ENOMEM, HEAT_ECUDA, HEAT_ENUMERIC, HEAT_ETIMEOUT, HEAT_ESTATE = range(7)
 HEAT_F64, HEAT_F32 = 0, 1
 HEAT_BUILD_F64, HEAT_BUILD_F32 = 0, 1
+HEAT_HEATING_INTEGRAL, HEAT_HEATING_POINT = 0, 1
 HEAT_EMIS_NONE, HEAT_EMIS_F64, HEAT_EMIS_BF16X3, HEAT_EMIS_TF32X3, HEAT_EMIS_BF16, HEAT_EMIS_TF32 = -1, 0, 1, 2, 3, 4
 EMIS_NAMES = {HEAT_EMIS_F64: "f64", HEAT_EMIS_BF16X3: "bf16x3", HEAT_EMIS_TF32X3: "tf32x3", HEAT_EMIS_BF16: "bf16",
               HEAT_EMIS_TF32: "tf32"}
@@ -41,7 +42,7 @@ class heat_opts(ctypes.Structure):
     _fields_ = [("build", ctypes.c_int), ("emis", ctypes.c_int), ("j_dtype", ctypes.c_int),
                 ("size_integrate", ctypes.c_int), ("cell_begin", ctypes.c_int), ("cell_count", ctypes.c_int),
                 ("chunk_cells", ctypes.c_int), ("host_io", ctypes.c_int), ("timing", ctypes.c_int),
-                ("ledger_out", ctypes.c_void_p), ("streams", ctypes.c_int)]
+                ("ledger_out", ctypes.c_void_p), ("streams", ctypes.c_int), ("heating", ctypes.c_int)]
 
 
 _lib = None
