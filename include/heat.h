@@ -112,6 +112,17 @@ typedef struct heat_opts {
     int heating;        /* HEAT_HEATING_INTEGRAL (default) or HEAT_HEATING_POINT (needs
                            HEAT_BUILD_F64).  The ledger's absorbed power [0] is the physical one
                            either way, so with the point rule [1]/[0] shows what the rule loses */
+    double prune_eps;   /* 0 (default): every bin is solved.  eps in (0, 1): tail pruning, an
+                           approximation in the spirit of the paper's level cut-off (appendix,
+                           algorithm optimisations: pruning):
+                           a spectrum's recursion stops once every bin of the current row's band
+                           window has X_i below 2^-L of the largest X so far and X_i Kmax_i below
+                           2^-L of the largest such product (Kmax_i = max over the grid of
+                           C_abs B_lambda(T_i); 2^-L <= eps, compared on binary exponents), and
+                           P of the bins above is 0.  Those bins carry less than about eps of the
+                           probability and of j_lambda at any wavelength relative to its peak.
+                           Results still do not depend on chunking or grouping.  Outside [0, 1):
+                           HEAT_EINVAL                                                          */
 } heat_opts;
 
 /* kernel classes reported by heat_get_timing */

@@ -55,7 +55,7 @@ struct heat_ctx {
     std::vector<int> grain_order, grain_order_build;  // task orders of the recursion and the build
     DevBuf d_bin_off, d_cabs, d_T, d_E, d_Cf, d_invC, d_invdE, d_invdE32, d_Cact, d_sC, d_ca32, d_ce32, d_sC32,
         d_rowptr, d_wmax, d_seg_ptr, d_pat64, d_pat32, d_soft, d_soft_off, d_K, d_Kw, d_w, d_koff_all, d_cde,
-        d_pent, d_pcol;
+        d_pent, d_pcol, d_kexp;
     // fields
     int n_cells = 0;
     const void* u_dev = nullptr;

@@ -244,6 +244,7 @@ void heat_default_opts(heat_opts* o) {
     o->ledger_out = nullptr;
     o->streams = 0;
     o->heating = HEAT_HEATING_INTEGRAL;
+    o->prune_eps = 0.0;
 }
 
 heat_status heat_create_grid(heat_ctx** out, int device, int n_lambda, const double* lambda_cm) {
@@ -546,6 +547,8 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
     CKR(launch_planck(N, nbt, ctx->d_lam.as<double>(), ctx->d_cabs.as<double>(), d_bg.as<int>(), ctx->d_T.as<double>(),
                       ctx->d_E.as<double>(), ctx->d_w.as<double>(), ctx->d_K.as<double>(),
                       ctx->has_w ? ctx->d_Kw.as<double>() : nullptr, 0));
+    if (ctx->d_kexp.ensure(sizeof(int) * nbt)) return ctx->fail(HEAT_ENOMEM, "heat_set_grains: allocation");
+    CKR(launch_kexp(N, nbt, ctx->d_K.as<double>(), ctx->d_kexp.as<int>(), 0));
     CKR(cudaDeviceSynchronize());
     std::vector<double> Cf(nbt), invC(nbt, 0.0), cde(nbt, 0.0);
     CKR(cudaMemcpy(Cf.data(), ctx->d_Cf.p, sizeof(double) * nbt, cudaMemcpyDeviceToHost));
@@ -603,6 +606,14 @@ static int default_chunk(heat_ctx* ctx, int build, int count, int nslots) {
     return (int)(std::min(groups, std::max<size_t>(1, want)) * 32);
 }
 
+// Tail-pruning threshold as a power of two: the smallest L with 2^-L <= eps (0 = off).  The
+// recursion compares binary exponents, e(a) < e(b) - L, which implies a < 2^-L b <= eps b.
+static int prune_log2(double eps) {
+    if (!(eps > 0.0)) return 0;
+    int L = (int)std::ceil(-std::log2(eps));
+    return std::max(1, std::min(L, 1000));
+}
+
 heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void* j_out, void* stream) {
     if (!ctx || !opts) return HEAT_EINVAL;
     if (ctx->G == 0) return ctx->fail(HEAT_ESTATE, "heat_solve: grains not set");
@@ -615,6 +626,8 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
         return ctx->fail(HEAT_EINVAL, "heat_solve: bad heating option");
     if (o.heating == HEAT_HEATING_POINT && o.build != HEAT_BUILD_F64)
         return ctx->fail(HEAT_EINVAL, "heat_solve: the point rule needs the FP64 build");
+    if (!(o.prune_eps >= 0.0 && o.prune_eps < 1.0))
+        return ctx->fail(HEAT_EINVAL, "heat_solve: prune_eps must be in [0, 1)");
     if (o.size_integrate && !ctx->has_w) return ctx->fail(HEAT_EINVAL, "heat_solve: size integration needs weights");
     if (o.chunk_cells < 0 || (o.chunk_cells % 32) != 0)
         return ctx->fail(HEAT_EINVAL, "heat_solve: chunk_cells must be a non-negative multiple of 32");
@@ -742,6 +755,7 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
     gd.soft_off = ctx->d_soft_off.as<int>();
     gd.pent = ctx->d_pent.as<PointEnt>();
     gd.pcol = ctx->d_pcol.as<int>();
+    gd.kexp = ctx->d_kexp.as<int>();
 
     // fork: every slot stream starts after the work already queued on the caller's stream
     if (nslots > 1) {
@@ -757,6 +771,7 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
         ChunkDev ch{};
         ch.small = count <= kSmallCells ? 1 : 0;
         ch.point = o.heating == HEAT_HEATING_POINT ? 1 : 0;
+        ch.prune = prune_log2(o.prune_eps);
         ch.cells = cells;
         ch.Cc = cc_pad;
         ch.NG = cc_pad / 32;
@@ -1047,7 +1062,7 @@ void heat_destroy(heat_ctx* ctx) {
                       &ctx->d_T, &ctx->d_E, &ctx->d_Cf, &ctx->d_invC, &ctx->d_invdE, &ctx->d_invdE32, &ctx->d_Cact,
                       &ctx->d_sC, &ctx->d_ca32, &ctx->d_ce32, &ctx->d_sC32, &ctx->d_rowptr, &ctx->d_wmax, &ctx->d_seg_ptr,
                       &ctx->d_pat64, &ctx->d_pat32, &ctx->d_soft, &ctx->d_soft_off, &ctx->d_K, &ctx->d_Kw, &ctx->d_w,
-                      &ctx->d_koff_all, &ctx->d_cde, &ctx->d_pent, &ctx->d_pcol, &ctx->d_u_own, &ctx->s_tasks, &ctx->s_tasks_tail, &ctx->d_status};
+                      &ctx->d_koff_all, &ctx->d_cde, &ctx->d_pent, &ctx->d_pcol, &ctx->d_kexp, &ctx->d_u_own, &ctx->s_tasks, &ctx->s_tasks_tail, &ctx->d_status};
     for (DevBuf* b : bufs) b->release();
     for (auto& sl : ctx->slots) {
         DevBuf* sb[] = {&sl.ua64, &sl.su64, &sl.ua32, &sl.Bb64, &sl.Bb32, &sl.xs, &sl.ep,
@@ -1111,6 +1126,7 @@ __attribute__((visibility("hidden"))) heat_status heat_internal_grain_view(heat_
     gd->soft_off = ctx->d_soft_off.as<int>();
     gd->pent = ctx->d_pent.as<PointEnt>();
     gd->pcol = ctx->d_pcol.as<int>();
+    gd->kexp = ctx->d_kexp.as<int>();
     *device = ctx->device;
     *status = ctx->d_status.as<int>();
     return HEAT_OK;

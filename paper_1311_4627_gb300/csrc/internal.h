@@ -14,6 +14,7 @@ struct SoftF64;
 cudaError_t set_gauss_legendre(const double* x, const double* w);
 cudaError_t launch_cooling(int N, const double* lam, const double* cabs, const int* bin_off, int G, const double* T,
                            const double* E, double* Cf, const int2* work, int n_work, cudaStream_t st);
+cudaError_t launch_kexp(int N, int nbt, const double* K, int* kexp, cudaStream_t st);
 cudaError_t launch_planck(int N, int nbt, const double* lam, const double* cabs, const int* bin_grain, const double* T,
                           const double* E, const double* w, double* K, double* Kw, cudaStream_t st);
 
@@ -51,6 +52,7 @@ struct GrainDev {
     const int* soft_off;    // [G+1] start of each grain's soft list
     const PointEnt* pent;   // point-rule entries, column by column (u descending within a column)
     const int* pcol;        // [nbt + 1] entries of column j of grain g at pcol[off_g + j] .. pcol[off_g + j + 1]
+    const int* kexp;        // [nbt] biased binary exponent of max_lambda K[i][lambda] (-100000: none)
 };
 
 // Per-chunk scratch.
@@ -77,6 +79,7 @@ struct ChunkDev {
     int* status;
     int small;          // 1: the solve has few cells (kSmallCells): element-parallel kernels
     int point;          // 1: point-rule heating (HEAT_HEATING_POINT, FP64 build only)
+    int prune;          // L > 0: stop a spectrum's recursion at the tail test with threshold 2^-L; 0: off
 };
 
 // Solves of at most this many cells use the element-parallel build and recursion (a block

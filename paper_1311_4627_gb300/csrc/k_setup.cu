@@ -125,6 +125,24 @@ cudaError_t launch_planck(int N, int nbt, const double* lam, const double* cabs,
     return cudaGetLastError();
 }
 
+// Binary exponent (biased, as stored in the double) of Kmax_i = max_lambda K[i][lambda], the
+// largest emission kernel of bin i; warp per bin.  -100000 where the bin emits nothing on the grid.
+__global__ void k_kexp(int N, int nbt, const double* __restrict__ K, int* __restrict__ kexp) {
+    const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= nbt) return;
+    double m = 0.0;
+    for (int n = lane; n < N; n += 32) m = fmax(m, K[(size_t)w * N + n]);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) kexp[w] = m > 0.0 ? ((__double2hiint(m) >> 20) & 0x7ff) : -100000;
+}
+
+cudaError_t launch_kexp(int N, int nbt, const double* K, int* kexp, cudaStream_t st) {
+    const long long threads = (long long)nbt * 32;
+    k_kexp<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(N, nbt, K, kexp);
+    return cudaGetLastError();
+}
+
 cudaError_t set_gauss_legendre(const double* x, const double* w) {
     cudaError_t e = cudaMemcpyToSymbol(c_gl_x, x, sizeof(double) * kGLPoints);
     if (e != cudaSuccess) return e;

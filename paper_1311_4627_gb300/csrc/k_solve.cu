@@ -289,7 +289,17 @@ __device__ __forceinline__ void window_tail(int nreg, const typename BandRaw<BUI
 // (its last min(width, W) elements), prefetched one row ahead.  The row loop's fixed
 // cost grows with W, so grains whose rows are all narrow (the large grains: nearly a
 // chain) use a small W.
-template <int BUILD, int W>
+//
+// PRUNE (heat_opts.prune_eps > 0, threshold 2^-L): a row f is "small" for a cell when both
+// X_f < 2^-L max_{i<=f} X_i and X_f Kmax_f < 2^-L max_{i<=f} X_i Kmax_i (Kmax_i: the bin's
+// largest emission kernel over the grid), tested on binary exponents.  Once every row of
+// the band window [f - width_f, f] is small, the cell's X_f' for f' > f are set to zero:
+// X_f' is a combination of the window's values only, so beyond this point the spectrum
+// carries no more than a 2^-L share of the probability or of any wavelength's emission,
+// unless it grows again (which a steady state past its mode does not).  The decision is per
+// cell, so results do not depend on which cells share a warp; the warp leaves the row loop
+// once all its cells have stopped.
+template <int BUILD, int W, bool PRUNE>
 __device__ __forceinline__ void recur_task(const GrainDev& gd, const ChunkDev& ch, int g, int grp, int lane) {
     using Raw = BandRaw<BUILD>;
     const int nbt = gd.nbt;
@@ -333,7 +343,15 @@ __device__ __forceinline__ void recur_task(const GrainDev& gd, const ChunkDev& c
     // 128-byte line of element pf + k (lines of all 32 lanes of one element)
     const size_t lane_base = bb - lane;
     int pf = e;
+    // tail pruning state: running maxima of the true binary exponents (epoch included) of X
+    // and of X Kmax, the last row that was not small, whether this cell has stopped
+    const int* kx = gd.kexp + off;
+    int xmax = 1023, cmax = 0, last_big = 0, f_last = M;
+    bool stopped = false;
+    if constexpr (PRUNE) cmax = 1023 + kx[0];
     for (int f = 1; f <= M; ++f) {
+        int kf = 0;
+        if constexpr (PRUNE) kf = kx[f];
         // next row's loads
         const bool more = f < M;
         const int e3 = f + 2 <= M ? rp[f + 3] : e2;
@@ -401,7 +419,20 @@ __device__ __forceinline__ void recur_task(const GrainDev& gd, const ChunkDev& c
         double X = S * ic;
         if (__double2hiint(ic) == 0 && __double2loint(ic) == 0) {  // zero cooling rate
             X = 0.0;
-            if (S != 0.0) numeric_bad = true;
+            if (S != 0.0 && !(PRUNE && stopped)) numeric_bad = true;
+        }
+        if constexpr (PRUNE) {
+            if (stopped) {
+                X = 0.0;
+            } else {
+                const int L = ch.prune;
+                const int xe = ((__double2hiint(X) >> 20) & 0x7ff) + 800 * epoch;
+                const int ce = xe + kf;
+                xmax = max(xmax, xe);
+                cmax = max(cmax, ce);
+                if (!(xe < xmax - L && ce < cmax - L)) last_big = f;
+                stopped = last_big < f - width;
+            }
         }
         xl[f * 32] = X;
         epl[f * 32] = (unsigned short)epoch;
@@ -420,6 +451,12 @@ __device__ __forceinline__ void recur_task(const GrainDev& gd, const ChunkDev& c
 #pragma unroll
             for (int k = 0; k < W; ++k) w[k] *= kRescaleSmall;
         }
+        if constexpr (PRUNE) {
+            if (__all_sync(0xffffffffu, stopped)) {
+                f_last = f;
+                break;
+            }
+        }
         // rotate the row pipeline
         e = e1;
         e1 = e2;
@@ -433,7 +470,8 @@ __device__ __forceinline__ void recur_task(const GrainDev& gd, const ChunkDev& c
         double* prow = ch.P + (size_t)cc * ch.ldP + off;
         double emit = 0.0;
         const double* cde = gd.cde + off;
-        for (int i = 0; i <= M; ++i) {
+        const int i_end = PRUNE ? f_last : M;
+        for (int i = 0; i <= i_end; ++i) {
             const int d = epoch - (int)epl[i * 32];  // rescales this value has not seen
             const double x = xl[i * 32];
             // scale X first (as the plain rescale would have), then normalise: the factor
@@ -442,6 +480,8 @@ __device__ __forceinline__ void recur_task(const GrainDev& gd, const ChunkDev& c
             prow[i] = p;
             if (ch.ledger) emit = fma(p, cde[i], emit);
         }
+        if constexpr (PRUNE)
+            for (int i = f_last + 1; i <= M; ++i) prow[i] = 0.0;  // rows past a pruned tail
         if (ch.ledger) {
             double* lg = ch.ledger + ((size_t)cc * gd.G + g) * 2;
             lg[0] = ch.pabs[(size_t)cc * gd.G + g];
@@ -451,7 +491,7 @@ __device__ __forceinline__ void recur_task(const GrainDev& gd, const ChunkDev& c
     if (numeric_bad) atomicOr(ch.status, kStatNumeric);
 }
 
-template <int BUILD>
+template <int BUILD, bool PRUNE>
 __global__ void __launch_bounds__(128, 4) k_recur(GrainDev gd, ChunkDev ch) {
     const int task = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -459,13 +499,13 @@ __global__ void __launch_bounds__(128, 4) k_recur(GrainDev gd, ChunkDev ch) {
     const int g = ch.tasks[task].x, grp = ch.tasks[task].y;
     const int wm = gd.wmax[g];  // warp-uniform
     if (wm <= 1)
-        recur_task<BUILD, 1>(gd, ch, g, grp, lane);
+        recur_task<BUILD, 1, PRUNE>(gd, ch, g, grp, lane);
     else if (wm <= 2)
-        recur_task<BUILD, 2>(gd, ch, g, grp, lane);
+        recur_task<BUILD, 2, PRUNE>(gd, ch, g, grp, lane);
     else if (wm <= 4)
-        recur_task<BUILD, 4>(gd, ch, g, grp, lane);
+        recur_task<BUILD, 4, PRUNE>(gd, ch, g, grp, lane);
     else
-        recur_task<BUILD, 8>(gd, ch, g, grp, lane);
+        recur_task<BUILD, 8, PRUNE>(gd, ch, g, grp, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -626,9 +666,9 @@ __global__ void __launch_bounds__(256) k_build_small(GrainDev gd, ChunkDev ch) {
 }
 
 // Warp per spectrum, lanes over each row's band; X history in shared memory
-// (dynamic: max_bins doubles per warp).  Same recursion (Eq. xf), rescale and normalisation
-// as k_recur; each row's sum is reduced across lanes.
-template <int BUILD>
+// (dynamic: max_bins doubles per warp).  Same recursion (Eq. xf), rescale, normalisation and
+// tail pruning as k_recur; each row's sum is reduced across lanes.
+template <int BUILD, bool PRUNE>
 __global__ void __launch_bounds__(128) k_recur_small(GrainDev gd, ChunkDev ch) {
     extern __shared__ double smx[];
     const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -647,6 +687,9 @@ __global__ void __launch_bounds__(128) k_recur_small(GrainDev gd, ChunkDev ch) {
     bool numeric_bad = false;
     if (lane == 0) xs[0] = 1.0;
     double total = 1.0;
+    const int* kx = gd.kexp + off;
+    const int L = ch.prune;
+    int xmax = 1023, cmax = PRUNE ? 1023 + kx[0] : 0, last_big = 0, f_last = M, shift = 0;
     __syncwarp();
     for (int f = 1; f <= M; ++f) {
         const int e0 = rp[f], width = rp[f + 1] - e0, j0 = f - width;
@@ -663,18 +706,32 @@ __global__ void __launch_bounds__(128) k_recur_small(GrainDev gd, ChunkDev ch) {
         }
         if (lane == 0) xs[f] = X;
         total += X;
+        bool stop = false;
+        if (PRUNE) {  // the same test as k_recur, on lane-uniform values
+            const int xe = ((__double2hiint(X) >> 20) & 0x7ff) + shift;
+            const int ce = xe + kx[f];
+            xmax = max(xmax, xe);
+            cmax = max(cmax, ce);
+            if (!(xe < xmax - L && ce < cmax - L)) last_big = f;
+            stop = last_big < f - width;
+        }
         if (above_rescale(X)) {
             __syncwarp();
             for (int i = lane; i <= f; i += 32) xs[i] *= kRescaleSmall;
             total *= kRescaleSmall;
+            shift += 800;
         }
         __syncwarp();
+        if (stop) {
+            f_last = f;
+            break;
+        }
     }
     const double inv = 1.0 / total;
     double* prow = ch.P + (size_t)cell * ch.ldP + off;
     double emit = 0.0;
     for (int i = lane; i <= M; i += 32) {
-        const double p = xs[i] * inv;
+        const double p = i <= f_last ? xs[i] * inv : 0.0;
         prow[i] = p;
         emit = fma(p, gd.cde[off + i], emit);
     }
@@ -823,25 +880,20 @@ cudaError_t launch_recur(const GrainDev& g, const ChunkDev& ch, int build, cudaS
         const long long warps = (long long)ch.cells * g.G;
         if (warps == 0) return cudaSuccess;
         const size_t smem = sizeof(double) * 4 * (size_t)g.max_bins;  // 4 warps per block
+        auto kern = build == 0 ? (ch.prune ? k_recur_small<0, true> : k_recur_small<0, false>)
+                               : (ch.prune ? k_recur_small<1, true> : k_recur_small<1, false>);
         if (smem > 48 * 1024) {
-            cudaError_t e = build == 0 ? cudaFuncSetAttribute(k_recur_small<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                              (int)smem)
-                                       : cudaFuncSetAttribute(k_recur_small<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                              (int)smem);
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
         const unsigned blocks = (unsigned)((warps + 3) / 4);
-        if (build == 0)
-            k_recur_small<0><<<blocks, 128, smem, st>>>(g, ch);
-        else
-            k_recur_small<1><<<blocks, 128, smem, st>>>(g, ch);
+        kern<<<blocks, 128, smem, st>>>(g, ch);
         return cudaGetLastError();
     }
     int threads = 128, blocks = (ch.n_tasks + 3) / 4;
-    if (build == 0)
-        k_recur<0><<<blocks, threads, 0, st>>>(g, ch);
-    else
-        k_recur<1><<<blocks, threads, 0, st>>>(g, ch);
+    auto kern = build == 0 ? (ch.prune ? k_recur<0, true> : k_recur<0, false>)
+                           : (ch.prune ? k_recur<1, true> : k_recur<1, false>);
+    kern<<<blocks, threads, 0, st>>>(g, ch);
     return cudaGetLastError();
 }
 

@@ -42,7 +42,8 @@ class heat_opts(ctypes.Structure):
     _fields_ = [("build", ctypes.c_int), ("emis", ctypes.c_int), ("j_dtype", ctypes.c_int),
                 ("size_integrate", ctypes.c_int), ("cell_begin", ctypes.c_int), ("cell_count", ctypes.c_int),
                 ("chunk_cells", ctypes.c_int), ("host_io", ctypes.c_int), ("timing", ctypes.c_int),
-                ("ledger_out", ctypes.c_void_p), ("streams", ctypes.c_int), ("heating", ctypes.c_int)]
+                ("ledger_out", ctypes.c_void_p), ("streams", ctypes.c_int), ("heating", ctypes.c_int),
+                ("prune_eps", ctypes.c_double)]
 
 
 _lib = None
@@ -146,7 +147,7 @@ def heat_default_opts(**kw) -> heat_opts:
     o = heat_opts()
     lib().heat_default_opts(ctypes.byref(o))
     for k, v in kw.items():
-        setattr(o, k, _ptr(v) if k == "ledger_out" else int(v))
+        setattr(o, k, _ptr(v) if k == "ledger_out" else (float(v) if k == "prune_eps" else int(v)))
     return o
 
 

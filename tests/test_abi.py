@@ -31,12 +31,13 @@ def test_library_exports_every_declared_symbol(libheat):
 def test_default_opts_and_null_handling(libheat):
     o = heat.heat_default_opts()
     assert (o.build, o.emis, o.j_dtype, o.size_integrate, o.host_io) == (0, 0, 0, 0, 0)
-    assert (o.streams, o.heating) == (0, heat.HEAT_HEATING_INTEGRAL)
+    assert (o.streams, o.heating, o.prune_eps) == (0, heat.HEAT_HEATING_INTEGRAL, 0.0)
     # the binding's struct ends where the library's does: the last field is written by
     # heat_default_opts, so a poisoned value there must be overwritten
     o.heating = 12345
+    o.prune_eps = 0.5
     libheat.heat_default_opts(ctypes.byref(o))
-    assert o.heating == heat.HEAT_HEATING_INTEGRAL
+    assert o.heating == heat.HEAT_HEATING_INTEGRAL and o.prune_eps == 0.0
     # null contexts are rejected without touching a device
     assert libheat.heat_sync(None) == heat.HEAT_EINVAL
     assert libheat.heat_solve(None, ctypes.byref(o), None, None, None) == heat.HEAT_EINVAL
