@@ -110,6 +110,24 @@ __device__ __forceinline__ double e1d(double z) {
     return z == 0.0 ? 1.0 : expm1(z) / z;
 }
 
+// Compensated FP32 running sum (Knuth's TwoSum error term collected in c): s + c carries the
+// sum of non-negative FP32 terms to about 2^-46 relative, on the FP32 pipes (a GB300 SM
+// sub-partition's FP64 unit takes 64 cycles per warp instruction).  val() rounds it to FP32.
+// The _rn intrinsics keep the compiler from fusing a product that feeds add() into an FMA,
+// so the sum is the same wherever the term comes from.
+struct Sum32 {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = __fadd_rn(s, x);
+        const float bp = __fsub_rn(t, s);
+        const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+        s = t;
+        c = __fadd_rn(c, err);
+    }
+    __device__ __forceinline__ float val() const { return __fadd_rn(s, c); }
+    __device__ __forceinline__ double wide() const { return (double)s + (double)c; }
+};
+
 // Widen a non-negative finite float to double with integer operations only
 // (rebias the exponent, shift the mantissa); zero and subnormals map to 0.
 // Keeps the conversion off the FP64 pipe, which is the bound of the recursion.

@@ -71,7 +71,8 @@ __global__ void k_field(int N, const double* __restrict__ dln, const TU* __restr
 // per cell.  With Omega = u C on the log-log interpolant (Eq. interpolation), slope
 // s_n and q = s_n + p + 1 on segment n:
 //   segment integral   int Omega lambda^p = Omega_n lambda_n^{p+1} dln_n E1(q dln_n)
-//   photon prefix      Phi_n = (1/h) sum_{m<n} int_m Omega lambda       (FP64 cumulative sum)
+//   photon prefix      Phi_n = (1/h) sum_{m<n} int_m Omega lambda       (cumulative sum: FP64 in
+//                      the FP64 build, compensated FP32 in the FP32 build)
 //   band element       B_fj = Phi(lambda_fj) = Phi_n + (Omega_n lambda_n^2/h) t E1(q t)
 //                      (Eq. bmatrix telescoped: the bins' wavelength ranges tile [0, lambda_fj])
 //   intra-bin term     W_j = c int_{hc/(Elo_{j+1}-E_j)}^{lambda_{N-1}} Omega, added to the diagonal
@@ -152,11 +153,12 @@ __global__ void __launch_bounds__(128) k_build(GrainDev gd, ChunkDev ch) {
         const float2* uasu = (const float2*)ch.ua32;
         float* Bb = ch.Bb32 + bb;
         float2 us_next = uasu[cc];
+        Sum32 Phi32;  // the photon prefix, compensated in FP32
         for (int n = 0; n < N - 1; ++n) {
             float2 us = us_next;
             if (n + 1 < N - 1) us_next = uasu[(size_t)(n + 1) * Cc + cc];  // one segment ahead
             float ua = us.x, su = us.y;
-            float phi = __double2float_rn(Phi);
+            float phi = Phi32.val();
             int k = sp[n], k1 = sp[n + 1];
             // every element's argument is z = q t with t in [0, dln]: when |q| dln <= 1/4 the
             // short series serves the whole segment.  The test is per lane (per cell), so a
@@ -185,10 +187,10 @@ __global__ void __launch_bounds__(128) k_build(GrainDev gd, ChunkDev ch) {
             float a = ua * ca[n];
             if (a > 0.0f) {
                 float dl = gd.dln32[n];
-                Phi += widen_pos(a * dl * e1f((su + sC[n] + 2.0f) * dl));
+                Phi32.add(a * dl * e1f((su + sC[n] + 2.0f) * dl));
             }
         }
-        float phi_end = __double2float_rn(Phi);
+        float phi_end = Phi32.val();
         for (int k = sp[N - 1]; k < sp[N]; ++k) Bb[gd.pat32[k].e * 32] = phi_end;
 
         auto put32 = [&](const SoftF64& sf, float v) {
@@ -199,7 +201,7 @@ __global__ void __launch_bounds__(128) k_build(GrainDev gd, ChunkDev ch) {
             put32(soft[p], 0.0f);
             ++p;
         }
-        double Psi = 0.0;  // c int Omega from lambda_{n+1} to lambda_{N-1} (FP64 cumulative sum)
+        Sum32 Psi32;  // c int Omega from lambda_{n+1} to lambda_{N-1} (compensated FP32 sum)
         us_next = uasu[(size_t)(N - 2) * Cc + cc];
         for (int n = N - 2; n >= 0; --n) {
             float2 us = us_next;
@@ -216,14 +218,14 @@ __global__ void __launch_bounds__(128) k_build(GrainDev gd, ChunkDev ch) {
                     float L = dl - ts;
                     part = b * __expf(q0 * ts) * L * e1f(q0 * L);
                 }
-                put32(sf, (part + __double2float_rn(Psi)) * gd.invdE32[off + sf.j]);
+                put32(sf, (part + Psi32.val()) * gd.invdE32[off + sf.j]);
                 ++p;
             }
-            if (b > 0.0f) Psi += widen_pos(b * dl * e1f(q0 * dl));
+            if (b > 0.0f) Psi32.add(b * dl * e1f(q0 * dl));
         }
-        float psi_end = __double2float_rn(Psi);
+        float psi_end = Psi32.val();
         for (; p < p1; ++p) put32(soft[p], psi_end * gd.invdE32[off + soft[p].j]);
-        if (ch.pabs) ch.pabs[(size_t)cc * gd.G + g] = Psi;
+        if (ch.pabs) ch.pabs[(size_t)cc * gd.G + g] = Psi32.wide();
     }
 }
 
@@ -537,6 +539,7 @@ __global__ void __launch_bounds__(256) k_build_small(GrainDev gd, ChunkDev ch) {
     double* sPhi = sm;          // [N]: Phi before segment n (exclusive prefix), then Phi at the end
     double* sPsi = sm + gd.N;   // [N]: Psi after the segments above n (exclusive suffix)
     __shared__ double sPhiEnd, sPsiTot;
+    __shared__ float sPsiEnd32;  // FP32 build: the FP32 value of the compensated total
     const int N = gd.N, Cc = ch.Cc;
     const int cell = blockIdx.x / gd.G, g = blockIdx.x % gd.G;
     if (cell >= ch.cells) return;
@@ -568,23 +571,45 @@ __global__ void __launch_bounds__(256) k_build_small(GrainDev gd, ChunkDev ch) {
         sPsi[n] = dpsi;
     }
     __syncthreads();
-    // 2. the cumulative sums, in the lane-per-cell kernel's order
+    // 2. the cumulative sums, in the lane-per-cell kernel's order and arithmetic (FP64 build:
+    // FP64 sums; FP32 build: compensated FP32 sums, whose FP32 values are kept)
     if (tid == 0) {
-        double Phi = 0.0;
-        for (int n = 0; n < N - 1; ++n) {
-            const double d = sPhi[n];
-            sPhi[n] = Phi;
-            Phi += d;
+        if (BUILD == 0) {
+            double Phi = 0.0;
+            for (int n = 0; n < N - 1; ++n) {
+                const double d = sPhi[n];
+                sPhi[n] = Phi;
+                Phi += d;
+            }
+            sPhiEnd = Phi;
+        } else {
+            Sum32 Phi;
+            for (int n = 0; n < N - 1; ++n) {
+                const float d = (float)sPhi[n];
+                sPhi[n] = Phi.val();
+                Phi.add(d);
+            }
+            sPhiEnd = Phi.val();
         }
-        sPhiEnd = Phi;
     } else if (tid == 32) {
-        double Psi = 0.0;
-        for (int n = N - 2; n >= 0; --n) {
-            const double d = sPsi[n];
-            sPsi[n] = Psi;
-            Psi += d;
+        if (BUILD == 0) {
+            double Psi = 0.0;
+            for (int n = N - 2; n >= 0; --n) {
+                const double d = sPsi[n];
+                sPsi[n] = Psi;
+                Psi += d;
+            }
+            sPsiTot = Psi;
+        } else {
+            Sum32 Psi;
+            for (int n = N - 2; n >= 0; --n) {
+                const float d = (float)sPsi[n];
+                sPsi[n] = Psi.val();
+                Psi.add(d);
+            }
+            sPsiTot = Psi.wide();
+            sPsiEnd32 = Psi.val();
         }
-        sPsiTot = Psi;
     }
     __syncthreads();
     // 3. band elements: warp per segment, lanes over its pattern entries
@@ -656,7 +681,7 @@ __global__ void __launch_bounds__(256) k_build_small(GrainDev gd, ChunkDev ch) {
                 }
                 v = (part + __double2float_rn(sPsi[sf.n])) * gd.invdE32[off + sf.j];
             } else {
-                v = __double2float_rn(sPsiTot) * gd.invdE32[off + sf.j];
+                v = sPsiEnd32 * gd.invdE32[off + sf.j];
             }
             float* q = ch.Bb32 + bb + (size_t)sf.e_diag * 32;
             *q = (sf.diag_in_band ? *q : 0.0f) + v;
