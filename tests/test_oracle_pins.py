@@ -403,6 +403,32 @@ def test_large_grain_reaches_thermal_equilibrium(radius):
     assert abs(led[0, 0, 0] / led[0, 0, 1] - 1.0) < 1e-10
 
 
+@pytest.mark.parametrize("T_rad", [60.0, 300.0])
+def test_undiluted_blackbody_gives_the_canonical_mean_energy(T_rad):
+    """Inside an undiluted blackbody a grain of any size is in equilibrium with the field, so
+    the mean enthalpy of P is the canonical one, H(T_rad) (Kirchhoff; H from the Debye model of
+    the inputs, interpolated on the bin grid).  The thermal-continuous cooling of Eq. adjacent
+    is not exact detailed balance, so for the smallest grains the mean is only close (within
+    10 %) and the variance of H falls short of the canonical k T^2 C: for 5 A it is
+    0.4-0.7 of it, the narrowing a drift-only cooling term gives (an exact Boltzmann P needs
+    exact-statistical cooling).  From 20 A up the mean agrees to 2 %."""
+    k = W.K_BOLTZ
+    lam = W.wavelength_grid(512)
+    for a in (5e-8, 10e-8, 20e-8, 50e-8, 250e-8):
+        wl = W.custom(lam, [a], ["carbonaceous"], [512], W.blackbody_field(lam, T_rad)[None, :])
+        P, _, _, st = oracle.solve_batch(wl, oracle.grain_cooling(wl), want_j=False)
+        assert st == oracle.OK
+        p, E, T = P[0], wl.E, wl.T
+        H = lambda t: math.exp(float(np.interp(math.log(t), np.log(T), np.log(E))))
+        Em = float(np.sum(p * E))
+        tol = 0.10 if a < 20e-8 else 0.02
+        assert abs(Em / H(T_rad) - 1.0) < tol, (a, Em / H(T_rad))
+        if a == 5e-8:
+            Cv = (H(1.001 * T_rad) - H(0.999 * T_rad)) / (0.002 * T_rad)
+            ratio = float(np.sum(p * (E - Em) ** 2)) / (k * T_rad**2 * Cv)
+            assert 0.3 < ratio < 0.8, ratio
+
+
 @pytest.mark.parametrize("radius", [0.25e-4, 1.0e-4])
 def test_large_grain_in_a_diluted_field_sits_at_the_balance_temperature(radius):
     """A large grain in a diluted 5000 K blackbody: T_eq from c int u C dlambda =
