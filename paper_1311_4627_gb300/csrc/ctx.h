@@ -71,7 +71,7 @@ struct heat_ctx {
     // tensor-core emissivity of the next
     static constexpr int kMaxSlots = 4;
     struct Slot {
-        DevBuf ua64, su64, ua32, Bb64, Bb32, xs, ep, pabs, P, j, led, A, rowscale;
+        DevBuf ua64, su64, ua32, Bb64, Bb32, xs, ep, pabs, P, j, led, A, rowscale, work;
         cudaStream_t stream = nullptr;  // created on first use
         cudaEvent_t done = nullptr;
     } slots[kMaxSlots];

@@ -709,6 +709,7 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
         ok &= !sl.xs.ensure(sizeof(double) * (size_t)NG * nbt * 32);
         ok &= !sl.ep.ensure(sizeof(unsigned short) * (size_t)NG * nbt * 32);
         ok &= !sl.pabs.ensure(sizeof(double) * (size_t)Cc * G);
+        ok &= !sl.work.ensure(sizeof(int) * 2);
         if (internal_P) ok &= !sl.P.ensure(sizeof(double) * (size_t)Cc * nbt);
         if (want_j && o.host_io) ok &= !sl.j.ensure(jel * (size_t)Cc * jrow);
         if (o.ledger_out && o.host_io) ok &= !sl.led.ensure(sizeof(double) * 2 * (size_t)Cc * G);
@@ -792,6 +793,8 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
         ch.ledger = !o.ledger_out ? nullptr
                     : (o.host_io ? sl.led.as<double>() : o.ledger_out + (size_t)c0 * G * 2);
         long long cell0 = (long long)c_begin + c0;
+        ch.work = sl.work.as<int>();
+        CKR(cudaMemsetAsync(ch.work, 0, sizeof(int) * 2, cs));
         TIMED(HEAT_T_FIELD, launch_field(gd, ctx->u_dev, ctx->u_dtype, cell0, ch, build, cs));
         TIMED(HEAT_T_BUILD, launch_build(gd, ch, build, cs));
         TIMED(HEAT_T_RECUR, launch_recur(gd, ch, build, cs));
@@ -1066,7 +1069,7 @@ void heat_destroy(heat_ctx* ctx) {
     for (DevBuf* b : bufs) b->release();
     for (auto& sl : ctx->slots) {
         DevBuf* sb[] = {&sl.ua64, &sl.su64, &sl.ua32, &sl.Bb64, &sl.Bb32, &sl.xs, &sl.ep,
-                        &sl.pabs, &sl.P, &sl.j, &sl.led, &sl.A, &sl.rowscale};
+                        &sl.pabs, &sl.P, &sl.j, &sl.led, &sl.A, &sl.rowscale, &sl.work};
         for (DevBuf* b : sb) b->release();
         if (sl.stream) cudaStreamDestroy(sl.stream);
         if (sl.done) cudaEventDestroy(sl.done);

@@ -80,6 +80,8 @@ struct ChunkDev {
     int small;          // 1: the solve has few cells (kSmallCells): element-parallel kernels
     int point;          // 1: point-rule heating (HEAT_HEATING_POINT, FP64 build only)
     int prune;          // L > 0: stop a spectrum's recursion at the tail test with threshold 2^-L; 0: off
+    int* work;          // [2] task counters of the persistent launches (the recursion uses [1]), zero
+                        //   before the launches; null: one warp per task
 };
 
 // Solves of at most this many cells use the element-parallel build and recursion (a block

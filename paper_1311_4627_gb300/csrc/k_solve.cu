@@ -82,10 +82,7 @@ __global__ void k_field(int N, const double* __restrict__ dln, const TU* __restr
 // falls in the current segment (the grain's pattern list) is written to the band
 // storage Bb, so the recursion streams B instead of gathering tables.
 template <int BUILD>
-__global__ void __launch_bounds__(128) k_build(GrainDev gd, ChunkDev ch) {
-    int task = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    int lane = threadIdx.x & 31;
-    if (task >= ch.n_tasks) return;
+__device__ __forceinline__ void build_task(const GrainDev& gd, const ChunkDev& ch, int task, int lane) {
     const int N = gd.N, Cc = ch.Cc;
     const int2 tk = (ch.btasks ? ch.btasks : ch.tasks)[task];
     int g = tk.x, grp = tk.y;
@@ -227,6 +224,31 @@ __global__ void __launch_bounds__(128) k_build(GrainDev gd, ChunkDev ch) {
         for (; p < p1; ++p) put32(soft[p], psi_end * gd.invdE32[off + soft[p].j]);
         if (ch.pabs) ch.pabs[(size_t)cc * gd.G + g] = Psi32.wide();
     }
+}
+
+// Task loop of the persistent launches: with ch.work set, each warp takes the next task of
+// the list from an atomic counter (dynamic scheduling per warp, in the list's order, as the
+// paper's dynamic OpenMP schedule does per thread); without it, one warp per task.
+template <typename F>
+__device__ __forceinline__ void for_each_task(const ChunkDev& ch, int counter, F&& run) {
+    const int lane = threadIdx.x & 31;
+    if (!ch.work) {
+        const int task = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+        if (task < ch.n_tasks) run(task, lane);
+        return;
+    }
+    for (;;) {
+        int task = 0;
+        if (lane == 0) task = atomicAdd(ch.work + counter, 1);
+        task = __shfl_sync(0xffffffffu, task, 0);
+        if (task >= ch.n_tasks) return;
+        run(task, lane);
+    }
+}
+
+template <int BUILD>
+__global__ void __launch_bounds__(128) k_build(GrainDev gd, ChunkDev ch) {
+    for_each_task(ch, 0, [&](int task, int lane) { build_task<BUILD>(gd, ch, task, lane); });
 }
 
 // ---------------------------------------------------------------------------
@@ -495,19 +517,18 @@ __device__ __forceinline__ void recur_task(const GrainDev& gd, const ChunkDev& c
 
 template <int BUILD, bool PRUNE>
 __global__ void __launch_bounds__(128, 4) k_recur(GrainDev gd, ChunkDev ch) {
-    const int task = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (task >= ch.n_tasks) return;
-    const int g = ch.tasks[task].x, grp = ch.tasks[task].y;
-    const int wm = gd.wmax[g];  // warp-uniform
-    if (wm <= 1)
-        recur_task<BUILD, 1, PRUNE>(gd, ch, g, grp, lane);
-    else if (wm <= 2)
-        recur_task<BUILD, 2, PRUNE>(gd, ch, g, grp, lane);
-    else if (wm <= 4)
-        recur_task<BUILD, 4, PRUNE>(gd, ch, g, grp, lane);
-    else
-        recur_task<BUILD, 8, PRUNE>(gd, ch, g, grp, lane);
+    for_each_task(ch, 1, [&](int task, int lane) {
+        const int g = ch.tasks[task].x, grp = ch.tasks[task].y;
+        const int wm = gd.wmax[g];  // warp-uniform
+        if (wm <= 1)
+            recur_task<BUILD, 1, PRUNE>(gd, ch, g, grp, lane);
+        else if (wm <= 2)
+            recur_task<BUILD, 2, PRUNE>(gd, ch, g, grp, lane);
+        else if (wm <= 4)
+            recur_task<BUILD, 4, PRUNE>(gd, ch, g, grp, lane);
+        else
+            recur_task<BUILD, 8, PRUNE>(gd, ch, g, grp, lane);
+    });
 }
 
 // ---------------------------------------------------------------------------
@@ -843,6 +864,21 @@ __global__ void __launch_bounds__(128) k_build_point_small(GrainDev gd, ChunkDev
     if (threadIdx.x == 0 && ch.pabs) ch.pabs[(size_t)cell * gd.G + g] = absorbed_power(gd, ch, g, cell);
 }
 
+// Blocks of 128 threads (a warp per task) for the task-list kernels: one per 4 tasks, or, for
+// the persistent launches (ch.work set), no more than stay resident on the device at once.
+template <typename K>
+static unsigned task_grid(K kernel, const ChunkDev& ch) {
+    const unsigned full = (unsigned)((ch.n_tasks + 3) / 4);
+    if (!ch.work) return full;
+    int dev = 0, sms = 0, occ = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 128, 0) != cudaSuccess)
+        return full;
+    const unsigned cap = (unsigned)(sms > 0 && occ > 0 ? sms * occ : 1);
+    return full < cap ? full : cap;
+}
+
 cudaError_t launch_field(const GrainDev& g, const void* u, int dtype, long long cell0, const ChunkDev& ch, int build,
                          cudaStream_t st) {
     dim3 block(32, 8), grid((g.N + 31) / 32, ch.Cc / 32);
@@ -892,11 +928,13 @@ cudaError_t launch_build(const GrainDev& g, const ChunkDev& ch, int build, cudaS
             k_build_small<1><<<blocks, 256, smem, st>>>(g, ch);
         return cudaGetLastError();
     }
-    int threads = 128, blocks = (ch.n_tasks + 3) / 4;
-    if (build == 0)
-        k_build<0><<<blocks, threads, 0, st>>>(g, ch);
-    else
-        k_build<1><<<blocks, threads, 0, st>>>(g, ch);
+    if (ch.n_tasks == 0) return cudaSuccess;
+    // one warp per task: every task of a chunk fits on the device at once (39 registers,
+    // up to 16 blocks per SM), so a persistent launch only adds the counter traffic
+    ChunkDev c1 = ch;
+    c1.work = nullptr;
+    auto kern = build == 0 ? k_build<0> : k_build<1>;
+    kern<<<task_grid(kern, c1), 128, 0, st>>>(g, c1);
     return cudaGetLastError();
 }
 
@@ -915,10 +953,10 @@ cudaError_t launch_recur(const GrainDev& g, const ChunkDev& ch, int build, cudaS
         kern<<<blocks, 128, smem, st>>>(g, ch);
         return cudaGetLastError();
     }
-    int threads = 128, blocks = (ch.n_tasks + 3) / 4;
+    if (ch.n_tasks == 0) return cudaSuccess;
     auto kern = build == 0 ? (ch.prune ? k_recur<0, true> : k_recur<0, false>)
                            : (ch.prune ? k_recur<1, true> : k_recur<1, false>);
-    kern<<<blocks, threads, 0, st>>>(g, ch);
+    kern<<<task_grid(kern, ch), 128, 0, st>>>(g, ch);
     return cudaGetLastError();
 }
 
