@@ -551,17 +551,20 @@ def main():
     # the same solve captured once into a CUDA graph and replayed (heat_graph_*), L2 flushed
     # between replays as above
     if ws == 1:
-        g = heat.Graph(ctx, opts_for(args.path), None, j, sh)
+        gs = torch.cuda.Stream(dev)  # stream capture needs a stream other than the legacy default
+        torch.cuda.synchronize(dev)
+        g = heat.Graph(ctx, opts_for(args.path), None, j, gs.cuda_stream)
         for _ in range(2):
-            g.launch(sh)
+            g.launch(gs.cuda_stream)
         torch.cuda.synchronize(dev)
         gms = []
         for _ in range(args.steps):
-            flush.zero_()
+            with torch.cuda.stream(gs):
+                flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            g.launch(sh)
-            e1.record(stream)
+            e0.record(gs)
+            g.launch(gs.cuda_stream)
+            e1.record(gs)
             torch.cuda.synchronize(dev)
             gms.append(e0.elapsed_time(e1))
         heat.heat_sync(ctx)
