@@ -18,7 +18,7 @@ cudaError_t launch_kexp(int N, int nbt, const double* K, int* kexp, cudaStream_t
 cudaError_t launch_planck(int N, int nbt, const double* lam, const double* cabs, const int* bin_grain, const double* T,
                           const double* E, const double* w, double* K, double* Kw, cudaStream_t st);
 
-// ---- per-solve kernels (k_solve.cu)
+// ---- per-solve kernels (k_build.cu: field, build; k_recur.cu: recursion)
 
 // Per-grain device tables consumed by the solve kernels.
 struct GrainDev {
