@@ -93,8 +93,15 @@ typedef struct heat_opts {
     int cell_count;     /* cells solved; <= 0 means all cells from cell_begin                      */
     int chunk_cells;    /* cells per internal chunk (multiple of 32; 0 = library default: as many
                            as 45 % of the usable device memory holds)                             */
-    int host_io;        /* 1: P_out and j_out are host pointers; the library stages through device
-                           memory and the call returns after the results are on the host          */
+    int host_io;        /* 1: P_out, j_out and ledger_out are host pointers; the library stages
+                           through device memory and the call returns after the results are on
+                           the host.  2: the same, asynchronous: the call returns once the work is
+                           queued, the copies to the host run on an internal copy stream and the
+                           host buffers are complete after heat_sync (which waits for the device);
+                           the device staging alternates between two sets, so the copies of one
+                           call overlap the kernels of the next (a pipelined loop: set the next
+                           fields, solve, ...; heat_sync before reading the results of the last
+                           two calls).  cuda_stream continues after the kernels, not the copies */
     int timing;         /* 1: record CUDA events around every kernel launch (see heat_get_timing)  */
     double* ledger_out; /* NULL, or FP64 [cell_count][n_grains][2] (device; host with host_io): the
                            energy check of every spectrum, erg/s: [0] absorbed power c int u C dlambda
@@ -104,8 +111,9 @@ typedef struct heat_opts {
     int streams;        /* chunks in flight (1..4), each on an internal stream forked from and
                            joined back into cuda_stream, so that the recursion of one chunk
                            overlaps the matrix build and emissivity of the next; 0 = the
-                           library default (heat_autotune's choice, else 1 on device buffers and
-                           2 with host_io, whose copies then overlap the other chunk's kernels).
+                           library default (heat_autotune's choice, else 1 on device buffers, 2
+                           with host_io = 1, whose copies then overlap the other chunk's kernels,
+                           and 1 with host_io = 2).
                            Results do not depend on it or on chunk_cells, except that solves of
                            at most 16 cells take element-parallel kernels (same bounds against
                            the oracle, rounding differs in the last bits)                      */
@@ -175,7 +183,7 @@ heat_status heat_set_fields(heat_ctx* ctx, int n_cells, const void* u_lambda, in
  *   j_out  j_dtype, [cell_count][n_grains][n_lambda] (or [cell_count][n_lambda] with
  *          size_integrate) or NULL: the emissivity (Eq. emission).
  * Device pointers unless opts->host_io.  Asynchronous with respect to the host unless
- * host_io; device-side errors surface at heat_sync.  Non-interacting grains give
+ * host_io = 1; device-side errors surface at heat_sync.  Non-interacting grains give
  * P = delta_{i0} (no error).  Errors: HEAT_EINVAL, HEAT_ESTATE, HEAT_ENOMEM, HEAT_ECUDA. */
 heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void* j_out, void* cuda_stream);
 

@@ -72,11 +72,17 @@ struct heat_ctx {
     static constexpr int kMaxSlots = 4;
     struct Slot {
         DevBuf ua64, su64, ua32, Bb64, Bb32, xs, ep, pabs, P, j, led, A, rowscale, work;
+        DevBuf P_alt, j_alt, led_alt;   // second staging set of asynchronous host I/O
         cudaStream_t stream = nullptr;  // created on first use
         cudaEvent_t done = nullptr;
+        cudaStream_t copy = nullptr;    // asynchronous host I/O: copies to the host
+        cudaEvent_t computed = nullptr; // a chunk's kernels are done (copy stream waits on it)
+        cudaEvent_t copied[2] = {nullptr, nullptr};  // staging set k has been copied out
+        bool copied_valid[2] = {false, false};
     } slots[kMaxSlots];
     cudaEvent_t ev_fork = nullptr;
     int tuned_streams = 0, tuned_chunk = 0;  // heat_autotune's choice (0: none)
+    int io_parity = 0;  // staging set of the next asynchronous host-I/O solve
     DevBuf d_status;
     int sms = 0;
     std::vector<double> radius;

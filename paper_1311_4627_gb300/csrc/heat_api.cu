@@ -631,6 +631,7 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
     if (o.size_integrate && !ctx->has_w) return ctx->fail(HEAT_EINVAL, "heat_solve: size integration needs weights");
     if (o.chunk_cells < 0 || (o.chunk_cells % 32) != 0)
         return ctx->fail(HEAT_EINVAL, "heat_solve: chunk_cells must be a non-negative multiple of 32");
+    if (o.host_io < 0 || o.host_io > 2) return ctx->fail(HEAT_EINVAL, "heat_solve: host_io must be 0, 1 or 2");
     int c_begin = o.cell_begin, count = o.cell_count > 0 ? o.cell_count : ctx->n_cells - o.cell_begin;
     if (c_begin < 0 || count < 0 || c_begin + count > ctx->n_cells)
         return ctx->fail(HEAT_EINVAL, "heat_solve: cell range outside the fields");
@@ -654,10 +655,11 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
         nslots = ctx->tuned_streams;
         chunk = ctx->tuned_chunk;
     }
-    // with host buffers the default is two chunks in flight on two streams, so that one
-    // chunk's copy to the host overlaps the other's kernels (measured: ~4 % end to end on
-    // the batched workload; chaining the chunks' kernels instead was slower)
-    if (nslots == 0) nslots = (o.host_io && count >= 2 * kHostIoMinChunk) ? 2 : 1;
+    // with synchronous host buffers the default is two chunks in flight on two streams, so
+    // that one chunk's copy to the host overlaps the other's kernels (measured: ~4 % end to
+    // end on the batched workload; chaining the chunks' kernels instead was slower); with
+    // asynchronous host I/O the copies overlap the next call's kernels, so one chunk
+    if (nslots == 0) nslots = (o.host_io == 1 && count >= 2 * kHostIoMinChunk) ? 2 : 1;
     nslots = std::min(nslots, (int)heat_ctx::kMaxSlots);
     if (chunk == 0) chunk = default_chunk(ctx, build, count, nslots);
     const int n_chunks = (count + chunk - 1) / chunk;
@@ -695,6 +697,8 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
 
     // scratch of every slot in use
     bool internal_P = (P_out == nullptr) || o.host_io;
+    const bool async_io = o.host_io == 2;
+    const int io_set = async_io ? ctx->io_parity : 0;
     for (int k = 0; k < nslots; ++k) {
         auto& sl = ctx->slots[k];
         bool ok = true;
@@ -710,9 +714,14 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
         ok &= !sl.ep.ensure(sizeof(unsigned short) * (size_t)NG * nbt * 32);
         ok &= !sl.pabs.ensure(sizeof(double) * (size_t)Cc * G);
         ok &= !sl.work.ensure(sizeof(int) * 2);
-        if (internal_P) ok &= !sl.P.ensure(sizeof(double) * (size_t)Cc * nbt);
-        if (want_j && o.host_io) ok &= !sl.j.ensure(jel * (size_t)Cc * jrow);
-        if (o.ledger_out && o.host_io) ok &= !sl.led.ensure(sizeof(double) * 2 * (size_t)Cc * G);
+        // staging set of this call: asynchronous host I/O alternates between two, so that one
+        // call's copies to the host read a set that the next call does not write
+        DevBuf& stP = io_set ? sl.P_alt : sl.P;
+        DevBuf& stj = io_set ? sl.j_alt : sl.j;
+        DevBuf& stl = io_set ? sl.led_alt : sl.led;
+        if (internal_P) ok &= !(P_out && async_io ? stP : sl.P).ensure(sizeof(double) * (size_t)Cc * nbt);
+        if (want_j && o.host_io) ok &= !stj.ensure(jel * (size_t)Cc * jrow);
+        if (o.ledger_out && o.host_io) ok &= !stl.ensure(sizeof(double) * 2 * (size_t)Cc * G);
         if (tc) {
             auto& t = si ? ctx->tc_si[o.emis] : ctx->tc[o.emis];
             const int Gt = si ? 1 : G;
@@ -723,6 +732,11 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
         if (nslots > 1 && !sl.stream) {
             CKR(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking));
             CKR(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
+        }
+        if (async_io && !sl.copy) {
+            CKR(cudaStreamCreateWithFlags(&sl.copy, cudaStreamNonBlocking));
+            CKR(cudaEventCreateWithFlags(&sl.computed, cudaEventDisableTiming));
+            for (cudaEvent_t& e : sl.copied) CKR(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         }
     }
     if (nslots > 1 && !ctx->ev_fork) CKR(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
@@ -789,17 +803,24 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
         ch.pabs = sl.pabs.as<double>();
         ch.status = ctx->d_status.as<int>();
         ch.ldP = nbt;
-        ch.P = internal_P ? sl.P.as<double>() : P_out + (size_t)c0 * nbt;
+        DevBuf& stP = (P_out && async_io && io_set) ? sl.P_alt : sl.P;
+        DevBuf& stj = io_set ? sl.j_alt : sl.j;
+        DevBuf& stl = io_set ? sl.led_alt : sl.led;
+        ch.P = internal_P ? stP.as<double>() : P_out + (size_t)c0 * nbt;
         ch.ledger = !o.ledger_out ? nullptr
-                    : (o.host_io ? sl.led.as<double>() : o.ledger_out + (size_t)c0 * G * 2);
+                    : (o.host_io ? stl.as<double>() : o.ledger_out + (size_t)c0 * G * 2);
         long long cell0 = (long long)c_begin + c0;
+        // staging still being copied to the host by an earlier asynchronous call is not
+        // written before that copy is done
+        for (int k = 0; k < 2; ++k)
+            if (sl.copied_valid[k] && (!async_io || k == io_set)) CKR(cudaStreamWaitEvent(cs, sl.copied[k], 0));
         ch.work = sl.work.as<int>();
         CKR(cudaMemsetAsync(ch.work, 0, sizeof(int) * 2, cs));
         TIMED(HEAT_T_FIELD, launch_field(gd, ctx->u_dev, ctx->u_dtype, cell0, ch, build, cs));
         TIMED(HEAT_T_BUILD, launch_build(gd, ch, build, cs));
         TIMED(HEAT_T_RECUR, launch_recur(gd, ch, build, cs));
         if (want_j) {
-            char* jdst = o.host_io ? sl.j.as<char>() : (char*)j_out + (size_t)c0 * jrow * jel;
+            char* jdst = o.host_io ? stj.as<char>() : (char*)j_out + (size_t)c0 * jrow * jel;
             cudaEvent_t ta = nullptr;
             if (o.timing) {
                 ta = ctx->take_event();
@@ -820,16 +841,28 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
                 CKR(cudaEventRecord(tb, cs));
                 ctx->timed.push_back({HEAT_T_EMIS, ta, tb});
             }
-            if (o.host_io)
-                CKR(cudaMemcpyAsync((char*)j_out + (size_t)c0 * jrow * jel, jdst, (size_t)cells * jrow * jel,
-                                    cudaMemcpyDeviceToHost, cs));
         }
+        // copies to the host: on the chunk's stream (host_io = 1), or on the slot's copy
+        // stream after the chunk's kernels (host_io = 2)
+        cudaStream_t xs = cs;
+        if (async_io) {
+            CKR(cudaEventRecord(sl.computed, cs));
+            CKR(cudaStreamWaitEvent(sl.copy, sl.computed, 0));
+            xs = sl.copy;
+        }
+        if (want_j && o.host_io)
+            CKR(cudaMemcpyAsync((char*)j_out + (size_t)c0 * jrow * jel, stj.p, (size_t)cells * jrow * jel,
+                                cudaMemcpyDeviceToHost, xs));
         if (o.ledger_out && o.host_io)
             CKR(cudaMemcpyAsync(o.ledger_out + (size_t)c0 * G * 2, ch.ledger, sizeof(double) * 2 * (size_t)cells * G,
-                                cudaMemcpyDeviceToHost, cs));
+                                cudaMemcpyDeviceToHost, xs));
         if (P_out && o.host_io)
             CKR(cudaMemcpyAsync(P_out + (size_t)c0 * nbt, ch.P, sizeof(double) * (size_t)cells * nbt,
-                                cudaMemcpyDeviceToHost, cs));
+                                cudaMemcpyDeviceToHost, xs));
+        if (async_io) {
+            CKR(cudaEventRecord(sl.copied[io_set], sl.copy));
+            sl.copied_valid[io_set] = true;
+        }
     }
     // join: the caller's stream continues after every chunk
     if (nslots > 1)
@@ -837,7 +870,8 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
             CKR(cudaEventRecord(ctx->slots[k].done, ctx->slots[k].stream));
             CKR(cudaStreamWaitEvent(st, ctx->slots[k].done, 0));
         }
-    if (o.host_io) CKR(cudaStreamSynchronize(st));
+    if (o.host_io == 1) CKR(cudaStreamSynchronize(st));
+    if (async_io) ctx->io_parity ^= 1;
     return HEAT_OK;
 }
 
@@ -1068,11 +1102,16 @@ void heat_destroy(heat_ctx* ctx) {
                       &ctx->d_koff_all, &ctx->d_cde, &ctx->d_pent, &ctx->d_pcol, &ctx->d_kexp, &ctx->d_u_own, &ctx->s_tasks, &ctx->s_tasks_tail, &ctx->d_status};
     for (DevBuf* b : bufs) b->release();
     for (auto& sl : ctx->slots) {
-        DevBuf* sb[] = {&sl.ua64, &sl.su64, &sl.ua32, &sl.Bb64, &sl.Bb32, &sl.xs, &sl.ep,
-                        &sl.pabs, &sl.P, &sl.j, &sl.led, &sl.A, &sl.rowscale, &sl.work};
+        DevBuf* sb[] = {&sl.ua64, &sl.su64, &sl.ua32, &sl.Bb64, &sl.Bb32, &sl.xs, &sl.ep,   &sl.pabs,
+                        &sl.P,    &sl.j,    &sl.led,  &sl.A,    &sl.rowscale, &sl.work, &sl.P_alt, &sl.j_alt,
+                        &sl.led_alt};
         for (DevBuf* b : sb) b->release();
         if (sl.stream) cudaStreamDestroy(sl.stream);
         if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.copy) cudaStreamDestroy(sl.copy);
+        if (sl.computed) cudaEventDestroy(sl.computed);
+        for (cudaEvent_t e : sl.copied)
+            if (e) cudaEventDestroy(e);
     }
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     for (auto* modes : {ctx->tc, ctx->tc_si})
