@@ -100,13 +100,29 @@ __device__ __forceinline__ void build_task(const GrainDev& gd, const ChunkDev& c
             double q1 = su + sC[n] + 2.0;
             double ln = gd.lam[n];
             double a = om * ln * ln / kH;
-            double aq = (q1 != 0.0) ? a / q1 : a;
-            for (int k = sp[n]; k < sp[n + 1]; ++k) {
-                PatF64 pt = gd.pat64[k];
-                double B = Phi + (q1 != 0.0 ? aq * expm1(q1 * pt.t) : aq * pt.t);
-                ch.Bb64[bb + (size_t)pt.e * 32] = B;
+            const double dl = gd.dln[n];
+            const int cls = series_class64(q1, dl);  // per cell, like the FP32 build's series choice
+            if (cls == 2) {
+                for (int k = sp[n]; k < sp[n + 1]; ++k) {
+                    PatF64 pt = gd.pat64[k];
+                    ch.Bb64[bb + (size_t)pt.e * 32] = Phi + (a * pt.t) * e1d_series_short(q1 * pt.t);
+                }
+                if (om > 0.0) Phi += a * dl * e1d_series_short(q1 * dl);
+            } else if (cls == 1) {
+                for (int k = sp[n]; k < sp[n + 1]; ++k) {
+                    PatF64 pt = gd.pat64[k];
+                    ch.Bb64[bb + (size_t)pt.e * 32] = Phi + (a * pt.t) * e1d_series(q1 * pt.t);
+                }
+                if (om > 0.0) Phi += a * dl * e1d_series(q1 * dl);
+            } else {
+                double aq = (q1 != 0.0) ? a / q1 : a;
+                for (int k = sp[n]; k < sp[n + 1]; ++k) {
+                    PatF64 pt = gd.pat64[k];
+                    double B = Phi + (q1 != 0.0 ? aq * expm1(q1 * pt.t) : aq * pt.t);
+                    ch.Bb64[bb + (size_t)pt.e * 32] = B;
+                }
+                if (om > 0.0) Phi += a * dl * e1d(q1 * dl);
             }
-            if (om > 0.0) Phi += a * gd.dln[n] * e1d(q1 * gd.dln[n]);
         }
         for (int k = sp[N - 1]; k < sp[N]; ++k) ch.Bb64[bb + (size_t)gd.pat64[k].e * 32] = Phi;
 
@@ -274,7 +290,8 @@ __global__ void __launch_bounds__(256) k_build_small(GrainDev gd, ChunkDev ch) {
         if (BUILD == 0) {
             const SegF64 s = seg64(gd, g, n, ch.ua64[(size_t)n * Cc + cell], ch.su64[(size_t)n * Cc + cell]);
             if (s.om > 0.0) {
-                dphi = s.a * s.dl * e1d(s.q1 * s.dl);
+                const int cls = series_class64(s.q1, s.dl);
+                dphi = s.a * s.dl * (cls ? e1d_by_class(cls, s.q1 * s.dl) : e1d(s.q1 * s.dl));
                 dpsi = s.om * gd.lam[n] * s.dl * e1d(s.q0 * s.dl);
             }
         } else {
@@ -339,9 +356,12 @@ __global__ void __launch_bounds__(256) k_build_small(GrainDev gd, ChunkDev ch) {
             const SegF64 s = seg64(gd, g, n, ch.ua64[(size_t)n * Cc + cell], ch.su64[(size_t)n * Cc + cell]);
             const double aq = (s.q1 != 0.0) ? s.a / s.q1 : s.a;
             const double Phi = sPhi[n];
+            const int cls = series_class64(s.q1, s.dl);
             for (int k = k0 + lane; k < k1; k += 32) {
                 const PatF64 pt = gd.pat64[k];
-                ch.Bb64[bb + (size_t)pt.e * 32] = Phi + (s.q1 != 0.0 ? aq * expm1(s.q1 * pt.t) : aq * pt.t);
+                ch.Bb64[bb + (size_t)pt.e * 32] =
+                    cls ? Phi + (s.a * pt.t) * e1d_by_class(cls, s.q1 * pt.t)
+                        : Phi + (s.q1 != 0.0 ? aq * expm1(s.q1 * pt.t) : aq * pt.t);
             }
         } else {
             const float2 us = uasu[(size_t)n * Cc + cell];
@@ -425,6 +445,7 @@ __device__ __forceinline__ double point_column(const GrainDev& gd, const ChunkDe
     const int off = gd.bin_off[g];
     const int k1 = gd.pcol[off + j + 1];
     double acc = 0.0, om = 0.0, s = 0.0;
+    bool ser = false;
     int ncur = -1;
     for (int k = gd.pcol[off + j]; k < k1; ++k) {
         const PointEnt pe = gd.pent[k];
@@ -433,8 +454,10 @@ __device__ __forceinline__ double point_column(const GrainDev& gd, const ChunkDe
                 ncur = pe.n;
                 om = ch.ua64[(size_t)pe.n * Cc + cell] * Cact[pe.n];
                 s = ch.su64[(size_t)pe.n * Cc + cell] + sC[pe.n];
+                ser = short_series64(s, gd.dln[pe.n]);
             }
-            acc += om * exp(s * pe.t) * pe.fac;
+            const double z = s * pe.t;  // e^z = 1 + z E1(z)
+            acc += om * (ser ? fma(z, e1d_series(z), 1.0) : exp(z)) * pe.fac;
         }
         Bb[(size_t)pe.e * 32] = acc;
     }
