@@ -191,7 +191,10 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
  * a set of (streams, chunk_cells) pairs (the default first; each timed solve after a write
  * larger than L2; the median of three) and keep the fastest: later solves whose opts leave
  * both at 0 use it.  *streams_out / *chunk_out (or NULL) receive the choice (chunk 0 = the
- * default size).  Runs the candidates on cuda_stream and synchronises; j_out / P_out as in
+ * default size).  Then, on that configuration, it times the recursion's task order (grains
+ * longest first by band elements + w x rows, w in {0, 12, 30, 60}; 30 before tuning) and
+ * keeps the fastest w for all later solves on the ctx (heat_set_grains resets it).  Results
+ * do not depend on the order.  Runs the candidates on cuda_stream and synchronises; j_out / P_out as in
  * heat_solve (device, with room for the cells), overwritten.  Allocates a temporary buffer
  * of twice the L2 size.  Errors: as heat_solve. */
 heat_status heat_autotune(heat_ctx* ctx, const heat_opts* opts, double* P_out, void* j_out, void* cuda_stream,

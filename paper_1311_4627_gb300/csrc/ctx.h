@@ -53,6 +53,9 @@ struct heat_ctx {
     long long band_per_cell = 0;
     int max_bins = 0;
     std::vector<int> grain_order, grain_order_build;  // task orders of the recursion and the build
+    std::vector<long long> grain_band;                // band elements per cell of each grain
+    std::vector<int> grain_rows;                      // bins of each grain
+    int row_weight = 30;                              // recursion order: band + row_weight x rows
     DevBuf d_bin_off, d_cabs, d_T, d_E, d_Cf, d_invC, d_invdE, d_invdE32, d_Cact, d_sC, d_ca32, d_ce32, d_sC32,
         d_rowptr, d_wmax, d_seg_ptr, d_pat64, d_pat32, d_soft, d_soft_off, d_K, d_Kw, d_w, d_koff_all, d_cde,
         d_pent, d_pcol, d_kexp;

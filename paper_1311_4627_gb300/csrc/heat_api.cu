@@ -216,9 +216,27 @@ static heat_status emis_tc_chunk(heat_ctx* ctx, int m, bool si, const double* P,
     return HEAT_OK;
 }
 
-// (grain, group) task lists of a chunk of NG groups, longest first: the recursion's order
-// (grains by band + 30 x rows: a long chain of narrow rows takes its time whatever the
-// load, so it starts early) followed by the build's (band + 12 x rows).
+// Grain orders, longest first: the recursion's by band + row_weight x rows (a long chain of
+// narrow rows takes its time whatever the load, so it starts early; heat_autotune can pick the
+// weight), the build's by band + 12 x rows.
+static void order_grains(heat_ctx* ctx) {
+    const int G = ctx->G;
+    std::vector<long long> cost(G), cost_build(G);
+    for (int g = 0; g < G; ++g) {
+        cost[g] = ctx->grain_band[g] + (long long)ctx->row_weight * ctx->grain_rows[g];
+        cost_build[g] = ctx->grain_band[g] + 12LL * ctx->grain_rows[g];
+    }
+    ctx->grain_order.resize(G);
+    ctx->grain_order_build.resize(G);
+    for (int g = 0; g < G; ++g) ctx->grain_order[g] = ctx->grain_order_build[g] = g;
+    std::stable_sort(ctx->grain_order.begin(), ctx->grain_order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::stable_sort(ctx->grain_order_build.begin(), ctx->grain_order_build.end(),
+                     [&](int a, int b) { return cost_build[a] > cost_build[b]; });
+    ctx->tasks_NG = -1;  // the task lists follow the orders
+    ctx->tail_NG = -1;
+}
+
+// (grain, group) task lists of a chunk of NG groups: the recursion's order, then the build's.
 static std::vector<int2> make_tasks(const heat_ctx* ctx, int NG) {
     std::vector<int2> tasks;
     tasks.reserve(2 * (size_t)ctx->G * NG);
@@ -325,6 +343,7 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
     ctx->tasks_NG = -1;
     ctx->tail_NG = -1;
     ctx->tuned_streams = ctx->tuned_chunk = 0;
+    ctx->row_weight = 30;
     for (auto* modes : {ctx->tc, ctx->tc_si})
         for (int m = 0; m < 5; ++m) {
             modes[m].built = false;
@@ -359,7 +378,8 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
     std::vector<int> soft_off(G + 1, 0);
     std::vector<int> wmax(G, 1);
     std::vector<int> bin_grain(nbt);
-    std::vector<long long> cost(G, 0), cost_build(G, 0);
+    ctx->grain_band.assign(G, 0);
+    ctx->grain_rows.assign(G, 0);
     long long band_total = 0;
     struct Ent {
         int n, e;
@@ -497,8 +517,8 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
             return ctx->fail(HEAT_EINVAL, "heat_set_grains: band of the grains too large (over 6.7e7 elements)");
         // task order (longest first): a row costs about as much as 12 band elements in
         // the recursion (its chain waits on dependent FP64 ops), so many-row grains start early
-        cost[g] = band + 30LL * nb;
-        cost_build[g] = band + 12LL * nb;
+        ctx->grain_band[g] = band;
+        ctx->grain_rows[g] = nb;
     }
     soft_off[G] = (int)soft.size();
     pcol[nbt] = (int)pent.size();
@@ -507,13 +527,7 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
     ctx->band_per_cell = band_total;
     ctx->max_bins = 0;
     for (int g = 0; g < G; ++g) ctx->max_bins = std::max(ctx->max_bins, bin_offset[g + 1] - bin_offset[g]);
-    ctx->grain_order.resize(G);
-    ctx->grain_order_build.resize(G);
-    for (int g = 0; g < G; ++g) ctx->grain_order[g] = ctx->grain_order_build[g] = g;
-    std::stable_sort(ctx->grain_order.begin(), ctx->grain_order.end(),
-                     [&](int a, int b) { return cost[a] > cost[b]; });
-    std::stable_sort(ctx->grain_order_build.begin(), ctx->grain_order_build.end(),
-                     [&](int a, int b) { return cost_build[a] > cost_build[b]; });
+    order_grains(ctx);
 
     std::vector<double> cabs(c_abs_cm2, c_abs_cm2 + (size_t)G * N), T(T_bins_K, T_bins_K + nbt),
         E(H_bins_erg, H_bins_erg + nbt);
@@ -911,30 +925,56 @@ heat_status heat_autotune(heat_ctx* ctx, const heat_opts* opts, double* P_out, v
         cudaEventDestroy(e1);
         return h;
     };
-    float best = 1e30f;
-    Cand pick{1, 0};
-    for (const Cand& c : cands) {
+    // median of three cold-L2 solves of one configuration
+    auto time_config = [&](const Cand& c, float* ms) -> heat_status {
         heat_opts o = *opts;
         o.streams = c.streams;
         o.chunk_cells = c.chunk;
         o.timing = 0;
         heat_status h = heat_solve(ctx, &o, P_out, j_out, stream);  // warm-up: allocations, uploads
-        if (h != HEAT_OK) return done(h);
+        if (h != HEAT_OK) return h;
         float ms3[3];
         for (int rep = 0; rep < 3; ++rep) {
-            if (cudaMemsetAsync(flush.p, rep, flush.cap, st) != cudaSuccess) return done(HEAT_ECUDA);
-            if (cudaEventRecord(e0, st) != cudaSuccess) return done(HEAT_ECUDA);
-            if ((h = heat_solve(ctx, &o, P_out, j_out, stream)) != HEAT_OK) return done(h);
+            if (cudaMemsetAsync(flush.p, rep, flush.cap, st) != cudaSuccess) return HEAT_ECUDA;
+            if (cudaEventRecord(e0, st) != cudaSuccess) return HEAT_ECUDA;
+            if ((h = heat_solve(ctx, &o, P_out, j_out, stream)) != HEAT_OK) return h;
             if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
                 cudaEventElapsedTime(&ms3[rep], e0, e1) != cudaSuccess)
-                return done(ctx->fail(HEAT_ECUDA, "heat_autotune: timing"));
+                return ctx->fail(HEAT_ECUDA, "heat_autotune: timing");
         }
         std::sort(ms3, ms3 + 3);
-        if (ms3[1] < best) {
-            best = ms3[1];
+        *ms = ms3[1];
+        return HEAT_OK;
+    };
+    float best = 1e30f;
+    Cand pick{1, 0};
+    for (const Cand& c : cands) {
+        float ms = 0.0f;
+        heat_status h = time_config(c, &ms);
+        if (h != HEAT_OK) return done(h);
+        if (ms < best) {
+            best = ms;
             pick = c;
         }
     }
+    // then, on the chosen configuration, the recursion's task order: the weight of a row
+    // against a band element in the longest-first order
+    const int w0 = ctx->row_weight;
+    int best_w = w0;
+    for (int w : {0, 12, 30, 60}) {
+        if (w == w0) continue;
+        ctx->row_weight = w;
+        order_grains(ctx);
+        float ms = 0.0f;
+        heat_status h = time_config(pick, &ms);
+        if (h != HEAT_OK) return done(h);
+        if (ms < best) {
+            best = ms;
+            best_w = w;
+        }
+    }
+    ctx->row_weight = best_w;
+    order_grains(ctx);
     done(HEAT_OK);
     ctx->tuned_streams = pick.streams;
     ctx->tuned_chunk = pick.chunk;
