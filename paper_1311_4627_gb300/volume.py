@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import io
 import json
 import os
 import tempfile
@@ -86,10 +87,23 @@ class ChunkManifest:
         p = os.path.join(self.out_dir, e["file"])
         return os.path.exists(p) and sha256_file(p) == e["sha256"]
 
-    def record(self, k: int, fname: str, info: dict) -> None:
+    def record(self, k: int, fname: str, info: dict, sha256: str | None = None) -> None:
         p = os.path.join(self.out_dir, fname)
-        self.chunks[str(k)] = dict(info, file=fname, sha256=sha256_file(p))
+        self.chunks[str(k)] = dict(info, file=fname, sha256=sha256 if sha256 is not None else sha256_file(p))
         self.save()
+
+
+def write_chunk(out_dir: str, fname: str, J: np.ndarray) -> str:
+    """Write J as .npy under its final name atomically (temporary file, then rename) and
+    return the file's SHA-256, hashed from the bytes written rather than read back."""
+    buf = io.BytesIO()
+    np.save(buf, np.ascontiguousarray(J, dtype=np.float32))
+    data = buf.getbuffer()
+    fd, tmp = tempfile.mkstemp(dir=out_dir, prefix=".chunk.", suffix=".tmp")
+    with os.fdopen(fd, "wb") as f:
+        f.write(data)
+    os.replace(tmp, os.path.join(out_dir, fname))
+    return hashlib.sha256(data).hexdigest()
 
 
 def run_chunks(manifest: ChunkManifest, n_cells: int, chunk: int, solve_chunk, resume: bool = True,
@@ -97,12 +111,22 @@ def run_chunks(manifest: ChunkManifest, n_cells: int, chunk: int, solve_chunk, r
     """Drive the chunks of [0, n_cells): skip the finished ones, solve the others with
     solve_chunk(k, begin, end, prepared) -> (J float32 [cells][n_lambda], info dict), write
     J_k.npy and record it.  prepare(begin, end), if given, runs one chunk ahead in a host
-    thread (e.g. making the next chunk's fields while the GPU works).  stop_after: return
-    after that many chunks were solved in this call (an interrupted run)."""
+    thread (e.g. making the next chunk's fields while the GPU works); the file of a solved
+    chunk is written and hashed in another host thread while the next chunk is solved, and
+    recorded in the manifest once it is complete.  stop_after: return after that many
+    chunks were solved in this call (an interrupted run)."""
     manifest.load(resume)
     todo = [k for k in range((n_cells + chunk - 1) // chunk) if not manifest.done(k)]
     solved = 0
-    with ThreadPoolExecutor(1) as pool:
+    pending = None  # (k, fname, info, future) of the chunk being written
+
+    def finish(p):
+        k, fname, info, fut = p
+        manifest.record(k, fname, info, sha256=fut.result())
+        if log:
+            log(f"chunk {k}: cells {info['cells']} {json.dumps(info)}")
+
+    with ThreadPoolExecutor(1) as pool, ThreadPoolExecutor(1) as writer:
         nxt = None
         if prepare and todo:
             b = todo[0] * chunk
@@ -117,12 +141,13 @@ def run_chunks(manifest: ChunkManifest, n_cells: int, chunk: int, solve_chunk, r
                 b2 = todo[i + 1] * chunk
                 nxt = pool.submit(prepare, b2, min(n_cells, b2 + chunk))
             J, info = solve_chunk(k, b, e, prepared)
+            if pending is not None:  # at most one chunk waits for the disk
+                finish(pending)
             fname = f"J_{k:05d}.npy"
-            np.save(os.path.join(manifest.out_dir, fname), np.ascontiguousarray(J, dtype=np.float32))
-            manifest.record(k, fname, dict(info, cells=[b, e]))
+            pending = (k, fname, dict(info, cells=[b, e]), writer.submit(write_chunk, manifest.out_dir, fname, J))
             solved += 1
-            if log:
-                log(f"chunk {k}: cells [{b}, {e}) {json.dumps(info)}")
+        if pending is not None:
+            finish(pending)
     n_chunks = (n_cells + chunk - 1) // chunk
     return {"chunks": n_chunks, "solved_now": solved,
             "complete": all(manifest.done(k) for k in range(n_chunks))}
