@@ -99,13 +99,21 @@ def blackbody_field(lam_cm: np.ndarray, T: float) -> np.ndarray:
 
 
 def three_bb_fields(lam_cm: np.ndarray, chi: np.ndarray, hardness: np.ndarray, wts: np.ndarray) -> np.ndarray:
-    """u[c, n] for per-cell chi, hardness h and blackbody weights wts[c, 3]."""
+    """u[c, n] for per-cell chi, hardness h and blackbody weights wts[c, 3].  Every operation
+    is per cell (no cross-cell reductions or blocked library products), so a cell's field
+    does not depend on which other cells are generated with it."""
     basis = np.stack([_bb_energy_density(lam_cm, T) for T in FIELD_TEMPS])  # [3, N]
-    tilt = (lam_cm[None, :] / (0.55 * UM)) ** (-hardness[:, None])  # [cells, N]
-    shape = (wts @ basis) * tilt
+    u = np.multiply.outer(-hardness, np.log(lam_cm / (0.55 * UM)))  # tilt (lambda / 0.55 um)^-h
+    np.exp(u, out=u)
+    mix = wts[:, 0:1] * basis[0][None, :]
+    mix += wts[:, 1:2] * basis[1][None, :]
+    mix += wts[:, 2:3] * basis[2][None, :]
+    u *= mix
+    del mix
     dl = np.diff(lam_cm)
-    integral = np.sum(0.5 * (shape[:, 1:] + shape[:, :-1]) * dl[None, :], axis=1)
-    return (chi * ISRF_ENERGY_DENSITY / integral)[:, None] * shape
+    integral = np.sum(0.5 * (u[:, 1:] + u[:, :-1]) * dl[None, :], axis=1)
+    u *= (chi * ISRF_ENERGY_DENSITY / integral)[:, None]
+    return u
 
 
 # ----------------------------------------------------------------------------
@@ -281,10 +289,26 @@ class Volume:
     def n_cells(self) -> int:
         return int(self.chi.size)
 
-    def fields(self, begin: int, end: int) -> np.ndarray:
-        """u of cells [begin, end) (x-fastest order of the grid)."""
-        return three_bb_fields(self.grains.lam, self.chi[begin:end], self.hardness[begin:end],
-                               self.wts[begin:end])
+    def fields(self, begin: int, end: int, threads: int = 8) -> np.ndarray:
+        """u of cells [begin, end) (x-fastest order of the grid), generated in blocks of 4096
+        cells on host threads (numpy releases the GIL; the cells are independent)."""
+        from concurrent.futures import ThreadPoolExecutor
+
+        lam = self.grains.lam
+        out = np.empty((end - begin, lam.size))
+
+        def block(b):
+            e = min(end, b + 4096)
+            out[b - begin:e - begin] = three_bb_fields(lam, self.chi[b:e], self.hardness[b:e], self.wts[b:e])
+
+        starts = range(begin, end, 4096)
+        if threads > 1 and len(starts) > 1:
+            with ThreadPoolExecutor(min(threads, len(starts))) as pool:
+                list(pool.map(block, starts))
+        else:
+            for b in starts:
+                block(b)
+        return out
 
 
 def rt_volume(shape=(128, 128, 64), corr_cells: float = 8.0, radii_per_composition: int = 40, nbins: int = 512,
