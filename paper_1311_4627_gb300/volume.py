@@ -245,6 +245,7 @@ def main(argv=None):
     t0 = time.perf_counter()
     vol = W.rt_volume(tuple(args.shape), radii_per_composition=args.radii, nbins=args.bins, n_lambda=args.n_lambda)
     solver = VolumeSolver(vol, args.chunk, emis=args.emis)
+    setup_s = time.perf_counter() - t0
     man = ChunkManifest(args.out, volume_config(vol, args.chunk, args.emis))
     res = run_chunks(man, vol.n_cells, args.chunk, solver.solve_chunk, resume=not args.no_resume,
                      stop_after=args.stop_after, prepare=solver.prepare, log=print)
@@ -255,7 +256,7 @@ def main(argv=None):
     ratios = [c["energy"]["weighted_ratio"] for c in ch if c["energy"]["weighted_ratio"] is not None]
     res.update({"cells": vol.n_cells, "spectra": spectra, "gpu_s": round(gpu_s, 3),
                 "spectra_per_s_gpu": spectra / gpu_s if gpu_s > 0 else None,
-                "wall_s": round(time.perf_counter() - t0, 2),
+                "wall_s": round(time.perf_counter() - t0, 2), "setup_s": round(setup_s, 2),
                 "energy_weighted_ratio_range": [min(ratios), max(ratios)] if ratios else None,
                 "config": man.config})
     print(json.dumps(res))
