@@ -5,6 +5,11 @@ parallel with no exchange), so ranks take contiguous cell ranges, replicate the 
 tables and need no collective on the data path.  The collectives here are off the hot
 path: the max over ranks of a timing, and an optional gather of per-cell outputs (e.g. the
 size-integrated J) to one rank.
+
+For devices of unequal speed (the paper's host + coprocessor runs hand chunks of cells to
+whichever device is free) ChunkQueue assigns chunks dynamically: each rank claims the next
+unclaimed chunk from an atomic counter in a torch.distributed key-value store, so a faster
+rank takes more chunks; gather_chunks assembles the results in chunk order.
 """
 from __future__ import annotations
 
@@ -49,3 +54,54 @@ def gather_rows(local, n_cells: int, dst: int = 0):
     if rank != dst:
         return None
     return torch.cat([p[: e - b] for p, (b, e) in zip(parts, rows)])
+
+
+class ChunkQueue:
+    """Dynamic assignment of chunks [0, n_chunks) to ranks.  claim() atomically takes the next
+    chunk from a counter in `store` (a torch.distributed Store shared by the ranks: TCPStore,
+    FileStore, ...) and returns its index, or None once all are taken; every chunk goes to
+    exactly one claimant.  `name` keys the counter, so one store can serve several runs."""
+
+    def __init__(self, store, n_chunks: int, name: str = "heat_chunk_queue"):
+        if n_chunks < 0:
+            raise ValueError("n_chunks must be >= 0")
+        self.store, self.n_chunks, self.key = store, int(n_chunks), name
+
+    def claim(self):
+        k = int(self.store.add(self.key, 1)) - 1
+        return k if k < self.n_chunks else None
+
+    def __iter__(self):
+        while True:
+            k = self.claim()
+            if k is None:
+                return
+            yield k
+
+
+def chunk_bounds(k: int, chunk: int, n_cells: int) -> tuple[int, int]:
+    """[begin, end) of chunk k of `chunk` cells."""
+    return k * chunk, min(n_cells, (k + 1) * chunk)
+
+
+def gather_chunks(results: dict, n_chunks: int, dst: int = 0):
+    """Assemble {chunk index: array of that chunk's rows} held by the ranks into one array in
+    chunk order on rank dst (others get None).  Raises if a chunk is missing or held twice."""
+    import numpy as np
+    import torch.distributed as dist
+
+    world, rank = dist.get_world_size(), dist.get_rank()
+    parts = [None] * world if rank == dst else None
+    dist.gather_object(results, parts, dst=dst)
+    if rank != dst:
+        return None
+    merged = {}
+    for part in parts:
+        for k, v in part.items():
+            if k in merged:
+                raise RuntimeError(f"chunk {k} was solved by two ranks")
+            merged[k] = v
+    missing = [k for k in range(n_chunks) if k not in merged]
+    if missing:
+        raise RuntimeError(f"chunks {missing} were not solved")
+    return np.concatenate([merged[k] for k in range(n_chunks)])

@@ -66,3 +66,64 @@ def test_two_ranks_gather_equals_one_process(tmp_path):
     got = np.load(os.path.join(tmp_path, "gathered.npy"))
     assert np.array_equal(got, ref)
     assert float(np.load(os.path.join(tmp_path, "tmax.npy"))[0]) == 2.0
+
+
+def test_chunk_queue_hands_out_every_chunk_once():
+    import torch.distributed as dist
+
+    store = dist.HashStore()
+    q = shard.ChunkQueue(store, 5, name="t")
+    assert [q.claim() for _ in range(7)] == [0, 1, 2, 3, 4, None, None]
+    assert list(shard.ChunkQueue(store, 3, name="u")) == [0, 1, 2]
+    assert list(shard.ChunkQueue(store, 0, name="v")) == []
+    assert shard.chunk_bounds(2, 16, 40) == (32, 40)
+
+
+def _dyn_worker(rank, world, port, out_dir):
+    import time
+
+    import torch.distributed as dist
+
+    import oracle
+    from paper_1311_4627_gb300 import workloads as W
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    store = dist.FileStore(os.path.join(out_dir, "queue"), world)
+    full = W.batched(cells=48, n_lambda=64)
+    wl = W.grain_subset(full, [0, 40])
+    Cf = oracle.grain_cooling(wl)
+    chunk, n_chunks = 4, 12
+    results = {}
+    for k in shard.ChunkQueue(store, n_chunks):
+        if rank == 0:
+            time.sleep(0.15)  # a slow device
+        b, e = shard.chunk_bounds(k, chunk, wl.n_cells)
+        _, j, _, st = oracle.solve_batch(W.field_subset(wl, np.arange(b, e)), Cf, n_threads=1)
+        assert st == oracle.OK
+        results[k] = oracle.size_integrate(wl.size_weight, j)
+    np.save(os.path.join(out_dir, f"claims{rank}.npy"), np.array(sorted(results), dtype=np.int64))
+    got = shard.gather_chunks(results, n_chunks)
+    if rank == 0:
+        np.save(os.path.join(out_dir, "gathered.npy"), got)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_dynamic_chunks_over_three_ranks_of_unequal_speed(tmp_path):
+    """Three gloo ranks claim 12 chunks from a shared queue; rank 0 is slow.  Every chunk is
+    solved once, the slow rank takes fewer chunks, and the gathered result equals the
+    single-process one bit for bit."""
+    import oracle
+    from paper_1311_4627_gb300 import workloads as W
+
+    mp.spawn(_dyn_worker, args=(3, _free_port(), str(tmp_path)), nprocs=3, join=True)
+    claims = [np.load(os.path.join(tmp_path, f"claims{r}.npy")) for r in range(3)]
+    allc = np.sort(np.concatenate(claims))
+    assert np.array_equal(allc, np.arange(12))
+    assert len(claims[0]) < min(len(claims[1]), len(claims[2]))
+    full = W.batched(cells=48, n_lambda=64)
+    wl = W.grain_subset(full, [0, 40])
+    _, j, _, _ = oracle.solve_batch(wl, oracle.grain_cooling(wl), n_threads=1)
+    ref = oracle.size_integrate(wl.size_weight, j)
+    assert np.array_equal(np.load(os.path.join(tmp_path, "gathered.npy")), ref)
