@@ -16,8 +16,6 @@ constexpr int kStatNumeric = 1;   // zero cooling rate with non-zero inflow
 constexpr int kStatBadInput = 2;  // non-finite or negative field value
 constexpr int kStatTimeout = 4;   // bounded wait gave up
 
-constexpr double kRescaleBig = 0x1p800;     // exact power of two
-constexpr double kRescaleSmall = 0x1p-800;
 
 // Pattern entry of a band element, grouped by wavelength segment (the matrix build walks
 // the segments in order and fills every element whose transition wavelength

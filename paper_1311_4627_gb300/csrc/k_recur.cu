@@ -64,6 +64,17 @@ struct BandRaw<1> {
     static __device__ __forceinline__ double wide(T v) { return widen_pos(v); }
 };
 
+// x * 2^(-800 d) for x >= 0 and d >= 0 on the integer pipe (the exponent field lowered), zero
+// where the result would fall below the normal range (values under 2^-1022 of the current
+// scale, far below anything an output resolves).  The recursion's rescales and the
+// normalisation's epoch corrections use it: a multiply or the library ldexp would put every
+// one of them on the FP64 unit, which the band's FMAs already keep busy.
+__device__ __forceinline__ double scale_down_800(double x, int d) {
+    const long long bits = __double_as_longlong(x);
+    const long long e = (bits >> 52) - 800LL * d;
+    return (d == 0) ? x : (e > 0 ? __longlong_as_double(bits - ((800LL * d) << 52)) : 0.0);
+}
+
 // Window part of a row: element e1-1-k multiplies X_{f-1-k} = w[k] for k < nreg (<= W),
 // accumulated into S in element order; a jump into the unrolled tail, so no predicated-off
 // FMA occupies the FP64 pipe.
@@ -219,7 +230,8 @@ __device__ __forceinline__ void recur_task(const GrainDev& gd, const ChunkDev& c
         double X = S * ic;
         if (__double2hiint(ic) == 0 && __double2loint(ic) == 0) {  // zero cooling rate
             X = 0.0;
-            if (S != 0.0 && !(PRUNE && stopped)) numeric_bad = true;
+            // S >= 0: non-zero bits, tested on the integer pipe
+            if (__double_as_longlong(S) != 0 && !(PRUNE && stopped)) numeric_bad = true;
         }
         if constexpr (PRUNE) {
             if (stopped) {
@@ -243,13 +255,14 @@ __device__ __forceinline__ void recur_task(const GrainDev& gd, const ChunkDev& c
         if (above_rescale(X)) {
             ++epoch;
             const int lo = more ? (f + 1) - (e2 - e1) : f + 1;  // next row's band start
+            // exact power-of-two scaling on the integer pipe (the exponent field lowered by 800)
             for (int i = lo; i <= f; ++i) {
-                xl[i * 32] *= kRescaleSmall;
+                xl[i * 32] = scale_down_800(xl[i * 32], 1);
                 epl[i * 32] = (unsigned short)epoch;
             }
-            total *= kRescaleSmall;
+            total = scale_down_800(total, 1);
 #pragma unroll
-            for (int k = 0; k < W; ++k) w[k] *= kRescaleSmall;
+            for (int k = 0; k < W; ++k) w[k] = scale_down_800(w[k], 1);
         }
         if constexpr (PRUNE) {
             if (__all_sync(0xffffffffu, stopped)) {
@@ -271,14 +284,17 @@ __device__ __forceinline__ void recur_task(const GrainDev& gd, const ChunkDev& c
         double emit = 0.0;
         const double* cde = gd.cde + off;
         const int i_end = PRUNE ? f_last : M;
-        for (int i = 0; i <= i_end; ++i) {
-            const int d = epoch - (int)epl[i * 32];  // rescales this value has not seen
-            const double x = xl[i * 32];
-            // scale X first (as the plain rescale would have), then normalise: the factor
-            // alone could underflow where the product is still a normal number
-            const double p = d == 0 ? x * inv : ldexp(x, -800 * d) * inv;
-            prow[i] = p;
-            if (ch.ledger) emit = fma(p, cde[i], emit);
+        // scale X first (as the plain rescale would have), then normalise: the factor alone
+        // could underflow where the product is still a normal number.  Two loops, so that
+        // no predicated-off FMA of the energy check occupies the FP64 unit without a ledger
+        if (ch.ledger) {
+            for (int i = 0; i <= i_end; ++i) {
+                const double p = scale_down_800(xl[i * 32], epoch - (int)epl[i * 32]) * inv;
+                prow[i] = p;
+                emit = fma(p, cde[i], emit);
+            }
+        } else {
+            for (int i = 0; i <= i_end; ++i) prow[i] = scale_down_800(xl[i * 32], epoch - (int)epl[i * 32]) * inv;
         }
         if constexpr (PRUNE)
             for (int i = f_last + 1; i <= M; ++i) prow[i] = 0.0;  // rows past a pruned tail
@@ -349,7 +365,7 @@ __global__ void __launch_bounds__(128) k_recur_small(GrainDev gd, ChunkDev ch) {
         double X = S * ic;
         if (__double2hiint(ic) == 0 && __double2loint(ic) == 0) {
             X = 0.0;
-            if (S != 0.0) numeric_bad = true;
+            if (__double_as_longlong(S) != 0) numeric_bad = true;  // S >= 0
         }
         if (lane == 0) xs[f] = X;
         total += X;
@@ -364,8 +380,8 @@ __global__ void __launch_bounds__(128) k_recur_small(GrainDev gd, ChunkDev ch) {
         }
         if (above_rescale(X)) {
             __syncwarp();
-            for (int i = lane; i <= f; i += 32) xs[i] *= kRescaleSmall;
-            total *= kRescaleSmall;
+            for (int i = lane; i <= f; i += 32) xs[i] = scale_down_800(xs[i], 1);
+            total = scale_down_800(total, 1);
             shift += 800;
         }
         __syncwarp();
