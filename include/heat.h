@@ -184,7 +184,8 @@ heat_status heat_set_fields(heat_ctx* ctx, int n_cells, const void* u_lambda, in
  *          size_integrate) or NULL: the emissivity (Eq. emission).
  * Device pointers unless opts->host_io.  Asynchronous with respect to the host unless
  * host_io = 1; device-side errors surface at heat_sync.  Non-interacting grains give
- * P = delta_{i0} (no error).  Errors: HEAT_EINVAL, HEAT_ESTATE, HEAT_ENOMEM, HEAT_ECUDA. */
+ * P = delta_{i0} (no error).  P entries below the normal FP64 range (about 2.2e-308) are
+ * returned as 0.  Errors: HEAT_EINVAL, HEAT_ESTATE, HEAT_ENOMEM, HEAT_ECUDA. */
 heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void* j_out, void* cuda_stream);
 
 /* Time heat_solve on cells [opts->cell_begin, +opts->cell_count) of the current fields for

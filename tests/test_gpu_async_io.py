@@ -57,3 +57,37 @@ def test_pipelined_host_solves_match_synchronous_ones():
         assert e.value.status == heat.HEAT_EINVAL
     finally:
         heat.heat_destroy(ctx)
+
+
+@pytest.mark.parametrize("streams,chunk,si", [(2, 32, 0), (3, 32, 1)])
+def test_pipelined_host_solves_with_chunks_in_flight(streams, chunk, si):
+    """Asynchronous host I/O with several chunks in flight on several slots (each with its own
+    copy stream and staging sets), per-grain and size-integrated: two queued solves of
+    different fields equal their synchronous solves bit for bit."""
+    import torch
+
+    full = W.batched(cells=100)
+    wl = W.grain_subset(full, [2, 30, 63])
+    G, N = wl.n_grains, wl.n_lambda
+    ctx = heat.heat_create_grid(0, wl.lam)
+    try:
+        heat.heat_set_grains(ctx, wl.radius, wl.cabs, wl.bin_off, wl.T, wl.E, wl.size_weight)
+        st = torch.cuda.Stream()
+        sh = st.cuda_stream
+        fields = [torch.from_numpy(np.ascontiguousarray(wl.u[::s])).pin_memory() for s in (1, -1)]
+        shape = (wl.n_cells, N) if si else (wl.n_cells, G, N)
+        outs = [torch.empty(*shape, dtype=torch.float32).pin_memory() for _ in range(2)]
+        kw = dict(build=heat.HEAT_BUILD_F32, emis=heat.HEAT_EMIS_BF16X3, j_dtype=heat.HEAT_F32, streams=streams,
+                  chunk_cells=chunk, size_integrate=si)
+        for k in range(2):
+            heat.heat_set_fields(ctx, wl.n_cells, fields[k], heat.HEAT_F64, 0, sh)
+            heat.heat_solve(ctx, heat.heat_default_opts(host_io=2, **kw), None, outs[k], sh)
+        heat.heat_sync(ctx)
+        for k in range(2):
+            ref = torch.empty(*shape, dtype=torch.float32).pin_memory()
+            heat.heat_set_fields(ctx, wl.n_cells, fields[k], heat.HEAT_F64, 0, sh)
+            heat.heat_solve(ctx, heat.heat_default_opts(host_io=1, **kw), None, ref, sh)
+            heat.heat_sync(ctx)
+            assert torch.equal(outs[k], ref), k
+    finally:
+        heat.heat_destroy(ctx)
