@@ -289,10 +289,15 @@ class Volume:
     def n_cells(self) -> int:
         return int(self.chi.size)
 
-    def fields(self, begin: int, end: int, threads: int = 8) -> np.ndarray:
+    def fields(self, begin: int, end: int, threads: int | None = None) -> np.ndarray:
         """u of cells [begin, end) (x-fastest order of the grid), generated in blocks of 4096
-        cells on host threads (numpy releases the GIL; the cells are independent)."""
+        cells on host threads (numpy releases the GIL; the cells are independent; default one
+        thread per core, at most 16)."""
+        import os
         from concurrent.futures import ThreadPoolExecutor
+
+        if threads is None:
+            threads = min(16, os.cpu_count() or 1)
 
         lam = self.grains.lam
         out = np.empty((end - begin, lam.size))
