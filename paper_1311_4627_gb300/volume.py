@@ -163,8 +163,10 @@ def load_output(manifest_dir: str) -> np.ndarray:
 
 class VolumeSolver:
     """GPU side of a volume run: one ctx with the volume's grains; per chunk the fields are
-    copied from pinned host memory, solved on the mixed path with size-integrated output
-    and the energy ledger, and J is read back."""
+    made straight into one of two pinned host buffers (the next chunk's while this one is
+    solved), copied to the device, solved on the mixed path with size-integrated output and
+    the energy ledger, and J is read back into one of two pinned buffers (the other may still
+    be being written to disk)."""
 
     def __init__(self, vol, chunk: int, device: int = 0, emis: str = "bf16x3"):
         import torch
@@ -183,36 +185,46 @@ class VolumeSolver:
         self.u_dev = torch.empty(chunk, N, dtype=torch.float64, device=self.dev)
         self.J_dev = torch.empty(chunk, N, dtype=torch.float32, device=self.dev)
         self.led_dev = torch.empty(chunk, G, 2, dtype=torch.float64, device=self.dev)
-        self.u_pin = torch.empty(chunk, N, dtype=torch.float64).pin_memory()
-        self.J_pin = torch.empty(chunk, N, dtype=torch.float32).pin_memory()
+        self.u_pin = [torch.empty(chunk, N, dtype=torch.float64).pin_memory() for _ in range(2)]
+        self.J_pin = [torch.empty(chunk, N, dtype=torch.float32).pin_memory() for _ in range(2)]
         self.led_pin = torch.empty(chunk, G, 2, dtype=torch.float64).pin_memory()
+        self.prep_slot = 0  # pinned field buffer of the next prepare (alternates per call)
+        self.solve_slot = 0  # pinned J buffer of the next solve (alternates per call)
 
-    def prepare(self, begin: int, end: int) -> np.ndarray:
-        return self.vol.fields(begin, end)
+    def prepare(self, begin: int, end: int):
+        """Make the fields of [begin, end) in the next pinned buffer: (buffer index, array)."""
+        s = self.prep_slot
+        self.prep_slot ^= 1
+        buf = self.u_pin[s][: end - begin].numpy()
+        return s, self.vol.fields(begin, end, out=buf)
 
-    def solve_chunk(self, k: int, begin: int, end: int, u: np.ndarray | None):
+    def solve_chunk(self, k: int, begin: int, end: int, prepared=None):
         torch, heat = self.torch, self.heat
         n = end - begin
-        if u is None:
-            u = self.prepare(begin, end)
+        if prepared is None:
+            prepared = self.prepare(begin, end)
+        s_in, _ = prepared
+        s_out = self.solve_slot
+        self.solve_slot ^= 1
         sh = self.stream.cuda_stream
         t0 = time.perf_counter()
-        self.u_pin[:n].copy_(torch.from_numpy(u))
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         with torch.cuda.stream(self.stream):
             ev[0].record(self.stream)
-            self.u_dev[:n].copy_(self.u_pin[:n], non_blocking=True)
+            self.u_dev[:n].copy_(self.u_pin[s_in][:n], non_blocking=True)
             heat.heat_set_fields(self.ctx, n, self.u_dev, heat.HEAT_F64, 1, sh)
             o = heat.heat_default_opts(build=heat.HEAT_BUILD_F32, emis=self.emis, j_dtype=heat.HEAT_F32,
                                        size_integrate=1, cell_count=n, ledger_out=self.led_dev)
             heat.heat_solve(self.ctx, o, None, self.J_dev, sh)
-            self.J_pin[:n].copy_(self.J_dev[:n], non_blocking=True)
+            self.J_pin[s_out][:n].copy_(self.J_dev[:n], non_blocking=True)
             self.led_pin[:n].copy_(self.led_dev[:n], non_blocking=True)
             ev[1].record(self.stream)
         self.stream.synchronize()
         heat.heat_sync(self.ctx)
         gpu_ms = ev[0].elapsed_time(ev[1])
-        J = self.J_pin[:n].numpy().copy()
+        # a view, not a copy: this buffer is filled again two solves later, after the chunk's
+        # file has been written (run_chunks keeps at most one chunk waiting for the disk)
+        J = self.J_pin[s_out][:n].numpy()
         info = {"gpu_ms": round(gpu_ms, 3), "wall_s": round(time.perf_counter() - t0, 3),
                 "spectra": n * self.vol.grains.n_grains,
                 "energy": energy_summary(self.led_pin[:n].numpy(), self.vol.grains.size_weight)}

@@ -289,10 +289,10 @@ class Volume:
     def n_cells(self) -> int:
         return int(self.chi.size)
 
-    def fields(self, begin: int, end: int, threads: int | None = None) -> np.ndarray:
+    def fields(self, begin: int, end: int, threads: int | None = None, out: np.ndarray | None = None) -> np.ndarray:
         """u of cells [begin, end) (x-fastest order of the grid), generated in blocks of 4096
         cells on host threads (numpy releases the GIL; the cells are independent; default one
-        thread per core, at most 16)."""
+        thread per core, at most 16); into `out` ([end - begin][n_lambda] FP64) if given."""
         import os
         from concurrent.futures import ThreadPoolExecutor
 
@@ -300,7 +300,8 @@ class Volume:
             threads = min(16, os.cpu_count() or 1)
 
         lam = self.grains.lam
-        out = np.empty((end - begin, lam.size))
+        if out is None:
+            out = np.empty((end - begin, lam.size))
 
         def block(b):
             e = min(end, b + 4096)
