@@ -95,15 +95,21 @@ class ChunkManifest:
 
 def write_chunk(out_dir: str, fname: str, J: np.ndarray) -> str:
     """Write J as .npy under its final name atomically (temporary file, then rename) and
-    return the file's SHA-256, hashed from the bytes written rather than read back."""
-    buf = io.BytesIO()
-    np.save(buf, np.ascontiguousarray(J, dtype=np.float32))
-    data = buf.getbuffer()
+    return the file's SHA-256, hashed from the bytes written rather than read back (the
+    array is written from its own memory, without an intermediate copy)."""
+    J = np.ascontiguousarray(J, dtype=np.float32)
+    head = io.BytesIO()
+    np.lib.format.write_array_header_1_0(head, np.lib.format.header_data_from_array_1_0(J))
+    header = head.getvalue()
+    body = memoryview(J).cast("B")
+    h = hashlib.sha256(header)
+    h.update(body)
     fd, tmp = tempfile.mkstemp(dir=out_dir, prefix=".chunk.", suffix=".tmp")
     with os.fdopen(fd, "wb") as f:
-        f.write(data)
+        f.write(header)
+        f.write(body)
     os.replace(tmp, os.path.join(out_dir, fname))
-    return hashlib.sha256(data).hexdigest()
+    return h.hexdigest()
 
 
 def run_chunks(manifest: ChunkManifest, n_cells: int, chunk: int, solve_chunk, resume: bool = True,
