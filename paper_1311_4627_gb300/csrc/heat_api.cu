@@ -240,9 +240,24 @@ static void order_grains(heat_ctx* ctx) {
 static std::vector<int2> make_tasks(const heat_ctx* ctx, int NG) {
     std::vector<int2> tasks;
     tasks.reserve(2 * (size_t)ctx->G * NG);
-    for (const auto* order : {&ctx->grain_order, &ctx->grain_order_build})
-        for (int gi = 0; gi < ctx->G; ++gi)
-            for (int grp = 0; grp < NG; ++grp) tasks.push_back(make_int2((*order)[gi], grp));
+    // recursion: near-chain grains (fewer than 8 band elements per row: their time is the
+    // per-row latency, they hardly use the FP64 unit) interleaved with the wide-band grains
+    // in proportion to each list's cost, so that every SM holds both kinds throughout
+    std::vector<int> chain, wide;
+    for (int g : ctx->grain_order) (ctx->grain_band[g] < 8LL * ctx->grain_rows[g] ? chain : wide).push_back(g);
+    auto cost = [&](int g) { return (double)(ctx->grain_band[g] + (long long)ctx->row_weight * ctx->grain_rows[g]); };
+    double tc = 0.0, tw = 0.0, dc = 0.0, dw = 0.0;
+    for (int g : chain) tc += cost(g);
+    for (int g : wide) tw += cost(g);
+    size_t ic = 0, iw = 0;
+    while (ic < chain.size() || iw < wide.size()) {
+        const bool take_chain = iw == wide.size() || (ic < chain.size() && dc / tc <= dw / tw);
+        const int g = take_chain ? chain[ic++] : wide[iw++];
+        (take_chain ? dc : dw) += cost(g);
+        for (int grp = 0; grp < NG; ++grp) tasks.push_back(make_int2(g, grp));
+    }
+    for (int gi = 0; gi < ctx->G; ++gi)
+        for (int grp = 0; grp < NG; ++grp) tasks.push_back(make_int2(ctx->grain_order_build[gi], grp));
     return tasks;
 }
 
