@@ -467,6 +467,22 @@ def test_size_integration_is_weighted_sum(c1):
     assert np.allclose(J, want, rtol=1e-14, atol=0)
 
 
+def test_size_integration_selects_and_adds(c1):
+    """Eq. convolution discretised: a unit weight on one grain returns that grain's j exactly
+    (a wrong axis or index fails it), and the sum is linear in the weights."""
+    wl, _, _, j, _ = c1
+    G = wl.n_grains
+    for g in (0, G // 2, G - 1):
+        w = np.zeros(G)
+        w[g] = 1.0
+        assert np.array_equal(oracle.size_integrate(w, j)[0], j[0, g])
+    rng = np.random.default_rng(4)
+    w1, w2 = rng.random(G), rng.random(G)
+    lhs = oracle.size_integrate(w1 + w2, j)
+    rhs = oracle.size_integrate(w1, j) + oracle.size_integrate(w2, j)
+    assert np.allclose(lhs, rhs, rtol=1e-13, atol=0)
+
+
 # ------------------------------------------------------- grain thermal model
 def test_debye_enthalpy_limits():
     theta, n = 420.0, 1.0e4
