@@ -128,3 +128,29 @@ def test_dynamic_chunks_over_three_ranks_of_unequal_speed(tmp_path):
     _, j, _, _ = oracle.solve_batch(wl, oracle.grain_cooling(wl), n_threads=1)
     ref = oracle.size_integrate(wl.size_weight, j)
     assert np.array_equal(np.load(os.path.join(tmp_path, "gathered.npy")), ref)
+
+
+def _gather_err_worker(rank, world, port, out_dir):
+    import torch.distributed as dist
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    msgs = []
+    for results in ({0: np.zeros(2)} if rank == 0 else {2: np.ones(2)},  # chunk 1 missing
+                    {0: np.zeros(2), 1: np.ones(2)} if rank == 0 else {1: np.ones(2)}):  # chunk 1 twice
+        try:
+            shard.gather_chunks(results, 3 if len(msgs) == 0 else 2)
+            msgs.append("ok")
+        except RuntimeError as e:
+            msgs.append(str(e))
+    if rank == 0:
+        with open(os.path.join(out_dir, "msgs.txt"), "w") as f:
+            f.write("\n".join(msgs))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_gather_chunks_refuses_missing_or_duplicated_chunks(tmp_path):
+    mp.spawn(_gather_err_worker, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
+    msgs = open(os.path.join(tmp_path, "msgs.txt")).read().split("\n")
+    assert "not solved" in msgs[0] and "two ranks" in msgs[1]

@@ -94,3 +94,14 @@ def test_energy_summary():
     wa = 1.0 + 1.0 + 4.0 + 1.0 + 0.5
     we = 1.1 + 0.9 + 4.0 + 0.9 + 0.5
     assert abs(s["weighted_ratio"] - we / wa) < 1e-12
+
+
+def test_write_chunk_hashes_what_it_writes(tmp_path):
+    """A chunk file is the .npy of J, written under its final name only when complete, and
+    the returned SHA-256 is the file's."""
+    J = np.random.default_rng(1).random((300, 16)).astype(np.float32)
+    sha = V.write_chunk(str(tmp_path), "J_00000.npy", J)
+    p = os.path.join(tmp_path, "J_00000.npy")
+    assert np.array_equal(np.load(p), J)
+    assert sha == V.sha256_file(p)
+    assert not [f for f in os.listdir(tmp_path) if f.endswith(".tmp")]
