@@ -114,6 +114,20 @@ def test_range_integral_pure_power_law(s, p):
         assert abs(got / want - 1.0) < 1e-12, (a, b, got, want)
 
 
+def test_range_integral_is_additive_across_segments():
+    """int_a^c = int_a^b + int_b^c for split points inside a segment, on a node and across
+    many segments (a wrong segment lookup or a dropped partial segment fails it)."""
+    wl = W.single_cell()
+    lam = wl.lam
+    om = wl.u[0] * wl.cabs[3]
+    for p in (0, 1):
+        for a, b, c in [(lam[3] * 1.1, lam[3] * 1.2, lam[3] * 1.3), (lam[10] * 1.01, lam[40], lam[200] * 0.97),
+                        (lam[0], lam[100] * 1.5, lam[-1]), (lam[50] * 0.999, lam[50] * 1.0005, lam[51] * 1.0001)]:
+            whole = oracle.range_integral(lam, om, p, a, c)
+            parts = oracle.range_integral(lam, om, p, a, b) + oracle.range_integral(lam, om, p, b, c)
+            assert abs(parts / whole - 1.0) < 1e-13, (p, a, b, c)
+
+
 def test_range_integral_bruteforce_quad():
     integrate = pytest.importorskip("scipy.integrate")
     rng = np.random.default_rng(7)
