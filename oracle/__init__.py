@@ -21,7 +21,6 @@ marshals numpy arrays through ctypes.  Functions and the passages they follow:
 from __future__ import annotations
 
 import ctypes
-import os
 
 import numpy as np
 
