@@ -168,6 +168,17 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
                             const int* bin_offset, const double* T_bins_K, const double* H_bins_erg,
                             const double* size_weight);
 
+/* Enthalpy bins on a temperature grid (Sec. 2: the bins sit on a user-supplied temperature
+ * grid, E_i = H(T_i); Sec. 2.1: the enthalpy is the integral of the grain's heat capacity):
+ * the Debye internal energy of 3 n_atoms modes above the zero-point energy,
+ *   H(T) = 9 n_atoms k T (T / theta_D)^3 int_0^{theta_D/T} x^3 / (e^x - 1) dx   (erg),
+ * the integral summed in closed series (Bernoulli series below theta_D/T = 1, exponential
+ * series above), relative accuracy about 1e-14.  theta_D in K (> 0), n_atoms > 0, T in K
+ * (>= 0; H(0) = 0); all finite, else NaN.  Host function: no ctx, no device, thread-safe.
+ * Limits: (3 pi^4 / 5) n_atoms k T^4 / theta_D^3 for T << theta_D; 3 n_atoms k T -
+ * (9/8) n_atoms k theta_D for T >> theta_D. */
+double heat_debye_enthalpy(double theta_D, double n_atoms, double T);
+
 /* Set the radiation fields u_lambda[n_cells][n_lambda] (erg cm^-3 cm^-1, >= 0, finite),
  * element type `dtype` (HEAT_F64 or HEAT_F32).  on_device = 1: `u_lambda` is a device
  * pointer, borrowed until the solves that use it complete; on_device = 0: host memory
@@ -226,6 +237,18 @@ void heat_graph_destroy(heat_graph* graph);
 /* Wait for all work of the ctx's last calls and return the device status:
  * HEAT_OK, HEAT_ENUMERIC, HEAT_EINVAL (bad field values) or HEAT_ECUDA.  Clears the status. */
 heat_status heat_sync(heat_ctx* ctx);
+
+/* Give-up limit of the device-side waits (failure detection).  The tensor-core kernels
+ * (emissivity, surrogate GEMMs) hand tiles between a copy role, an MMA role and an epilogue
+ * role through shared-memory barriers; a role that has polled a barrier `polls` times without
+ * the other role arriving gives up: it records HEAT_ETIMEOUT in the device status word (seen
+ * by heat_sync), tells the other roles to stop, waits for the copies and MMAs it already
+ * issued to finish, frees its tensor memory and returns, so the context stays usable; the
+ * outputs of that launch are undefined.  polls = 0 makes every such wait give up at once
+ * (a test of this path); the default, HEAT_WAIT_POLLS_DEFAULT, is far above any wait of a
+ * healthy launch.  Applies to launches queued after the call.  Errors: HEAT_EINVAL (polls < 0). */
+#define HEAT_WAIT_POLLS_DEFAULT (1LL << 22)
+heat_status heat_set_wait_limit(heat_ctx* ctx, long long polls);
 
 /* Message of the last failure on ctx (never NULL; "" when none). */
 const char* heat_last_error(const heat_ctx* ctx);
@@ -336,7 +359,13 @@ heat_status heat_surrogate_load(heat_ctx* ctx, const char* path);
  *     bytes (band = heat_band_elements, G grains, N wavelengths, nbt total bins).  If that
  *     exceeds the array, the call
  *     returns HEAT_EINVAL with a message (heat_last_error) and queues nothing.
- * Errors: HEAT_EINVAL, HEAT_ESTATE (grains not set), HEAT_ECUDA; device-side errors at heat_sync. */
+ *   - Cells run in a plain grain-major task order with one warp per task: the results equal
+ *     heat_solve's, but without heat_solve's longest-first persistent scheduling the call
+ *     can take longer on grain sets of very uneven bin counts.
+ * Errors: HEAT_EINVAL, HEAT_ESTATE (grains not set), HEAT_ECUDA, each with a message in
+ * heat_last_error; device-side errors at heat_sync.  When a call fails after it has queued
+ * work for some groups of cells (a later launch failing), P_out is partly written: treat
+ * its contents as undefined after any error. */
 #define HEAT_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 heat_status heat_solve_noalloc(heat_ctx* ctx, int build, const double* u_dev, int n_cells, double* P_out,
                                void* cuda_stream);

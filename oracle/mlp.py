@@ -4,6 +4,13 @@ TEST INFRASTRUCTURE: it checks the gradients of the GPU training kernels.  Plain
 float64; the architecture follows the library's surrogate: layers W_l [out][in], b_l, GELU
 (exact, with erf) after every layer but the last, loss = mean over non-NaN targets of
 (y - t)^2.  Parameters use the library's flat layout: for each layer W (row-major) then b.
+
+``quantize`` (optional, e.g. ``bf16_round``) is applied where the GPU stores a value in a
+narrower type before its next use: every hidden activation GELU(z), the loss gradient
+2 (y - t) / count and each back-propagated dZ = dA * GELU'(z).  The arithmetic between
+those points stays FP64, so with the same inputs the two sides take the same rounding
+decisions (up to values within FP32 rounding of a BF16 tie) and their gradients can be
+compared element by element.
 """
 from __future__ import annotations
 
@@ -46,13 +53,27 @@ def flatten(layers):
     return np.concatenate([np.concatenate([W.ravel(), b]) for W, b in layers])
 
 
-def forward(layers, x):
+def bf16_round(a):
+    """Round to the nearest bfloat16 (ties to even), returned as float64.  Values are first
+    rounded to float32, as the GPU holds them."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _ident(a):
+    return a
+
+
+def forward(layers, x, quantize=None):
+    q = quantize or _ident
     a, zs, acts = np.asarray(x, np.float64), [], []
     for i, (W, b) in enumerate(layers):
         acts.append(a)
         z = a @ W.T + b
         zs.append(z)
-        a = gelu(z) if i + 1 < len(layers) else z
+        a = q(gelu(z)) if i + 1 < len(layers) else z
     return a, zs, acts
 
 
@@ -63,18 +84,19 @@ def loss(layers, x, t):
     return float(np.sum(d * d) / max(1, m.sum()))
 
 
-def loss_and_grad(layers, x, t):
+def loss_and_grad(layers, x, t, quantize=None):
     """Masked mean squared error and its gradient (same flat layout as the parameters)."""
-    y, zs, acts = forward(layers, x)
+    q = quantize or _ident
+    y, zs, acts = forward(layers, x, quantize)
     m = ~np.isnan(t)
     cnt = max(1, int(m.sum()))
     d = np.where(m, y - np.nan_to_num(t), 0.0)
     L = float(np.sum(d * d) / cnt)
-    g = 2.0 * d / cnt
+    g = q(2.0 * d / cnt)
     grads = [None] * len(layers)
     for i in range(len(layers) - 1, -1, -1):
         W, _ = layers[i]
         grads[i] = (g.T @ acts[i], g.sum(axis=0))
         if i > 0:
-            g = (g @ W) * gelu_grad(zs[i - 1])
+            g = q((g @ W) * gelu_grad(zs[i - 1]))
     return L, flatten(grads)

@@ -87,6 +87,7 @@ struct heat_ctx {
     int tuned_streams = 0, tuned_chunk = 0;  // heat_autotune's choice (0: none)
     int io_parity = 0;  // staging set of the next asynchronous host-I/O solve
     DevBuf d_status;
+    long long wait_polls = HEAT_WAIT_POLLS_DEFAULT;  // give-up limit of the tcgen05 kernels' waits
     int sms = 0;
     std::vector<double> radius;
     heat::Surrogate* sur = nullptr;  // learned surrogate (heat_surrogate_init)

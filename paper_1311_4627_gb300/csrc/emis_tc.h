@@ -20,6 +20,7 @@ struct EmisTcParams {
     void* j;                       // j[cell * ldj + g * N + n]
     long long ldj;
     int j_f64;
+    long long wait_polls;          // polls before a wait on another role gives up (kStatTimeout)
     int* status;
 };
 

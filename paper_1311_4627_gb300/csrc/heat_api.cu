@@ -211,6 +211,7 @@ static heat_status emis_tc_chunk(heat_ctx* ctx, int m, bool si, const double* P,
         prm.ldj = (long long)G * N;
         prm.j_f64 = j_f64 ? 1 : 0;
         prm.status = ctx->d_status.as<int>();
+        prm.wait_polls = ctx->wait_polls;
         CKR(launch_emis_tc(prm, tf32, split, ctx->sms, st));
     }
     return HEAT_OK;
@@ -1105,6 +1106,13 @@ heat_status heat_sync(heat_ctx* ctx) {
 }
 
 const char* heat_last_error(const heat_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+heat_status heat_set_wait_limit(heat_ctx* ctx, long long polls) {
+    if (!ctx) return HEAT_EINVAL;
+    if (polls < 0) return ctx->fail(HEAT_EINVAL, "heat_set_wait_limit: polls must be >= 0");
+    ctx->wait_polls = polls;
+    return HEAT_OK;
+}
 
 heat_status heat_get_cooling(heat_ctx* ctx, double* Cf) {
     if (!ctx || !Cf) return HEAT_EINVAL;

@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(192, 1) k_emis_tc(const __grid_constant__ Emis
                 tile_of(p, t, gi, mt, nt);
                 const int khalf = p.ksteps[gi] * KE;  // elements of one operand part
                 for (int ks = 0; ks < p.ksteps[gi]; ++ks) {
-                    if (!mbar_wait(b_empty + 8 * stage, phase ^ 1, abort_flag)) {
+                    if (!mbar_wait(b_empty + 8 * stage, phase ^ 1, abort_flag, p.wait_polls)) {
                         ok = false;
                         break;
                     }
@@ -148,14 +148,14 @@ __global__ void __launch_bounds__(192, 1) k_emis_tc(const __grid_constant__ Emis
             for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
                 int gi, mt, nt;
                 tile_of(p, t, gi, mt, nt);
-                if (!mbar_wait(b_tempty + 8 * acc, acc_phase ^ 1, abort_flag)) {
+                if (!mbar_wait(b_tempty + 8 * acc, acc_phase ^ 1, abort_flag, p.wait_polls)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
                 const uint32_t d = tmem_base + (uint32_t)acc * kN;
                 for (int ks = 0; ks < p.ksteps[gi]; ++ks) {
-                    if (!mbar_wait(b_full + 8 * stage, phase, abort_flag)) {
+                    if (!mbar_wait(b_full + 8 * stage, phase, abort_flag, p.wait_polls)) {
                         ok = false;
                         break;
                     }
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(192, 1) k_emis_tc(const __grid_constant__ Emis
         for (int t = blockIdx.x; t < total; t += gridDim.x) {
             int gi, mt, nt;
             tile_of(p, t, gi, mt, nt);
-            bool ok = __all_sync(0xffffffffu, mbar_wait(b_tfull + 8 * acc, acc_phase, abort_flag));
+            bool ok = __all_sync(0xffffffffu, mbar_wait(b_tfull + 8 * acc, acc_phase, abort_flag, p.wait_polls));
             if (!ok) {  // warp-uniform: the tcgen05.ld below is a warp-wide instruction
                 if (lane == 0) {
                     atomicOr(p.status, kStatTimeout);

@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(192, 1) k_gemm_bf16(const __grid_constant__ Ge
                 int z, mt, nt;
                 gtile(p, t, z, mt, nt);
                 for (int ks = 0; ks < ksteps; ++ks) {
-                    if (!mbar_wait(b_empty + 8 * stage, phase ^ 1, abort_flag)) {
+                    if (!mbar_wait(b_empty + 8 * stage, phase ^ 1, abort_flag, p.wait_polls)) {
                         ok = false;
                         break;
                     }
@@ -118,14 +118,14 @@ __global__ void __launch_bounds__(192, 1) k_gemm_bf16(const __grid_constant__ Ge
             uint32_t phase = 0, acc_phase = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
-                if (!mbar_wait(b_tempty + 8 * acc, acc_phase ^ 1, abort_flag)) {
+                if (!mbar_wait(b_tempty + 8 * acc, acc_phase ^ 1, abort_flag, p.wait_polls)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
                 const uint32_t d = tmem_base + (uint32_t)acc * gN;
                 for (int ks = 0; ks < ksteps; ++ks) {
-                    if (!mbar_wait(b_full + 8 * stage, phase, abort_flag)) {
+                    if (!mbar_wait(b_full + 8 * stage, phase, abort_flag, p.wait_polls)) {
                         ok = false;
                         break;
                     }
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(192, 1) k_gemm_bf16(const __grid_constant__ Ge
         for (int t = blockIdx.x; t < total; t += gridDim.x) {
             int z, mt, nt;
             gtile(p, t, z, mt, nt);
-            bool ok = __all_sync(0xffffffffu, mbar_wait(b_tfull + 8 * acc, acc_phase, abort_flag));
+            bool ok = __all_sync(0xffffffffu, mbar_wait(b_tfull + 8 * acc, acc_phase, abort_flag, p.wait_polls));
             if (!ok) {
                 if (lane == 0) {
                     atomicOr(p.status, kStatTimeout);

@@ -19,6 +19,7 @@ struct GemmTcParams {
     int mtiles, ntiles;
     int accumulate;                // 1: c += result
     int act;                       // 1: the BF16 output is GELU of the result (the FP32 output is not)
+    long long wait_polls;          // polls before a wait on another role gives up (kStatTimeout)
     int* status;
 };
 

@@ -14,6 +14,7 @@
 // threads) race on it and produce garbage.  Serialise them.
 #include <algorithm>
 #include <mutex>
+#include <string>
 
 #include "../../include/heat.h"
 #include "common.cuh"
@@ -23,7 +24,10 @@ namespace heat {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[HEAT_NOALLOC_SCRATCH_BYTES];
 
-// Task list for the no-allocation solve: grain-major (grain, 32-cell group) pairs.
+// Task list for the no-allocation solve: grain-major (grain, 32-cell group) pairs, one warp
+// per task (no task counters).  heat_solve instead runs its recursion persistently over a
+// cost-ordered list (longest tasks first); the results are the same, but here large grains
+// may start late, so this solve can take longer than heat_solve on the same cells.
 __global__ void k_noalloc_tasks(int2* tasks, int G, int NG) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < G * NG) tasks[t] = make_int2(t / NG, t % NG);
@@ -59,16 +63,29 @@ extern "C" heat_status heat_solve_noalloc(heat_ctx* ctx, int build, const double
                                           void* stream) {
     using namespace heat;
     if (!ctx) return HEAT_EINVAL;
-    if ((build != HEAT_BUILD_F64 && build != HEAT_BUILD_F32) || n_cells < 0 || (n_cells > 0 && (!u_dev || !P_out)))
-        return HEAT_EINVAL;
+    auto fail = [&](heat_status s, const char* msg) {
+        heat_internal_fail(ctx, msg);
+        return s;
+    };
+    auto cuda_fail = [&](cudaError_t e, const char* where) {
+        std::string m = std::string("heat_solve_noalloc: ") + where + ": " + cudaGetErrorString(e);
+        heat_internal_fail(ctx, m.c_str());
+        return HEAT_ECUDA;
+    };
+    if (build != HEAT_BUILD_F64 && build != HEAT_BUILD_F32)
+        return fail(HEAT_EINVAL, "heat_solve_noalloc: build must be HEAT_BUILD_F64 or HEAT_BUILD_F32");
+    if (n_cells < 0 || (n_cells > 0 && (!u_dev || !P_out)))
+        return fail(HEAT_EINVAL, "heat_solve_noalloc: negative cell count or null field/output pointer");
     GrainDev gd;
     int device = 0;
     int* status = nullptr;
     heat_status s = heat_internal_grain_view(ctx, &gd, &device, &status);
     if (s != HEAT_OK) return s;
     if (n_cells == 0) return HEAT_OK;
-    if (device < 0 || device >= kMaxDevices) return HEAT_EINVAL;
-    if (cudaSetDevice(device) != cudaSuccess) return HEAT_ECUDA;
+    if (device < 0 || device >= kMaxDevices)
+        return fail(HEAT_EINVAL, "heat_solve_noalloc: device ordinal beyond the supported 64");
+    cudaError_t ce = cudaSetDevice(device);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaSetDevice");
 
     // One-time set-up per device: the host-side symbol is only a stand-in, so look up
     // the array's device address with this device current.
@@ -77,7 +94,9 @@ extern "C" heat_status heat_solve_noalloc(heat_ctx* ctx, int build, const double
         std::lock_guard<std::mutex> lk(g_addr_mutex);
         if (!g_addr[device]) {
             void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return HEAT_ECUDA;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the scratch array");
+            if (!p) return fail(HEAT_ECUDA, "heat_solve_noalloc: null device address of the scratch array");
             g_addr[device] = p;
         }
         base = g_addr[device];
@@ -127,14 +146,16 @@ extern "C" heat_status heat_solve_noalloc(heat_ctx* ctx, int build, const double
         ch.P = P_out + (size_t)g0 * 32 * nbt;
         ch.ldP = nbt;
         ch.status = status;
-        if ((size_t)(p - (unsigned char*)base) > HEAT_NOALLOC_SCRATCH_BYTES) return HEAT_EINVAL;
+        if ((size_t)(p - (unsigned char*)base) > HEAT_NOALLOC_SCRATCH_BYTES)
+            return fail(HEAT_EINVAL, "heat_solve_noalloc: internal error: scratch carve-up exceeds the array");
         // Every scratch word is written before it is read (tasks, field tables, the B band,
         // intra-bin terms, then X row by row), so nothing needs clearing.
         k_noalloc_tasks<<<(ch.n_tasks + 127) / 128, 128, 0, st>>>(tasks, G, NG);
-        if (cudaGetLastError() != cudaSuccess) return HEAT_ECUDA;
-        if (launch_field(gd, u_dev, HEAT_F64, (long long)g0 * 32, ch, build, st) != cudaSuccess) return HEAT_ECUDA;
-        if (launch_build(gd, ch, build, st) != cudaSuccess) return HEAT_ECUDA;
-        if (launch_recur(gd, ch, build, st) != cudaSuccess) return HEAT_ECUDA;
+        if ((ce = cudaGetLastError()) != cudaSuccess) return cuda_fail(ce, "task-list launch");
+        if ((ce = launch_field(gd, u_dev, HEAT_F64, (long long)g0 * 32, ch, build, st)) != cudaSuccess)
+            return cuda_fail(ce, "field launch");
+        if ((ce = launch_build(gd, ch, build, st)) != cudaSuccess) return cuda_fail(ce, "build launch");
+        if ((ce = launch_recur(gd, ch, build, st)) != cudaSuccess) return cuda_fail(ce, "recursion launch");
     }
     return HEAT_OK;
 }

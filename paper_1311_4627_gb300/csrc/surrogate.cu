@@ -432,6 +432,7 @@ heat_status gemm(heat_ctx* ctx, int M, int N, int K, const __nv_bfloat16* A, con
     p.accumulate = accumulate;
     p.act = act;
     p.status = ctx->d_status.as<int>();
+    p.wait_polls = ctx->wait_polls;
     SCK(launch_gemm_bf16(p, ctx->sms, st));
     return HEAT_OK;
 }
@@ -486,6 +487,7 @@ heat_status gemm_members(heat_ctx* ctx, Surrogate* s, int l, int M, const __nv_b
     p.ntiles = (N + 127) / 128;
     p.act = act;
     p.status = ctx->d_status.as<int>();
+    p.wait_polls = ctx->wait_polls;
     SCK(launch_gemm_bf16(p, ctx->sms, st));
     return HEAT_OK;
 }

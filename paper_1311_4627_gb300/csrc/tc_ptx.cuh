@@ -8,7 +8,10 @@
 namespace heat {
 namespace tc {
 
-constexpr long long kTcSpinLimit = 1LL << 22;  // bounded mbarrier waits
+// Polls of a wait that drains the kernel's own copies and MMAs before it exits (these always
+// complete); waits on another role use the launch's wait_polls instead (HEAT_WAIT_POLLS_DEFAULT
+// unless heat_set_wait_limit changed it).
+constexpr long long kTcSpinLimit = 1LL << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -30,9 +33,10 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait; false when the limit is hit or another role has aborted.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-    for (long long i = 0; i < kTcSpinLimit; ++i) {
+// Bounded wait of at most `polls` polls; false when the limit is hit or another role has
+// aborted (polls = 0: give up at once).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, long long polls) {
+    for (long long i = 0; i < polls; ++i) {
         if (mbar_try(bar, parity)) return true;
         if ((i & 255) == 255 && *abort_flag) return false;
     }

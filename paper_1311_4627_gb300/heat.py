@@ -93,6 +93,10 @@ def lib():
                                     ctypes.POINTER(ctypes.c_int)]
         L.heat_get_timing.restype = ctypes.c_int
         L.heat_get_timing.argtypes = [_vp, _vp, _vp, ctypes.c_int]
+        L.heat_set_wait_limit.restype = ctypes.c_int
+        L.heat_set_wait_limit.argtypes = [_vp, ctypes.c_longlong]
+        L.heat_debye_enthalpy.restype = ctypes.c_double
+        L.heat_debye_enthalpy.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
         L.heat_solve_noalloc.restype = ctypes.c_int
         L.heat_solve_noalloc.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]
         for name, args in [
@@ -170,6 +174,20 @@ def heat_set_grains(ctx, radius_cm, c_abs_cm2, bin_offset, T_bins_K, H_bins_erg,
     st = lib().heat_set_grains(ctx, r.size, r.ctypes.data, c.ctypes.data, o.ctypes.data, t.ctypes.data,
                                e.ctypes.data, None if w is None else w.ctypes.data)
     _check(ctx, st)
+
+
+WAIT_POLLS_DEFAULT = 1 << 22
+
+
+def heat_set_wait_limit(ctx, polls):
+    _check(ctx, lib().heat_set_wait_limit(ctx, int(polls)))
+
+
+def heat_debye_enthalpy(theta_D: float, n_atoms: float, T) -> np.ndarray:
+    """H(T) in erg for each temperature in T (host; one call per value)."""
+    L = lib()
+    T = np.atleast_1d(np.asarray(T, dtype=np.float64))
+    return np.array([L.heat_debye_enthalpy(float(theta_D), float(n_atoms), float(t)) for t in T.ravel()]).reshape(T.shape)
 
 
 def heat_set_fields(ctx, n_cells, u, dtype, on_device, stream=None):

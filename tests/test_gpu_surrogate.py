@@ -17,12 +17,7 @@ pytestmark = pytest.mark.gpu
 DIMS = None  # set from n_lambda
 
 
-def _bf16(a):
-    """Round float32 values to bfloat16 (nearest even), as float64."""
-    a = np.ascontiguousarray(a, dtype=np.float32)
-    u = a.view(np.uint32).astype(np.uint64)
-    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
-    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+_bf16 = mlp.bf16_round
 
 
 @pytest.fixture(scope="module")
@@ -56,16 +51,23 @@ def test_gradients_match_cpu_fp64_mlp(small):
     G = torch.zeros(flat.size, dtype=torch.float32, device="cuda")
     loss_gpu = heat.heat_surrogate_grads(lib.ctx, 0, X, T, n, G, torch.cuda.current_stream().cuda_stream)
     g_gpu = G.cpu().numpy().astype(np.float64)
-    loss_cpu, g_cpu = mlp.loss_and_grad(mlp.unflatten(flat_b, dims), xn, tn.astype(np.float64))
-    assert abs(loss_gpu / loss_cpu - 1.0) < 2e-2
+    # the CPU side rounds to BF16 where the GPU stores BF16 (activations, dY, dZ), so the
+    # remaining differences are FP32 accumulation order and the odd value within FP32
+    # rounding of a BF16 tie: compared element by element, each within 1e-2 of itself plus
+    # 1e-3 of its block's largest element (a wrong row, column or tile edge is off by O(1))
+    loss_cpu, g_cpu = mlp.loss_and_grad(mlp.unflatten(flat_b, dims), xn, tn.astype(np.float32).astype(np.float64),
+                                        quantize=_bf16)
+    assert abs(loss_gpu / loss_cpu - 1.0) < 1e-3
     k = 0
     for i in range(len(dims) - 1):
         for size in (dims[i] * dims[i + 1], dims[i + 1]):
             a, b = g_gpu[k:k + size], g_cpu[k:k + size]
             k += size
+            bound = 1e-2 * np.abs(b) + 1e-3 * np.max(np.abs(b))
+            bad = np.abs(a - b) > bound
+            assert not np.any(bad), (i, size, int(bad.sum()), float(np.max(np.abs(a - b) / (np.abs(b) + 1e-30))))
             rel = np.linalg.norm(a - b) / np.linalg.norm(b)
-            cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
-            assert rel < 5e-2 and cos > 0.998, (i, size, rel, cos)
+            assert rel < 1e-2, (i, size, rel)
 
 
 @pytest.fixture(scope="module")

@@ -47,6 +47,40 @@ def test_noalloc_matches_heat_solve_on_two_calls(lib200, build):
         assert ok and r <= EXACT_TOL, (call, r)
 
 
+@pytest.mark.parametrize("n_cells", [1, 16])
+@pytest.mark.parametrize("build", [heat.HEAT_BUILD_F64, heat.HEAT_BUILD_F32])
+def test_noalloc_small_solves_match_heat_solve(lib200, build, n_cells):
+    """At most 16 cells take the element-parallel build and recursion in both entry points;
+    the no-allocation call must pick them too and give heat_solve's P on two calls."""
+    import torch
+
+    wl, lib = lib200
+    P_ref, _ = lib.solve(want_j=False, build=build, cell_count=n_cells)
+    stream = torch.cuda.current_stream().cuda_stream
+    for call in range(2):
+        P = torch.full((n_cells, wl.total_bins), float("nan"), dtype=torch.float64, device="cuda")
+        heat.heat_solve_noalloc(lib.ctx, build, lib.u, n_cells, P, stream)
+        heat.heat_sync(lib.ctx)
+        Pg = P.cpu().numpy()
+        assert np.all(np.isfinite(Pg)), f"call {call}: unwritten output"
+        r, ok = relerr(Pg, P_ref)
+        assert ok and r <= EXACT_TOL, (call, r)
+
+
+def test_noalloc_argument_errors_carry_a_message(lib200):
+    import torch
+
+    wl, lib = lib200
+    P = torch.zeros((4, wl.total_bins), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    with pytest.raises(heat.HeatError) as ei:
+        heat.heat_solve_noalloc(lib.ctx, 7, lib.u, 4, P, stream)
+    assert ei.value.status == heat.HEAT_EINVAL and "build" in str(ei.value)
+    with pytest.raises(heat.HeatError) as ei:
+        heat.heat_solve_noalloc(lib.ctx, heat.HEAT_BUILD_F64, None, 4, P, stream)
+    assert ei.value.status == heat.HEAT_EINVAL and "null" in str(ei.value)
+
+
 def test_noalloc_rejects_grains_beyond_the_static_scratch():
     import torch
 
