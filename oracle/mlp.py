@@ -100,3 +100,23 @@ def loss_and_grad(layers, x, t, quantize=None):
         if i > 0:
             g = q((g @ W) * gelu_grad(zs[i - 1]))
     return L, flatten(grads)
+
+
+def gradient_scale(layers, x, t, quantize=None):
+    """For every gradient element, the sum of the absolute values of the terms that make it:
+    the backward pass of loss_and_grad run on |.| of every factor (|2 (y - t)| / count, |W|,
+    |GELU'(z)|, |activations|).  It bounds |gradient| elementwise (triangle inequality) and is
+    the scale against which rounding differences of the terms are measured."""
+    q = quantize or _ident
+    y, zs, acts = forward(layers, x, quantize)
+    m = ~np.isnan(t)
+    cnt = max(1, int(m.sum()))
+    d = np.where(m, y - np.nan_to_num(t), 0.0)
+    g = np.abs(q(2.0 * d / cnt))
+    out = [None] * len(layers)
+    for i in range(len(layers) - 1, -1, -1):
+        W, _ = layers[i]
+        out[i] = (g.T @ np.abs(acts[i]), g.sum(axis=0))
+        if i > 0:
+            g = (g @ np.abs(W)) * np.abs(gelu_grad(zs[i - 1]))
+    return flatten(out)

@@ -63,3 +63,20 @@ def test_quantized_gradient_reduces_to_the_exact_one():
     L2, g2 = mlp.loss_and_grad(layers, x, t, quantize=mlp.bf16_round)
     assert abs(L2 / L0 - 1.0) < 2e-2
     assert 0.0 < np.linalg.norm(g2 - g0) / np.linalg.norm(g0) < 2e-2
+
+
+def test_gradient_scale_bounds_the_gradient():
+    """The absolute-term sums bound every gradient element, with and without BF16 storage,
+    and are not vacuous (most elements are within a factor 100 of their bound)."""
+    rng = np.random.default_rng(9)
+    dims = [12, 20, 20, 6]
+    n_params = sum(dims[i] * dims[i + 1] + dims[i + 1] for i in range(len(dims) - 1))
+    layers = mlp.unflatten(rng.normal(0, 0.4, n_params), dims)
+    x = rng.normal(0, 1, (32, dims[0]))
+    t = rng.normal(0, 1, (32, dims[-1]))
+    t[rng.random(t.shape) < 0.15] = np.nan
+    for q in (None, mlp.bf16_round):
+        _, g = mlp.loss_and_grad(layers, x, t, quantize=q)
+        sc = mlp.gradient_scale(layers, x, t, quantize=q)
+        assert np.all(np.abs(g) <= sc * (1 + 1e-12))
+        assert np.median(np.abs(g) / sc) > 1e-2
