@@ -131,6 +131,14 @@ typedef struct heat_opts {
                            probability and of j_lambda at any wavelength relative to its peak.
                            Results still do not depend on chunking or grouping.  Outside [0, 1):
                            HEAT_EINVAL                                                          */
+    int fused_build;    /* 0 (default): a build kernel writes the B band to device memory, then the
+                           recursion reads it.  1: on the mixed path (HEAT_BUILD_F32, integral
+                           heating, more than 16 cells) the matrix build runs inside the recursion
+                           kernel and the B band never exists in memory (4 bytes per band element
+                           and cell less scratch, so larger default chunks); timed as HEAT_T_RECUR
+                           with no HEAT_T_BUILD launches.  Elsewhere it is ignored.  Results are
+                           bit-identical either way.  On a GB300 the fused kernel is slower (it
+                           issues the build's instructions in the recursion's warps)            */
 } heat_opts;
 
 /* kernel classes reported by heat_get_timing */

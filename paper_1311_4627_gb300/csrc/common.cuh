@@ -37,6 +37,19 @@ struct __align__(16) PatF32 {  // one 128-bit load
     float zt;
 };
 
+// Band element in row order (the fused build + recursion of the mixed path): with the
+// cell's photon prefix phi_n at the start of segment n and its field values (u_n, su_n),
+//   B = phi_n + u_n cat E1(fmaf(su_n, t, zt))          (the same expression as PatF32)
+// n = the segment of the transition wavelength; N-1 where it is at or beyond the last node
+// (cat = t = zt = 0: B = the whole grid's prefix); N for a diagonal element whose transition
+// wavelength is below the grid (no photon part: B = 0 before the intra-bin term).
+struct __align__(16) RowEnt32 {
+    int n;
+    float t;
+    float cat;
+    float zt;
+};
+
 // Point-rule element (Eq. heating at the bin centres) of band element e = (u, j):
 // T_uj = Omega(lambda_uj) fac with lambda_uj = hc / (E_u - E_j) in segment n at offset
 // t = ln(lambda_uj / lambda_n), fac = lambda_uj^3 dE_u / (h^2 c); n = -1 where lambda_uj is

@@ -279,6 +279,7 @@ void heat_default_opts(heat_opts* o) {
     o->streams = 0;
     o->heating = HEAT_HEATING_INTEGRAL;
     o->prune_eps = 0.0;
+    o->fused_build = 0;
 }
 
 heat_status heat_create_grid(heat_ctx** out, int device, int n_lambda, const double* lambda_cm) {
@@ -403,6 +404,7 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
     };
     std::vector<int> diag_e(nbt, 0), diag_ok(nbt, 0);
     std::vector<PointEnt> pent;  // point-rule entries (Eq. heating), column by column
+    std::vector<RowEnt32> rent;  // every band element in row order (fused kernel)
     std::vector<int> pcol(nbt + 1, 0);
     for (int g = 0; g < G; ++g) {
         const int off = bin_offset[g], nb = bin_offset[g + 1] - off, M = nb - 1;
@@ -440,6 +442,10 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
                 double lf = kHChost / (Elo[f] - E[j]);
                 Ent en;
                 en.e = (int)(band_total + band);
+                RowEnt32 re;
+                re.n = N;  // no photon part unless the pattern loop below sets the segment
+                re.t = re.cat = re.zt = 0.0f;
+                rent.push_back(re);
                 if (!diag_in_band) {  // below the grid: no photon part, no pattern entry
                     ++band;
                     continue;
@@ -504,6 +510,11 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
             b.zt = (float)(s2 * en.t);
             pat64.push_back(a);
             pat32.push_back(b);
+            RowEnt32& re = rent[(size_t)en.e];  // the same element in row order
+            re.n = en.n;
+            re.t = b.t;
+            re.cat = b.cat;
+            re.zt = b.zt;
         }
         // soft-photon abscissae, sorted by segment, descending
         soft_off[g] = (int)soft.size();
@@ -538,8 +549,14 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
     }
     soft_off[G] = (int)soft.size();
     pcol[nbt] = (int)pent.size();
-    if ((long long)pent.size() != band_total)
-        return ctx->fail(HEAT_EINVAL, "heat_set_grains: point-rule table does not cover the band");
+    if ((long long)pent.size() != band_total || (long long)rent.size() != band_total)
+        return ctx->fail(HEAT_EINVAL, "heat_set_grains: element tables do not cover the band");
+    {   // padding: the fused kernel makes its B values in whole runs that may pass the end
+        RowEnt32 pad;
+        pad.n = N;
+        pad.t = pad.cat = pad.zt = 0.0f;
+        rent.insert(rent.end(), 128, pad);
+    }
     ctx->band_per_cell = band_total;
     ctx->max_bins = 0;
     for (int g = 0; g < G; ++g) ctx->max_bins = std::max(ctx->max_bins, bin_offset[g + 1] - bin_offset[g]);
@@ -553,7 +570,8 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
         upload(ctx->d_sC, sC) || upload(ctx->d_ca32, ca32) || upload(ctx->d_ce32, ce32) ||
         upload(ctx->d_sC32, sC32) || upload(ctx->d_rowptr, rowptr) || upload(ctx->d_wmax, wmax) || upload(ctx->d_pat64, pat64) ||
         upload(ctx->d_pat32, pat32) || upload(ctx->d_seg_ptr, seg_ptr) || upload(ctx->d_soft, soft) || upload(ctx->d_soft_off, soft_off) ||
-        upload(ctx->d_w, ctx->w) || upload(ctx->d_pent, pent) || upload(ctx->d_pcol, pcol))
+        upload(ctx->d_w, ctx->w) || upload(ctx->d_pent, pent) || upload(ctx->d_pcol, pcol) ||
+        upload(ctx->d_rent, rent))
         return ctx->fail(HEAT_ENOMEM, "heat_set_grains: device allocation failed");
     std::vector<int> koff_all = {0, nbt};
     if (upload(ctx->d_koff_all, koff_all)) return ctx->fail(HEAT_ENOMEM, "heat_set_grains: device allocation failed");
@@ -621,9 +639,14 @@ constexpr int kHostIoMinChunk = 1024;
 // X history, field tables per 32-cell group), at least one group; with several slots the range
 // is also split evenly over them.  More cells per chunk means more warps in flight for the
 // latency-bound build and recursion kernels.
-static int default_chunk(heat_ctx* ctx, int build, int count, int nslots) {
-    const size_t per_group = (size_t)ctx->band_per_cell * 32 * (build == 0 ? 8 : 4) + (size_t)ctx->nbt * 32 * 10 +
-                             (size_t)ctx->N * 32 * 16;
+// Whether a solve of `count` cells with these options runs the fused build + recursion.
+static bool uses_fused(const heat_opts& o, int count) {
+    return o.build == HEAT_BUILD_F32 && o.heating == HEAT_HEATING_INTEGRAL && count > kSmallCells && o.fused_build;
+}
+
+static int default_chunk(heat_ctx* ctx, int build, int count, int nslots, bool fused) {
+    const size_t band_bytes = fused ? 0 : (size_t)ctx->band_per_cell * 32 * (build == 0 ? 8 : 4);
+    const size_t per_group = band_bytes + (size_t)ctx->nbt * 32 * 10 + (size_t)ctx->N * 32 * 16;
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = size_t(16) << 30;
     size_t held = 0;
@@ -662,6 +685,8 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
     if (o.chunk_cells < 0 || (o.chunk_cells % 32) != 0)
         return ctx->fail(HEAT_EINVAL, "heat_solve: chunk_cells must be a non-negative multiple of 32");
     if (o.host_io < 0 || o.host_io > 2) return ctx->fail(HEAT_EINVAL, "heat_solve: host_io must be 0, 1 or 2");
+    if (o.fused_build != 0 && o.fused_build != 1)
+        return ctx->fail(HEAT_EINVAL, "heat_solve: fused_build must be 0 or 1");
     int c_begin = o.cell_begin, count = o.cell_count > 0 ? o.cell_count : ctx->n_cells - o.cell_begin;
     if (c_begin < 0 || count < 0 || c_begin + count > ctx->n_cells)
         return ctx->fail(HEAT_EINVAL, "heat_solve: cell range outside the fields");
@@ -691,7 +716,7 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
     // asynchronous host I/O the copies overlap the next call's kernels, so one chunk
     if (nslots == 0) nslots = (o.host_io == 1 && count >= 2 * kHostIoMinChunk) ? 2 : 1;
     nslots = std::min(nslots, (int)heat_ctx::kMaxSlots);
-    if (chunk == 0) chunk = default_chunk(ctx, build, count, nslots);
+    if (chunk == 0) chunk = default_chunk(ctx, build, count, nslots, uses_fused(o, count));
     const int n_chunks = (count + chunk - 1) / chunk;
     nslots = std::max(1, std::min(nslots, n_chunks));
     const int span = std::min(count, chunk);
@@ -700,6 +725,10 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
     const int tail_NG = (tail_cells + 31) / 32;
     const bool tc = want_j && o.emis > HEAT_EMIS_F64;
     const bool si = o.size_integrate != 0;
+    // the mixed path's build runs inside the recursion (no B band in memory)
+    const bool fused = uses_fused(o, count);
+    const int fused_nw = fused ? fused_warps(G * NG) : 0;
+    if (fused && fused_nw <= 0) return ctx->fail(HEAT_ECUDA, "heat_solve: occupancy query of the fused kernel failed");
 
     // task lists (uploaded before any chunk is launched: nothing in the chunk loop waits for the host)
     if (ctx->tasks_NG != NG) {
@@ -738,7 +767,10 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
             ok &= !sl.Bb64.ensure(sizeof(double) * (size_t)NG * std::max(1LL, ctx->band_per_cell) * 32);
         } else {
             ok &= !sl.ua32.ensure(sizeof(float2) * (size_t)N * Cc);  // (u, slope) pairs
-            ok &= !sl.Bb32.ensure(sizeof(float) * (size_t)NG * std::max(1LL, ctx->band_per_cell) * 32);
+            if (fused)
+                ok &= !sl.phs.ensure(sizeof(float) * (size_t)fused_nw * (N + 1) * 32);
+            else
+                ok &= !sl.Bb32.ensure(sizeof(float) * (size_t)NG * std::max(1LL, ctx->band_per_cell) * 32);
         }
         ok &= !sl.xs.ensure(sizeof(double) * (size_t)NG * nbt * 32);
         ok &= !sl.ep.ensure(sizeof(unsigned short) * (size_t)NG * nbt * 32);
@@ -801,6 +833,7 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
     gd.pent = ctx->d_pent.as<PointEnt>();
     gd.pcol = ctx->d_pcol.as<int>();
     gd.kexp = ctx->d_kexp.as<int>();
+    gd.rent = ctx->d_rent.as<RowEnt32>();
 
     // fork: every slot stream starts after the work already queued on the caller's stream
     if (nslots > 1) {
@@ -847,8 +880,13 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
         ch.work = sl.work.as<int>();
         CKR(cudaMemsetAsync(ch.work, 0, sizeof(int) * 2, cs));
         TIMED(HEAT_T_FIELD, launch_field(gd, ctx->u_dev, ctx->u_dtype, cell0, ch, build, cs));
-        TIMED(HEAT_T_BUILD, launch_build(gd, ch, build, cs));
-        TIMED(HEAT_T_RECUR, launch_recur(gd, ch, build, cs));
+        if (fused) {
+            ch.phs = sl.phs.as<float>();
+            TIMED(HEAT_T_RECUR, launch_fused(gd, ch, cs));
+        } else {
+            TIMED(HEAT_T_BUILD, launch_build(gd, ch, build, cs));
+            TIMED(HEAT_T_RECUR, launch_recur(gd, ch, build, cs));
+        }
         if (want_j) {
             char* jdst = o.host_io ? stj.as<char>() : (char*)j_out + (size_t)c0 * jrow * jel;
             cudaEvent_t ta = nullptr;
@@ -1024,7 +1062,8 @@ heat_status heat_graph_create(heat_ctx* ctx, const heat_opts* opts, double* P_ou
     if (o.streams == 0) o.streams = 1;
     if (o.chunk_cells == 0) {
         const int count = o.cell_count > 0 ? o.cell_count : ctx->n_cells - o.cell_begin;
-        o.chunk_cells = default_chunk(ctx, o.build, std::max(count, 1), std::min(o.streams, (int)heat_ctx::kMaxSlots));
+        o.chunk_cells = default_chunk(ctx, o.build, std::max(count, 1), std::min(o.streams, (int)heat_ctx::kMaxSlots),
+                                      uses_fused(o, count));
     }
     heat_status h = heat_solve(ctx, &o, P_out, j_out, stream);  // allocations, uploads, streams
     if (h != HEAT_OK) return h;
@@ -1162,12 +1201,12 @@ void heat_destroy(heat_ctx* ctx) {
                       &ctx->d_T, &ctx->d_E, &ctx->d_Cf, &ctx->d_invC, &ctx->d_invdE, &ctx->d_invdE32, &ctx->d_Cact,
                       &ctx->d_sC, &ctx->d_ca32, &ctx->d_ce32, &ctx->d_sC32, &ctx->d_rowptr, &ctx->d_wmax, &ctx->d_seg_ptr,
                       &ctx->d_pat64, &ctx->d_pat32, &ctx->d_soft, &ctx->d_soft_off, &ctx->d_K, &ctx->d_Kw, &ctx->d_w,
-                      &ctx->d_koff_all, &ctx->d_cde, &ctx->d_pent, &ctx->d_pcol, &ctx->d_kexp, &ctx->d_u_own, &ctx->s_tasks, &ctx->s_tasks_tail, &ctx->d_status};
+                      &ctx->d_koff_all, &ctx->d_cde, &ctx->d_pent, &ctx->d_pcol, &ctx->d_kexp, &ctx->d_rent, &ctx->d_u_own, &ctx->s_tasks, &ctx->s_tasks_tail, &ctx->d_status};
     for (DevBuf* b : bufs) b->release();
     for (auto& sl : ctx->slots) {
         DevBuf* sb[] = {&sl.ua64, &sl.su64, &sl.ua32, &sl.Bb64, &sl.Bb32, &sl.xs, &sl.ep,   &sl.pabs,
                         &sl.P,    &sl.j,    &sl.led,  &sl.A,    &sl.rowscale, &sl.work, &sl.P_alt, &sl.j_alt,
-                        &sl.led_alt};
+                        &sl.led_alt, &sl.phs};
         for (DevBuf* b : sb) b->release();
         if (sl.stream) cudaStreamDestroy(sl.stream);
         if (sl.done) cudaEventDestroy(sl.done);
@@ -1232,6 +1271,7 @@ __attribute__((visibility("hidden"))) heat_status heat_internal_grain_view(heat_
     gd->pent = ctx->d_pent.as<PointEnt>();
     gd->pcol = ctx->d_pcol.as<int>();
     gd->kexp = ctx->d_kexp.as<int>();
+    gd->rent = ctx->d_rent.as<RowEnt32>();
     *device = ctx->device;
     *status = ctx->d_status.as<int>();
     return HEAT_OK;

@@ -9,6 +9,7 @@ constexpr int kGLPoints = 16;
 struct PatF64;
 struct PatF32;
 struct SoftF64;
+struct RowEnt32;
 
 // ---- grain set-up (k_setup.cu)
 cudaError_t set_gauss_legendre(const double* x, const double* w);
@@ -53,6 +54,7 @@ struct GrainDev {
     const PointEnt* pent;   // point-rule entries, column by column (u descending within a column)
     const int* pcol;        // [nbt + 1] entries of column j of grain g at pcol[off_g + j] .. pcol[off_g + j + 1]
     const int* kexp;        // [nbt] biased binary exponent of max_lambda K[i][lambda] (-100000: none)
+    const RowEnt32* rent;   // [band_total] every band element in band (row) order, for the fused kernel
 };
 
 // Per-chunk scratch.
@@ -82,6 +84,8 @@ struct ChunkDev {
     int prune;          // L > 0: stop a spectrum's recursion at the tail test with threshold 2^-L; 0: off
     int* work;          // [2] task counters of the persistent launches (the recursion uses [1]), zero
                         //   before the launches; null: one warp per task
+    float* phs;         // fused kernel: per resident warp, the photon prefix table [N+1][32] (FP32,
+                        //   sign bit = the segment's short-series flag); null otherwise
 };
 
 // Solves of at most this many cells use the element-parallel build and recursion (a block
@@ -94,6 +98,11 @@ cudaError_t launch_field(const GrainDev& g, const void* u, int dtype, long long 
                          cudaStream_t st);
 cudaError_t launch_build(const GrainDev& g, const ChunkDev& ch, int build, cudaStream_t st);
 cudaError_t launch_recur(const GrainDev& g, const ChunkDev& ch, int build, cudaStream_t st);
+// The mixed path (FP32 build, integral heating, more than kSmallCells cells) with the matrix
+// build fused into the persistent recursion (k_fused.cu): B never goes to memory.  Needs
+// ch.work and ch.phs sized for fused_warps() warps.
+int fused_warps(int n_tasks);  // resident warps of the persistent launch for n_tasks tasks
+cudaError_t launch_fused(const GrainDev& g, const ChunkDev& ch, cudaStream_t st);
 
 // ---- emissivity (k_emis.cu)
 // C[z][m][n] = sum_{k in [koff[z], koff[z+1])} A[m][k] B[k][n] for z < nz, m < M, n < N;
