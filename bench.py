@@ -499,10 +499,9 @@ def main():
 
         total_ms = shard.max_over_ranks(total_ms)
     value = ws * cells * G * args.steps / (total_ms / 1e3)
-    # kernel launches: one per timed region, except that a tensor-core emissivity region holds
-    # two kernels (P packing, then the GEMM)
-    tc_path = PATHS[args.path][1] != "f64"
-    gpu_launches = int(sum(n * (2 if (name == "emis" and tc_path) else 1) for name, (_, n) in kt.items()))
+    # kernel launches: one per timed region (the per-grain tensor-core emissivity's operand is
+    # packed by the recursion's epilogue, so its region holds the GEMM alone)
+    gpu_launches = int(sum(n for _, (_, n) in kt.items()))
 
     # roofline of every kernel class, the dominant one as "roofline"
     nbt = wl.total_bins

@@ -139,6 +139,10 @@ typedef struct heat_opts {
                            with no HEAT_T_BUILD launches.  Elsewhere it is ignored.  Results are
                            bit-identical either way.  On a GB300 the fused kernel is slower (it
                            issues the build's instructions in the recursion's warps)            */
+    int recur_blocks_per_sm; /* resident blocks per SM of the persistent recursion (1..4); 0 = as many
+                           as fit (heat_autotune's choice if it made one).  Fewer leave room on
+                           every SM for another chunk's build kernel when chunks are in flight on
+                           several streams.  Results do not depend on it                        */
 } heat_opts;
 
 /* kernel classes reported by heat_get_timing */

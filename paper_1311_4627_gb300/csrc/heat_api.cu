@@ -174,17 +174,19 @@ static heat_status prepare_tc_rows(heat_ctx* ctx, int m, bool si, int Cc_alloc) 
     return HEAT_OK;
 }
 
-// Tensor-core emissivity of one chunk whose P rows are ready at P (row stride nbt): per-grain
-// j [cells][G][N], or with si the size-integrated J [cells][N].  A / rowscale: the slot's
+// Tensor-core emissivity of one chunk whose P rows are ready at P (row stride nbt), or, with
+// `packed`, whose operand A' and row scales the recursion has written: per-grain j
+// [cells][G][N], or with si the size-integrated J [cells][N].  A / rowscale: the slot's
 // operand buffers (sized by the caller).
 static heat_status emis_tc_chunk(heat_ctx* ctx, int m, bool si, const double* P, int cells, void* A, float* rowscale,
-                                 void* jdst, bool j_f64, cudaStream_t st) {
+                                 void* jdst, bool j_f64, bool packed, cudaStream_t st) {
     auto& t = si ? ctx->tc_si[m] : ctx->tc[m];
     const int G = si ? 1 : ctx->G, N = ctx->N;
     const bool tf32 = mode_tf32(m), split = mode_split(m);
     const size_t es = tf32 ? 4 : 2;
-    CKR(launch_pack_p(cells, G, si ? ctx->d_koff_all.as<int>() : ctx->d_bin_off.as<int>(), P, ctx->nbt,
-                      t.aoff.as<long long>(), t.kp.as<int>(), split, tf32, A, rowscale, st));
+    if (!packed)  // else the recursion's epilogue has written A' and the row scales
+        CKR(launch_pack_p(cells, G, si ? ctx->d_koff_all.as<int>() : ctx->d_bin_off.as<int>(), P, ctx->nbt,
+                          t.aoff.as<long long>(), t.kp.as<int>(), split, tf32, A, rowscale, st));
     EmisTcParams prm;  // ~25 KB of tensor maps, copied into the launch's parameters
     for (int g0 = 0; g0 < G; g0 += kMaxTcGrains) {
         int ng = std::min(kMaxTcGrains, G - g0);
@@ -280,6 +282,7 @@ void heat_default_opts(heat_opts* o) {
     o->heating = HEAT_HEATING_INTEGRAL;
     o->prune_eps = 0.0;
     o->fused_build = 0;
+    o->recur_blocks_per_sm = 0;
 }
 
 heat_status heat_create_grid(heat_ctx** out, int device, int n_lambda, const double* lambda_cm) {
@@ -687,6 +690,8 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
     if (o.host_io < 0 || o.host_io > 2) return ctx->fail(HEAT_EINVAL, "heat_solve: host_io must be 0, 1 or 2");
     if (o.fused_build != 0 && o.fused_build != 1)
         return ctx->fail(HEAT_EINVAL, "heat_solve: fused_build must be 0 or 1");
+    if (o.recur_blocks_per_sm < 0 || o.recur_blocks_per_sm > 4)
+        return ctx->fail(HEAT_EINVAL, "heat_solve: recur_blocks_per_sm must be in 0..4");
     int c_begin = o.cell_begin, count = o.cell_count > 0 ? o.cell_count : ctx->n_cells - o.cell_begin;
     if (c_begin < 0 || count < 0 || c_begin + count > ctx->n_cells)
         return ctx->fail(HEAT_EINVAL, "heat_solve: cell range outside the fields");
@@ -754,6 +759,9 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
         if ((hs = prepare_tc_rows(ctx, o.emis, si, Cc)) != HEAT_OK) return hs;
     }
 
+    // the recursion's epilogue packs the tensor-core operand (per-grain output, lane-per-cell
+    // kernels); P then goes to memory only where the caller asked for it
+    const bool pack_in_recur = tc && !si && !fused && count > kSmallCells;
     // scratch of every slot in use
     bool internal_P = (P_out == nullptr) || o.host_io;
     const bool async_io = o.host_io == 2;
@@ -870,6 +878,16 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
         DevBuf& stj = io_set ? sl.j_alt : sl.j;
         DevBuf& stl = io_set ? sl.led_alt : sl.led;
         ch.P = internal_P ? stP.as<double>() : P_out + (size_t)c0 * nbt;
+        if (pack_in_recur) {
+            auto& t = ctx->tc[o.emis];
+            ch.packA = sl.A.p;
+            ch.pack_aoff = t.aoff.as<long long>();
+            ch.pack_kp = t.kp.as<int>();
+            ch.pack_rowscale = sl.rowscale.as<float>();
+            ch.pack_tf32 = mode_tf32(o.emis) ? 1 : 0;
+            ch.pack_split = mode_split(o.emis) ? 1 : 0;
+            if (P_out == nullptr) ch.P = nullptr;  // nobody reads it
+        }
         ch.ledger = !o.ledger_out ? nullptr
                     : (o.host_io ? stl.as<double>() : o.ledger_out + (size_t)c0 * G * 2);
         long long cell0 = (long long)c_begin + c0;
@@ -878,6 +896,7 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
         for (int k = 0; k < 2; ++k)
             if (sl.copied_valid[k] && (!async_io || k == io_set)) CKR(cudaStreamWaitEvent(cs, sl.copied[k], 0));
         ch.work = sl.work.as<int>();
+        ch.blocks_per_sm = o.recur_blocks_per_sm > 0 ? o.recur_blocks_per_sm : ctx->tuned_recur_bps;
         CKR(cudaMemsetAsync(ch.work, 0, sizeof(int) * 2, cs));
         TIMED(HEAT_T_FIELD, launch_field(gd, ctx->u_dev, ctx->u_dtype, cell0, ch, build, cs));
         if (fused) {
@@ -896,7 +915,7 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
             }
             if (tc) {
                 heat_status hs = emis_tc_chunk(ctx, o.emis, si, ch.P, cells, sl.A.p, sl.rowscale.as<float>(), jdst,
-                                               o.j_dtype == HEAT_F64, cs);
+                                               o.j_dtype == HEAT_F64, pack_in_recur, cs);
                 if (hs != HEAT_OK) return hs;
             } else if (si)
                 CKR(launch_gemm_f64(cells, N, 1, ctx->d_koff_all.as<int>(), ch.P, nbt, ctx->d_Kw.as<double>(), N, jdst,

@@ -86,6 +86,16 @@ struct ChunkDev {
                         //   before the launches; null: one warp per task
     float* phs;         // fused kernel: per resident warp, the photon prefix table [N+1][32] (FP32,
                         //   sign bit = the segment's short-series flag); null otherwise
+    int blocks_per_sm;  // cap on the persistent recursion's resident blocks per SM (0: occupancy)
+    // The tensor-core emissivity's P operand, written by k_recur's epilogue (null: k_pack_p
+    // packs P afterwards, and P is always written).  Per grain, A'_g [cells][Kp_g] at packA +
+    // pack_aoff[g] elements (2 bytes, BF16, or 4, TF32), [P_hi | P_lo] when split, and the
+    // row scales [cells][G].  With packA set, P may be null (P not requested).
+    void* packA;
+    const long long* pack_aoff;
+    const int* pack_kp;
+    float* pack_rowscale;
+    int pack_tf32, pack_split;
 };
 
 // Solves of at most this many cells use the element-parallel build and recursion (a block

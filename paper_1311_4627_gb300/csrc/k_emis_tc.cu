@@ -21,6 +21,7 @@
 
 #include "common.cuh"
 #include "emis_tc.h"
+#include "pack.cuh"
 #include "tc_ptx.cuh"
 
 namespace heat {
@@ -306,18 +307,6 @@ cudaError_t launch_emis_tc(const EmisTcParams& p, bool tf32, bool split, int sms
 // ---------------------------------------------------------------------------
 // Operand packing.
 
-__device__ __forceinline__ uint16_t bf16_rn(float x) {
-    return __bfloat16_as_ushort(__float2bfloat16_rn(x));
-}
-__device__ __forceinline__ float bf16_f(uint16_t h) { return __bfloat162float(__ushort_as_bfloat16(h)); }
-
-// Round an FP32 value to TF32 (10 explicit mantissa bits), ties away from zero.
-__device__ __forceinline__ float tf32_rn(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-
 // Split a value already scaled into [0, 1] into hi + lo for the operand format.
 __device__ __forceinline__ void split_bf16(double v, uint16_t& hi, uint16_t& lo) {
     hi = bf16_rn((float)v);
@@ -336,21 +325,6 @@ __device__ __forceinline__ int scale_exp(double m) {
     return e;
 }
 
-// P * 2^-e rounded to FP32 (to nearest even) with integer operations only: P >= 0 is an
-// FP64 value and e its row's scale exponent; results below the FP32 normal range flush
-// to 0.  The FP64 pipe (one warp-wide instruction per 64 cycles on this part) stays out
-// of the packing, which is then bound by its memory traffic.
-__device__ __forceinline__ float scaled_to_f32(double p, int e) {
-    const unsigned hi = (unsigned)__double2hiint(p), lo = (unsigned)__double2loint(p);
-    const int fe = (int)(hi >> 20) - e - 896;  // FP32 biased exponent of p * 2^-e
-    if (fe <= 0) return 0.0f;
-    const unsigned m23 = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
-    const unsigned rest = lo & 0x1FFFFFFFu;
-    unsigned fb = ((unsigned)fe << 23) | m23;
-    fb += (rest > 0x10000000u || (rest == 0x10000000u && (m23 & 1u))) ? 1u : 0u;
-    return __uint_as_float(fb);
-}
-
 // A' for one chunk: one warp per (cell, grain).  P [cells][nbt] FP64 in, per grain
 // A'_g [cells][Kp_g] (BF16 or TF32-in-FP32; [P_hi | P_lo] when split) out, and rowscale [cells][G] = 2^e with e
 // the smallest exponent for which the row's largest P divided by 2^e is below 1.
@@ -367,8 +341,7 @@ __global__ void k_pack_p(int cells, int G, const int* __restrict__ bin_off, cons
     unsigned mh = 0;
     for (int i = lane; i < nb; i += 32) mh = max(mh, (unsigned)__double2hiint(pr[i]));
     mh = __reduce_max_sync(0xffffffffu, mh);
-    // frexp exponent of the maximum: m = f 2^e, f in [0.5, 1); 0 for an all-zero row
-    const int e = mh >= 0x00100000u ? (int)(mh >> 20) - 1022 : 0;
+    const int e = row_scale_exp(mh);
     if (lane == 0) rowscale[(size_t)c * G + g] = ldexpf(1.0f, e);
     const int K = kp[g], half = split ? K / 2 : K;  // [hi | lo], each part half wide
     if (tf32) {

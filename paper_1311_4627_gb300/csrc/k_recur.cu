@@ -4,6 +4,7 @@
 // element-parallel kernel for solves of few cells.
 #include "common.cuh"
 #include "internal.h"
+#include "pack.cuh"
 
 namespace heat {
 
@@ -95,6 +96,76 @@ __device__ __forceinline__ void window_tail(int nreg, const typename BandRaw<BUI
     }
 }
 
+// Epilogue with the emissivity operand (ch.packA): P_i = X_i / sum X for i <= i_end (0 above,
+// the pruned tail), written to P when requested and weighted by the bin's emitted power for
+// the energy check (returned), and packed for the tensor cores exactly as k_pack_p packs a P
+// row: row scale 2^e from the row's largest P (its running maximum, normalised), then each P
+// divided by 2^e, rounded to FP32 and split into hi + lo, eight bins per 16-byte store (each
+// lane writes its own cell's row).
+__device__ __noinline__ double pack_epilogue(const GrainDev& gd, const ChunkDev& ch, int g, int cc, int M, int i_end,
+                                             double inv, int epoch, long long xmaxb, const double* xl,
+                                             const unsigned short* epl) {
+    const int off = gd.bin_off[g];
+    double* prow = ch.P ? ch.P + (size_t)cc * ch.ldP + off : nullptr;
+    const double* cde = gd.cde + off;
+    double emit = 0.0;
+    const int e = row_scale_exp((unsigned)__double2hiint(__longlong_as_double(xmaxb) * inv));
+    ch.pack_rowscale[(size_t)cc * gd.G + g] = ldexpf(1.0f, e);
+    const int K = ch.pack_kp[g], half = ch.pack_split ? K / 2 : K;
+    const bool ledger = ch.ledger != nullptr;
+    auto p_of = [&](int i) {
+        return i <= i_end ? scale_down_800(xl[i * 32], epoch - (int)epl[i * 32]) * inv : 0.0;
+    };
+    if (ch.pack_tf32) {
+        float* row = (float*)ch.packA + ch.pack_aoff[g] + (size_t)cc * K;
+        for (int i0 = 0; i0 < half; i0 += 4) {
+            float4 h, l;
+            float* hv = &h.x;
+            float* lv = &l.x;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int i = i0 + k;
+                const double p = p_of(i);
+                if (i <= M && prow) prow[i] = p;
+                if (ledger && i <= i_end) emit = fma(p, cde[i], emit);
+                const float v = scaled_to_f32(p, e);
+                hv[k] = tf32_rn(v);
+                lv[k] = tf32_rn(v - hv[k]);
+            }
+            *(float4*)(row + i0) = h;
+            if (ch.pack_split) *(float4*)(row + half + i0) = l;
+        }
+    } else {
+        uint16_t* row = (uint16_t*)ch.packA + ch.pack_aoff[g] + (size_t)cc * K;
+        for (int i0 = 0; i0 < half; i0 += 8) {
+            uint4 h, l;
+            unsigned* hv = &h.x;
+            unsigned* lv = &l.x;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                unsigned hp = 0, lp = 0;
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    const int i = i0 + 2 * k + s;
+                    const double p = p_of(i);
+                    if (i <= M && prow) prow[i] = p;
+                    if (ledger && i <= i_end) emit = fma(p, cde[i], emit);
+                    const float v = scaled_to_f32(p, e);
+                    const uint16_t hb = bf16_rn(v);
+                    const uint16_t lb = bf16_rn(v - bf16_f(hb));
+                    hp |= (unsigned)hb << (16 * s);
+                    lp |= (unsigned)lb << (16 * s);
+                }
+                hv[k] = hp;
+                lv[k] = lp;
+            }
+            *(uint4*)(row + i0) = h;
+            if (ch.pack_split) *(uint4*)(row + half + i0) = l;
+        }
+    }
+    return emit;
+}
+
 // One task: the recursion of grain g for the 32 cells of group grp (lane = cell).  W is
 // the register window: the last W values of X, and the window part of each row's band
 // (its last min(width, W) elements), prefetched one row ahead.  The row loop's fixed
@@ -131,6 +202,9 @@ __device__ __forceinline__ void recur_task(const GrainDev& gd, const ChunkDev& c
     xl[0] = 1.0;
     epl[0] = 0;
     double total = 1.0;  // running sum of X, rescaled with it
+    // running maximum of X (bit pattern: X >= 0 orders as its bits), rescaled with it; it
+    // gives the row scale of the packed emissivity operand without another pass over X
+    long long xmaxb = __double_as_longlong(1.0);
     // register window: w[k] = X_{f-1-k}; the band's last elements read it instead of
     // reloading what this thread just stored
     double w[W];
@@ -249,11 +323,13 @@ __device__ __forceinline__ void recur_task(const GrainDev& gd, const ChunkDev& c
         xl[f * 32] = X;
         epl[f * 32] = (unsigned short)epoch;
         total += X;
+        xmaxb = max(xmaxb, __double_as_longlong(X));
 #pragma unroll
         for (int k = W - 1; k > 0; --k) w[k] = w[k - 1];
         w[0] = X;
         if (above_rescale(X)) {
             ++epoch;
+            xmaxb = __double_as_longlong(scale_down_800(__longlong_as_double(xmaxb), 1));
             const int lo = more ? (f + 1) - (e2 - e1) : f + 1;  // next row's band start
             // exact power-of-two scaling on the integer pipe (the exponent field lowered by 800)
             for (int i = lo; i <= f; ++i) {
@@ -278,7 +354,15 @@ __device__ __forceinline__ void recur_task(const GrainDev& gd, const ChunkDev& c
 #pragma unroll
         for (int k = 0; k < W; ++k) br[k] = br_n[k];
     }
-    if (cc < ch.cells) {
+    if (cc < ch.cells && ch.packA) {
+        const double inv = 1.0 / total;
+        const double emit = pack_epilogue(gd, ch, g, cc, M, PRUNE ? f_last : M, inv, epoch, xmaxb, xl, epl);
+        if (ch.ledger) {
+            double* lg = ch.ledger + ((size_t)cc * gd.G + g) * 2;
+            lg[0] = ch.pabs[(size_t)cc * gd.G + g];
+            lg[1] = emit;
+        }
+    } else if (cc < ch.cells) {
         const double inv = 1.0 / total;
         double* prow = ch.P + (size_t)cc * ch.ldP + off;
         double emit = 0.0;
@@ -420,6 +504,7 @@ static unsigned task_grid(K kernel, const ChunkDev& ch) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 128, 0) != cudaSuccess)
         return full;
+    if (ch.blocks_per_sm > 0 && ch.blocks_per_sm < occ) occ = ch.blocks_per_sm;
     const unsigned cap = (unsigned)(sms > 0 && occ > 0 ? sms * occ : 1);
     return full < cap ? full : cap;
 }

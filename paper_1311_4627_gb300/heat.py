@@ -43,7 +43,8 @@ class heat_opts(ctypes.Structure):
                 ("size_integrate", ctypes.c_int), ("cell_begin", ctypes.c_int), ("cell_count", ctypes.c_int),
                 ("chunk_cells", ctypes.c_int), ("host_io", ctypes.c_int), ("timing", ctypes.c_int),
                 ("ledger_out", ctypes.c_void_p), ("streams", ctypes.c_int), ("heating", ctypes.c_int),
-                ("prune_eps", ctypes.c_double), ("fused_build", ctypes.c_int)]
+                ("prune_eps", ctypes.c_double), ("fused_build", ctypes.c_int),
+                ("recur_blocks_per_sm", ctypes.c_int)]
 
 
 _lib = None
