@@ -131,18 +131,22 @@ typedef struct heat_opts {
                            probability and of j_lambda at any wavelength relative to its peak.
                            Results still do not depend on chunking or grouping.  Outside [0, 1):
                            HEAT_EINVAL                                                          */
-    int fused_build;    /* 0 (default): a build kernel writes the B band to device memory, then the
-                           recursion reads it.  1: on the mixed path (HEAT_BUILD_F32, integral
-                           heating, more than 16 cells) the matrix build runs inside the recursion
-                           kernel and the B band never exists in memory (4 bytes per band element
-                           and cell less scratch, so larger default chunks); timed as HEAT_T_RECUR
-                           with no HEAT_T_BUILD launches.  Elsewhere it is ignored.  Results are
-                           bit-identical either way.  On a GB300 the fused kernel is slower (it
-                           issues the build's instructions in the recursion's warps)            */
+    int fused_build;    /* 1: on the mixed path (HEAT_BUILD_F32, integral heating, more than 16
+                           cells) the matrix build runs inside the recursion kernel and the B band
+                           never exists in memory (4 bytes per band element and cell less scratch,
+                           so larger default chunks); timed as HEAT_T_RECUR with no HEAT_T_BUILD
+                           launches.  2: a build kernel writes the B band to device memory, then
+                           the recursion reads it.  0 (default): heat_autotune's choice if it made
+                           one, else 2.  Elsewhere it is ignored.  Results are bit-identical either
+                           way.  On a GB300 the fused kernel is slower (it issues the build's
+                           instructions in the recursion's warps)                               */
     int recur_blocks_per_sm; /* resident blocks per SM of the persistent recursion (1..4); 0 = as many
                            as fit (heat_autotune's choice if it made one).  Fewer leave room on
                            every SM for another chunk's build kernel when chunks are in flight on
                            several streams.  Results do not depend on it                        */
+    int emis_n_tile;    /* wavelength columns of a tensor-core emissivity tile: 256 or 128 (tiles are
+                           128 cells x this; the operand ring holds 4 or 6 k-stages); 0 =
+                           heat_autotune's choice, else 256.  Results do not depend on it        */
 } heat_opts;
 
 /* kernel classes reported by heat_get_timing */
@@ -217,8 +221,12 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
  * both at 0 use it.  *streams_out / *chunk_out (or NULL) receive the choice (chunk 0 = the
  * default size).  Then, on that configuration, it times the recursion's task order (grains
  * longest first by band elements + w x rows, w in {0, 12, 30, 60}; 30 before tuning) and
- * keeps the fastest w for all later solves on the ctx (heat_set_grains resets it).  Results
- * do not depend on the order.  Runs the candidates on cuda_stream and synchronises; j_out / P_out as in
+ * keeps the fastest w for all later solves on the ctx (heat_set_grains resets it).  Then, one
+ * at a time on the configuration chosen so far, the launch shapes: the persistent recursion's
+ * resident blocks per SM (all, 3, 2), for tensor-core emissivity the tile width (256 or 128
+ * wavelengths), for the mixed path the fused build + recursion kernel; each kept if faster.
+ * heat_get_tuning reports the choice; solves whose opts leave a knob at 0 use it.  Results
+ * do not depend on any of them.  Runs the candidates on cuda_stream and synchronises; j_out / P_out as in
  * heat_solve (device, with room for the cells), overwritten.  Allocates a temporary buffer
  * of twice the L2 size.  Errors: as heat_solve. */
 heat_status heat_autotune(heat_ctx* ctx, const heat_opts* opts, double* P_out, void* j_out, void* cuda_stream,
@@ -237,6 +245,16 @@ heat_status heat_autotune(heat_ctx* ctx, const heat_opts* opts, double* P_out, v
  * heat_solve on the ctx with another configuration may reallocate that scratch: destroy
  * and recreate the graph after one.  opts->timing and opts->host_io are not allowed.
  * Errors: HEAT_EINVAL, HEAT_ESTATE, HEAT_ENOMEM, HEAT_ECUDA (capture refused). */
+/* The configuration heat_autotune chose for the ctx (all 0 before it ran; 0 = the default). */
+typedef struct heat_tuning {
+    int streams, chunk_cells;  /* chunks in flight and cells per chunk                            */
+    int row_weight;            /* the recursion's longest-first order: band + row_weight x rows   */
+    int recur_blocks_per_sm;   /* resident blocks per SM of the persistent recursion              */
+    int emis_n_tile;           /* tensor-core emissivity tile width (wavelengths)                 */
+    int fused_build;           /* 1: the mixed path's build runs inside the recursion             */
+} heat_tuning;
+heat_status heat_get_tuning(const heat_ctx* ctx, heat_tuning* out);
+
 typedef struct heat_graph heat_graph;
 heat_status heat_graph_create(heat_ctx* ctx, const heat_opts* opts, double* P_out, void* j_out, void* cuda_stream,
                               heat_graph** out);

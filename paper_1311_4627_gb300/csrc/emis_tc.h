@@ -9,7 +9,7 @@ constexpr int kMaxTcGrains = 96;  // grains per launch (tensor maps travel as ke
 
 struct EmisTcParams {
     CUtensorMap ta[kMaxTcGrains];  // A'_g: [cells][Kp_g] operand, 128B swizzle, box 128 rows
-    CUtensorMap tb[kMaxTcGrains];  // B'_g: [N][Kp_g] operand, box 256 rows
+    CUtensorMap tb[kMaxTcGrains];  // B'_g: [N][Kp_g] operand, box ntile rows (256 or 128)
     int ksteps[kMaxTcGrains];      // k blocks: (split ? Kp_g / 2 : Kp_g) / elements per 128-byte slice
     int grain[kMaxTcGrains];       // grain index of slot i
     int ng;                        // grains in this launch
@@ -25,7 +25,9 @@ struct EmisTcParams {
 };
 
 size_t emis_tc_smem_bytes();
-cudaError_t launch_emis_tc(const EmisTcParams& p, bool tf32, bool split, int sms, cudaStream_t st);
+// ntile: the tile's wavelength columns, 256 or 128 (p.ntiles = ceil(N / ntile); the B maps'
+// boxes are ntile rows high)
+cudaError_t launch_emis_tc(const EmisTcParams& p, bool tf32, bool split, int ntile, int sms, cudaStream_t st);
 cudaError_t launch_pack_p(int cells, int G, const int* bin_off, const double* P, long long ldP, const long long* aoff,
                           const int* kp, int split, int tf32, void* A, float* rowscale, cudaStream_t st);
 cudaError_t launch_pack_k(int N, int G, const int* bin_off, const double* K, const long long* boff, const int* kp,

@@ -179,7 +179,7 @@ static heat_status prepare_tc_rows(heat_ctx* ctx, int m, bool si, int Cc_alloc) 
 // [cells][G][N], or with si the size-integrated J [cells][N].  A / rowscale: the slot's
 // operand buffers (sized by the caller).
 static heat_status emis_tc_chunk(heat_ctx* ctx, int m, bool si, const double* P, int cells, void* A, float* rowscale,
-                                 void* jdst, bool j_f64, bool packed, cudaStream_t st) {
+                                 void* jdst, bool j_f64, bool packed, int ntile, cudaStream_t st) {
     auto& t = si ? ctx->tc_si[m] : ctx->tc[m];
     const int G = si ? 1 : ctx->G, N = ctx->N;
     const bool tf32 = mode_tf32(m), split = mode_split(m);
@@ -196,7 +196,7 @@ static heat_status emis_tc_chunk(heat_ctx* ctx, int m, bool si, const double* P,
             char* abase = (char*)A + es * (size_t)t.aoff_h[g];
             char* bbase = (char*)t.B.p + es * (size_t)t.boff_h[g];
             if (!encode_operand(&prm.ta[i], abase, tf32, t.kp_h[g], cells, 128) ||
-                !encode_operand(&prm.tb[i], bbase, tf32, t.kp_h[g], N, 256))
+                !encode_operand(&prm.tb[i], bbase, tf32, t.kp_h[g], N, ntile))
                 return ctx->fail(HEAT_ECUDA, "heat_solve: cuTensorMapEncodeTiled failed");
             prm.ksteps[i] = (split ? t.kp_h[g] / 2 : t.kp_h[g]) / (tf32 ? 32 : 64);
             prm.grain[i] = g;
@@ -206,7 +206,7 @@ static heat_status emis_tc_chunk(heat_ctx* ctx, int m, bool si, const double* P,
         prm.N = N;
         prm.G = G;
         prm.mtiles = (cells + 127) / 128;
-        prm.ntiles = (N + 255) / 256;
+        prm.ntiles = (N + ntile - 1) / ntile;
         prm.rowscale = rowscale;
         prm.colscale = t.colscale.as<float>();
         prm.j = jdst;
@@ -214,7 +214,7 @@ static heat_status emis_tc_chunk(heat_ctx* ctx, int m, bool si, const double* P,
         prm.j_f64 = j_f64 ? 1 : 0;
         prm.status = ctx->d_status.as<int>();
         prm.wait_polls = ctx->wait_polls;
-        CKR(launch_emis_tc(prm, tf32, split, ctx->sms, st));
+        CKR(launch_emis_tc(prm, tf32, split, ntile, ctx->sms, st));
     }
     return HEAT_OK;
 }
@@ -283,6 +283,7 @@ void heat_default_opts(heat_opts* o) {
     o->prune_eps = 0.0;
     o->fused_build = 0;
     o->recur_blocks_per_sm = 0;
+    o->emis_n_tile = 0;
 }
 
 heat_status heat_create_grid(heat_ctx** out, int device, int n_lambda, const double* lambda_cm) {
@@ -643,8 +644,9 @@ constexpr int kHostIoMinChunk = 1024;
 // is also split evenly over them.  More cells per chunk means more warps in flight for the
 // latency-bound build and recursion kernels.
 // Whether a solve of `count` cells with these options runs the fused build + recursion.
-static bool uses_fused(const heat_opts& o, int count) {
-    return o.build == HEAT_BUILD_F32 && o.heating == HEAT_HEATING_INTEGRAL && count > kSmallCells && o.fused_build;
+static bool uses_fused(const heat_ctx* ctx, const heat_opts& o, int count) {
+    const bool want = o.fused_build == 1 || (o.fused_build == 0 && ctx->tuned_fused);
+    return o.build == HEAT_BUILD_F32 && o.heating == HEAT_HEATING_INTEGRAL && count > kSmallCells && want;
 }
 
 static int default_chunk(heat_ctx* ctx, int build, int count, int nslots, bool fused) {
@@ -688,10 +690,13 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
     if (o.chunk_cells < 0 || (o.chunk_cells % 32) != 0)
         return ctx->fail(HEAT_EINVAL, "heat_solve: chunk_cells must be a non-negative multiple of 32");
     if (o.host_io < 0 || o.host_io > 2) return ctx->fail(HEAT_EINVAL, "heat_solve: host_io must be 0, 1 or 2");
-    if (o.fused_build != 0 && o.fused_build != 1)
-        return ctx->fail(HEAT_EINVAL, "heat_solve: fused_build must be 0 or 1");
+    if (o.fused_build < 0 || o.fused_build > 2)
+        return ctx->fail(HEAT_EINVAL, "heat_solve: fused_build must be 0, 1 or 2");
     if (o.recur_blocks_per_sm < 0 || o.recur_blocks_per_sm > 4)
         return ctx->fail(HEAT_EINVAL, "heat_solve: recur_blocks_per_sm must be in 0..4");
+    if (o.emis_n_tile != 0 && o.emis_n_tile != 128 && o.emis_n_tile != 256)
+        return ctx->fail(HEAT_EINVAL, "heat_solve: emis_n_tile must be 0, 128 or 256");
+    const int emis_nt = o.emis_n_tile ? o.emis_n_tile : (ctx->tuned_emis_nt ? ctx->tuned_emis_nt : 256);
     int c_begin = o.cell_begin, count = o.cell_count > 0 ? o.cell_count : ctx->n_cells - o.cell_begin;
     if (c_begin < 0 || count < 0 || c_begin + count > ctx->n_cells)
         return ctx->fail(HEAT_EINVAL, "heat_solve: cell range outside the fields");
@@ -721,7 +726,7 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
     // asynchronous host I/O the copies overlap the next call's kernels, so one chunk
     if (nslots == 0) nslots = (o.host_io == 1 && count >= 2 * kHostIoMinChunk) ? 2 : 1;
     nslots = std::min(nslots, (int)heat_ctx::kMaxSlots);
-    if (chunk == 0) chunk = default_chunk(ctx, build, count, nslots, uses_fused(o, count));
+    if (chunk == 0) chunk = default_chunk(ctx, build, count, nslots, uses_fused(ctx, o, count));
     const int n_chunks = (count + chunk - 1) / chunk;
     nslots = std::max(1, std::min(nslots, n_chunks));
     const int span = std::min(count, chunk);
@@ -731,7 +736,7 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
     const bool tc = want_j && o.emis > HEAT_EMIS_F64;
     const bool si = o.size_integrate != 0;
     // the mixed path's build runs inside the recursion (no B band in memory)
-    const bool fused = uses_fused(o, count);
+    const bool fused = uses_fused(ctx, o, count);
     const int fused_nw = fused ? fused_warps(G * NG) : 0;
     if (fused && fused_nw <= 0) return ctx->fail(HEAT_ECUDA, "heat_solve: occupancy query of the fused kernel failed");
 
@@ -915,7 +920,7 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
             }
             if (tc) {
                 heat_status hs = emis_tc_chunk(ctx, o.emis, si, ch.P, cells, sl.A.p, sl.rowscale.as<float>(), jdst,
-                                               o.j_dtype == HEAT_F64, pack_in_recur, cs);
+                                               o.j_dtype == HEAT_F64, pack_in_recur, emis_nt, cs);
                 if (hs != HEAT_OK) return hs;
             } else if (si)
                 CKR(launch_gemm_f64(cells, N, 1, ctx->d_koff_all.as<int>(), ch.P, nbt, ctx->d_Kw.as<double>(), N, jdst,
@@ -983,6 +988,9 @@ heat_status heat_autotune(heat_ctx* ctx, const heat_opts* opts, double* P_out, v
             if (sN == 1 && div == 1) continue;  // the default covers it
             cands.push_back({sN, chunk});
         }
+    // the launch-shape choices of an earlier tuning do not apply while these are timed
+    ctx->tuned_recur_bps = ctx->tuned_emis_nt = ctx->tuned_fused = 0;
+    ctx->tuned_streams = ctx->tuned_chunk = 0;
     // each timed solve starts with a cold L2 (a write larger than L2 before it), as a solve
     // on fresh fields would
     int l2 = 0;
@@ -1048,6 +1056,29 @@ heat_status heat_autotune(heat_ctx* ctx, const heat_opts* opts, double* P_out, v
     }
     ctx->row_weight = best_w;
     order_grains(ctx);
+    // then the launch shapes, each on the configuration chosen so far (kept where faster):
+    // the persistent recursion's resident blocks per SM, the tensor-core tile width and, on
+    // the mixed path, the fused build + recursion kernel
+    heat_status hk = HEAT_OK;
+    for (int v : {3, 2}) {  // resident recursion blocks per SM (0: as many as fit)
+        const int keep = ctx->tuned_recur_bps;
+        ctx->tuned_recur_bps = v;
+        float ms = 0.0f;
+        if ((hk = time_config(pick, &ms)) != HEAT_OK) return done(hk);
+        if (ms < best) best = ms; else ctx->tuned_recur_bps = keep;
+    }
+    if (opts->emis > HEAT_EMIS_F64 && opts->emis_n_tile == 0) {
+        ctx->tuned_emis_nt = 128;
+        float ms = 0.0f;
+        if ((hk = time_config(pick, &ms)) != HEAT_OK) return done(hk);
+        if (ms < best) best = ms; else ctx->tuned_emis_nt = 0;
+    }
+    if (opts->build == HEAT_BUILD_F32 && opts->heating == HEAT_HEATING_INTEGRAL && opts->fused_build == 0) {
+        ctx->tuned_fused = 1;
+        float ms = 0.0f;
+        if ((hk = time_config(pick, &ms)) != HEAT_OK) return done(hk);
+        if (ms < best) best = ms; else ctx->tuned_fused = 0;
+    }
     done(HEAT_OK);
     ctx->tuned_streams = pick.streams;
     ctx->tuned_chunk = pick.chunk;
@@ -1082,7 +1113,7 @@ heat_status heat_graph_create(heat_ctx* ctx, const heat_opts* opts, double* P_ou
     if (o.chunk_cells == 0) {
         const int count = o.cell_count > 0 ? o.cell_count : ctx->n_cells - o.cell_begin;
         o.chunk_cells = default_chunk(ctx, o.build, std::max(count, 1), std::min(o.streams, (int)heat_ctx::kMaxSlots),
-                                      uses_fused(o, count));
+                                      uses_fused(ctx, o, count));
     }
     heat_status h = heat_solve(ctx, &o, P_out, j_out, stream);  // allocations, uploads, streams
     if (h != HEAT_OK) return h;
@@ -1164,6 +1195,17 @@ heat_status heat_sync(heat_ctx* ctx) {
 }
 
 const char* heat_last_error(const heat_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+heat_status heat_get_tuning(const heat_ctx* ctx, heat_tuning* out) {
+    if (!ctx || !out) return HEAT_EINVAL;
+    out->streams = ctx->tuned_streams;
+    out->chunk_cells = ctx->tuned_chunk;
+    out->row_weight = ctx->row_weight;
+    out->recur_blocks_per_sm = ctx->tuned_recur_bps;
+    out->emis_n_tile = ctx->tuned_emis_nt;
+    out->fused_build = ctx->tuned_fused;
+    return HEAT_OK;
+}
 
 heat_status heat_set_wait_limit(heat_ctx* ctx, long long polls) {
     if (!ctx) return HEAT_EINVAL;

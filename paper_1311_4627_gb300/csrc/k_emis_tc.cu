@@ -28,11 +28,13 @@ namespace heat {
 
 namespace {
 
-constexpr int kM = 128, kN = 256;
-constexpr int kAStage = kM * 128;  // bytes of one A tile: 128 rows x 128 B
-constexpr int kBStage = kN * 128;  // bytes of one B tile: 256 rows x 128 B
-constexpr int kRingBytes = 4 * (kAStage + kBStage);
-constexpr int kMaxStages = 4;
+// Tile M = 128 rows (cells) by NT = 256 or 128 columns (wavelengths); the operand ring is
+// 192 KB either way: 4 stages of one A and one B tile at NT = 256 (2 when split), 6 at
+// NT = 128 (3 when split).
+constexpr int kM = 128;
+constexpr int kAStage = kM * 128;            // bytes of one A tile: 128 rows x 128 B
+constexpr int kRingBytes = 4 * (kAStage + 256 * 128);
+constexpr int kMaxStages = 6;
 constexpr int kEpiWarps = 4;
 
 }  // namespace
@@ -51,11 +53,14 @@ __device__ __forceinline__ void tile_of(const EmisTcParams& p, int t, int& gi, i
 
 }  // namespace
 
-template <bool TF32, bool SPLIT>
+template <bool TF32, bool SPLIT, int kN>
 __global__ void __launch_bounds__(192, 1) k_emis_tc(const __grid_constant__ EmisTcParams p) {
     constexpr int NP = SPLIT ? 2 : 1;                        // operand parts (hi, lo)
-    constexpr int kStages = kMaxStages / NP;
+    constexpr int kBStage = kN * 128;                        // bytes of one B tile: kN rows x 128 B
     constexpr int kStageBytes = NP * (kAStage + kBStage);
+    constexpr int kStages = kRingBytes / kStageBytes;
+    constexpr uint32_t kTmemCols = 2 * kN;                   // two accumulators
+    static_assert(kStages >= 2 && kStages <= kMaxStages, "operand ring");
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     // stage s: A parts at s * kStageBytes + q * kAStage, B parts after the NP A tiles
@@ -84,7 +89,8 @@ __global__ void __launch_bounds__(192, 1) k_emis_tc(const __grid_constant__ Emis
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "n"(kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
         tc_fence_before();
@@ -271,13 +277,14 @@ __global__ void __launch_bounds__(192, 1) k_emis_tc(const __grid_constant__ Emis
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem_base) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "n"(kTmemCols)
+                     : "memory");
     }
 }
 
 size_t emis_tc_smem_bytes() { return 1024 + (size_t)kRingBytes + (2 * kMaxStages + 5) * 8 + 16; }
 
-template <bool TF32, bool SPLIT>
+template <bool TF32, bool SPLIT, int NT>
 static cudaError_t launch_emis_tc_t(const EmisTcParams& p, int grid, size_t smem, cudaStream_t st) {
     // the shared-memory opt-in is set once per device (not a stream operation, but kept out
     // of the launch path so that a solve can be captured into a CUDA graph)
@@ -287,21 +294,32 @@ static cudaError_t launch_emis_tc_t(const EmisTcParams& p, int grid, size_t smem
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr_set[dev]) {
-        e = cudaFuncSetAttribute(k_emis_tc<TF32, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_emis_tc<TF32, SPLIT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_set[dev] = true;
     }
-    k_emis_tc<TF32, SPLIT><<<grid, 192, smem, st>>>(p);
+    k_emis_tc<TF32, SPLIT, NT><<<grid, 192, smem, st>>>(p);
     return cudaGetLastError();
 }
 
-cudaError_t launch_emis_tc(const EmisTcParams& p, bool tf32, bool split, int sms, cudaStream_t st) {
+template <int NT>
+static cudaError_t launch_emis_tc_nt(const EmisTcParams& p, bool tf32, bool split, int grid, size_t smem,
+                                     cudaStream_t st) {
+    if (tf32)
+        return split ? launch_emis_tc_t<true, true, NT>(p, grid, smem, st)
+                     : launch_emis_tc_t<true, false, NT>(p, grid, smem, st);
+    return split ? launch_emis_tc_t<false, true, NT>(p, grid, smem, st)
+                 : launch_emis_tc_t<false, false, NT>(p, grid, smem, st);
+}
+
+cudaError_t launch_emis_tc(const EmisTcParams& p, bool tf32, bool split, int ntile, int sms, cudaStream_t st) {
     int total = p.ng * p.mtiles * p.ntiles;
     if (total <= 0) return cudaSuccess;
     size_t smem = emis_tc_smem_bytes();
     int grid = total < sms ? total : sms;
-    if (tf32) return split ? launch_emis_tc_t<true, true>(p, grid, smem, st) : launch_emis_tc_t<true, false>(p, grid, smem, st);
-    return split ? launch_emis_tc_t<false, true>(p, grid, smem, st) : launch_emis_tc_t<false, false>(p, grid, smem, st);
+    if (ntile == 128) return launch_emis_tc_nt<128>(p, tf32, split, grid, smem, st);
+    if (ntile == 256) return launch_emis_tc_nt<256>(p, tf32, split, grid, smem, st);
+    return cudaErrorInvalidValue;
 }
 
 // ---------------------------------------------------------------------------

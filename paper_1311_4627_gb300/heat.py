@@ -44,7 +44,12 @@ class heat_opts(ctypes.Structure):
                 ("chunk_cells", ctypes.c_int), ("host_io", ctypes.c_int), ("timing", ctypes.c_int),
                 ("ledger_out", ctypes.c_void_p), ("streams", ctypes.c_int), ("heating", ctypes.c_int),
                 ("prune_eps", ctypes.c_double), ("fused_build", ctypes.c_int),
-                ("recur_blocks_per_sm", ctypes.c_int)]
+                ("recur_blocks_per_sm", ctypes.c_int), ("emis_n_tile", ctypes.c_int)]
+
+
+class heat_tuning(ctypes.Structure):
+    _fields_ = [("streams", ctypes.c_int), ("chunk_cells", ctypes.c_int), ("row_weight", ctypes.c_int),
+                ("recur_blocks_per_sm", ctypes.c_int), ("emis_n_tile", ctypes.c_int), ("fused_build", ctypes.c_int)]
 
 
 _lib = None
@@ -94,6 +99,8 @@ def lib():
                                     ctypes.POINTER(ctypes.c_int)]
         L.heat_get_timing.restype = ctypes.c_int
         L.heat_get_timing.argtypes = [_vp, _vp, _vp, ctypes.c_int]
+        L.heat_get_tuning.restype = ctypes.c_int
+        L.heat_get_tuning.argtypes = [_vp, ctypes.POINTER(heat_tuning)]
         L.heat_set_wait_limit.restype = ctypes.c_int
         L.heat_set_wait_limit.argtypes = [_vp, ctypes.c_longlong]
         L.heat_debye_enthalpy.restype = ctypes.c_double
@@ -175,6 +182,12 @@ def heat_set_grains(ctx, radius_cm, c_abs_cm2, bin_offset, T_bins_K, H_bins_erg,
     st = lib().heat_set_grains(ctx, r.size, r.ctypes.data, c.ctypes.data, o.ctypes.data, t.ctypes.data,
                                e.ctypes.data, None if w is None else w.ctypes.data)
     _check(ctx, st)
+
+
+def heat_get_tuning(ctx) -> dict:
+    t = heat_tuning()
+    _check(ctx, lib().heat_get_tuning(ctx, ctypes.byref(t)))
+    return {name: getattr(t, name) for name, _ in heat_tuning._fields_}
 
 
 WAIT_POLLS_DEFAULT = 1 << 22

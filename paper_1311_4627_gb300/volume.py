@@ -10,6 +10,13 @@ missing or whose checksum does not match is computed again.  The manifest is rep
 atomically (written to a temporary file, then renamed).
 
     python -m paper_1311_4627_gb300.volume --out DIR [--shape 128 128 64] [--chunk 65536]
+
+Several GPUs (one process each, launched by torchrun): the ranks take chunks from a shared
+queue (shard.ChunkQueue) as they become free, so a faster device solves more of them (the
+paper's host + coprocessor scheduling, Appendix B), each rank records its chunks in its own
+manifest shard, and rank 0 merges the shards into the manifest at the end.
+
+    torchrun --nproc-per-node N -m paper_1311_4627_gb300.volume --out DIR ...
 """
 from __future__ import annotations
 
@@ -50,34 +57,70 @@ def energy_summary(ledger: np.ndarray, weights: np.ndarray) -> dict:
             "weighted_ratio": tot_e / tot_a if tot_a > 0 else None}
 
 
-class ChunkManifest:
-    """Checkpoint state of a chunked run (host logic only)."""
+def _write_json_atomic(out_dir: str, path: str, obj: dict) -> None:
+    fd, tmp = tempfile.mkstemp(dir=out_dir, prefix=".manifest.", suffix=".tmp")
+    with os.fdopen(fd, "w") as f:
+        json.dump(obj, f, indent=1, sort_keys=True)
+        f.flush()
+        os.fsync(f.fileno())
+    os.replace(tmp, path)
 
-    def __init__(self, out_dir: str, config: dict):
+
+def _shard_files(out_dir: str) -> list[str]:
+    return sorted(os.path.join(out_dir, f) for f in os.listdir(out_dir)
+                  if f.startswith("manifest.") and f.endswith(".json") and f != MANIFEST)
+
+
+class ChunkManifest:
+    """Checkpoint state of a chunked run (host logic only).  With `shard` (a rank's name in a
+    run of several processes) the records this process makes go to manifest.<shard>.json, so
+    that no two processes write one file; load() sees the manifest and every shard, and
+    merge() folds the shards into the manifest."""
+
+    def __init__(self, out_dir: str, config: dict, shard: str | None = None):
         self.out_dir = out_dir
         self.config = config
-        self.path = os.path.join(out_dir, MANIFEST)
-        self.chunks: dict[str, dict] = {}
+        self.path = os.path.join(out_dir, MANIFEST if shard is None else f"manifest.{shard}.json")
+        self.shard = shard
+        self.chunks: dict[str, dict] = {}  # every record seen (manifest and shards)
+        self.own: dict[str, dict] = {}     # records written by this process's file
+
+    def _read(self, path: str) -> dict:
+        with open(path) as f:
+            m = json.load(f)
+        if m.get("config") != self.config:
+            raise ValueError(f"{path}: written by a run with another configuration")
+        return m.get("chunks", {})
 
     def load(self, resume: bool) -> None:
         os.makedirs(self.out_dir, exist_ok=True)
-        if not resume or not os.path.exists(self.path):
-            self.chunks = {}
+        main = os.path.join(self.out_dir, MANIFEST)
+        if self.shard is None and (not resume or not os.path.exists(main)):
+            for p in _shard_files(self.out_dir):  # shards of an earlier run do not count
+                os.remove(p)
+            self.chunks, self.own = {}, {}
             self.save()
             return
-        with open(self.path) as f:
-            m = json.load(f)
-        if m.get("config") != self.config:
-            raise ValueError(f"{self.path}: written by a run with another configuration")
-        self.chunks = m.get("chunks", {})
+        self.chunks = {}
+        for p in ([main] if os.path.exists(main) else []) + _shard_files(self.out_dir):
+            self.chunks.update(self._read(p))
+        self.own = dict(self._read(self.path)) if self.shard is not None and os.path.exists(self.path) else \
+            (dict(self.chunks) if self.shard is None else {})
 
     def save(self) -> None:
-        fd, tmp = tempfile.mkstemp(dir=self.out_dir, prefix=".manifest.", suffix=".tmp")
-        with os.fdopen(fd, "w") as f:
-            json.dump({"version": 1, "config": self.config, "chunks": self.chunks}, f, indent=1, sort_keys=True)
-            f.flush()
-            os.fsync(f.fileno())
-        os.replace(tmp, self.path)
+        _write_json_atomic(self.out_dir, self.path, {"version": 1, "config": self.config, "chunks": self.own})
+
+    def merge(self) -> None:
+        """Fold every shard into the manifest (one process, after all shards are written)."""
+        main = os.path.join(self.out_dir, MANIFEST)
+        chunks = self._read(main) if os.path.exists(main) else {}
+        shards = _shard_files(self.out_dir)
+        for p in shards:
+            chunks.update(self._read(p))
+        _write_json_atomic(self.out_dir, main, {"version": 1, "config": self.config, "chunks": chunks})
+        for p in shards:
+            os.remove(p)
+        self.chunks = dict(chunks)
 
     def done(self, k: int) -> bool:
         """Chunk k finished and its file intact."""
@@ -89,7 +132,9 @@ class ChunkManifest:
 
     def record(self, k: int, fname: str, info: dict, sha256: str | None = None) -> None:
         p = os.path.join(self.out_dir, fname)
-        self.chunks[str(k)] = dict(info, file=fname, sha256=sha256 if sha256 is not None else sha256_file(p))
+        e = dict(info, file=fname, sha256=sha256 if sha256 is not None else sha256_file(p))
+        self.chunks[str(k)] = e
+        self.own[str(k)] = e
         self.save()
 
 
@@ -113,16 +158,23 @@ def write_chunk(out_dir: str, fname: str, J: np.ndarray) -> str:
 
 
 def run_chunks(manifest: ChunkManifest, n_cells: int, chunk: int, solve_chunk, resume: bool = True,
-               stop_after: int | None = None, prepare=None, log=None) -> dict:
+               stop_after: int | None = None, prepare=None, log=None, claim=None) -> dict:
     """Drive the chunks of [0, n_cells): skip the finished ones, solve the others with
     solve_chunk(k, begin, end, prepared) -> (J float32 [cells][n_lambda], info dict), write
     J_k.npy and record it.  prepare(begin, end), if given, runs one chunk ahead in a host
     thread (e.g. making the next chunk's fields while the GPU works); the file of a solved
     chunk is written and hashed in another host thread while the next chunk is solved, and
     recorded in the manifest once it is complete.  stop_after: return after that many
-    chunks were solved in this call (an interrupted run)."""
+    chunks were solved in this call (an interrupted run).  claim: an iterable of chunk
+    indices handed to this process (a shard.ChunkQueue shared by several), taken one chunk
+    ahead of the solve; without it every chunk is this process's."""
     manifest.load(resume)
-    todo = [k for k in range((n_cells + chunk - 1) // chunk) if not manifest.done(k)]
+    n_all = (n_cells + chunk - 1) // chunk
+    if claim is None:
+        todo = iter([k for k in range(n_all) if not manifest.done(k)])
+    else:  # claimed chunks that an earlier run finished are skipped
+        todo = (k for k in claim if not manifest.done(k))
+    todo = _lookahead(todo)
     solved = 0
     pending = None  # (k, fname, info, future) of the chunk being written
 
@@ -134,17 +186,20 @@ def run_chunks(manifest: ChunkManifest, n_cells: int, chunk: int, solve_chunk, r
 
     with ThreadPoolExecutor(1) as pool, ThreadPoolExecutor(1) as writer:
         nxt = None
-        if prepare and todo:
-            b = todo[0] * chunk
+        first = todo.peek()
+        if prepare and first is not None:
+            b = first * chunk
             nxt = pool.submit(prepare, b, min(n_cells, b + chunk))
-        for i, k in enumerate(todo):
-            if stop_after is not None and solved >= stop_after:
+        while stop_after is None or solved < stop_after:  # no chunk is claimed past the stop
+            k = next(todo, None)
+            if k is None:
                 break
             b, e = k * chunk, min(n_cells, (k + 1) * chunk)
             prepared = nxt.result() if nxt is not None else None
             nxt = None
-            if prepare and i + 1 < len(todo):
-                b2 = todo[i + 1] * chunk
+            k2 = todo.peek() if (stop_after is None or solved + 1 < stop_after) else None
+            if prepare and k2 is not None:
+                b2 = k2 * chunk
                 nxt = pool.submit(prepare, b2, min(n_cells, b2 + chunk))
             J, info = solve_chunk(k, b, e, prepared)
             if pending is not None:  # at most one chunk waits for the disk
@@ -154,9 +209,81 @@ def run_chunks(manifest: ChunkManifest, n_cells: int, chunk: int, solve_chunk, r
             solved += 1
         if pending is not None:
             finish(pending)
-    n_chunks = (n_cells + chunk - 1) // chunk
-    return {"chunks": n_chunks, "solved_now": solved,
-            "complete": all(manifest.done(k) for k in range(n_chunks))}
+    return {"chunks": n_all, "solved_now": solved, "complete": all(manifest.done(k) for k in range(n_all))}
+
+
+class _lookahead:
+    """An iterator with peek(): the next item, taken from the source one step early (so a
+    claimed chunk's fields can be prepared while the previous chunk is solved)."""
+
+    _END = object()
+
+    def __init__(self, it):
+        self.it = iter(it)
+        self.buf = self._END
+        self.buffered = False
+
+    def peek(self):
+        if not self.buffered:
+            self.buf = next(self.it, self._END)
+            self.buffered = True
+        return None if self.buf is self._END else self.buf
+
+    def __iter__(self):
+        return self
+
+    def __next__(self):
+        v = self.peek()
+        self.buffered = False
+        if v is None:
+            raise StopIteration
+        return v
+
+
+def run_distributed(out_dir: str, config: dict, n_cells: int, chunk: int, solve_chunk, resume: bool = True,
+                    stop_after: int | None = None, prepare=None, log=None) -> dict:
+    """run_chunks on every rank of an initialised torch.distributed process group (any
+    backend: only barriers and one broadcast of a path pass through it), the chunks handed out
+    by a ChunkQueue on a FileStore in the output directory.  Each rank records its chunks in
+    its manifest shard; rank 0 resets or checks the manifest first and merges the shards at
+    the end.  Returns this rank's run_chunks result plus the chunks it solved and, on rank 0,
+    whether the merged run is complete."""
+    import shutil
+
+    import torch.distributed as dist
+
+    from .shard import ChunkQueue
+
+    rank, world = dist.get_rank(), dist.get_world_size()
+    n_all = (n_cells + chunk - 1) // chunk
+    qdir = [None]
+    if rank == 0:
+        ChunkManifest(out_dir, config).load(resume)  # start a run or check the one resumed
+        qdir = [tempfile.mkdtemp(dir=out_dir, prefix=".queue.")]
+    dist.broadcast_object_list(qdir, src=0)
+    store = dist.FileStore(os.path.join(qdir[0], "store"), world)
+    dist.barrier()
+    man = ChunkManifest(out_dir, config, shard=f"r{rank}")
+    mine = []
+
+    def claim():
+        for k in ChunkQueue(store, n_all, name="volume"):
+            mine.append(k)
+            yield k
+
+    res = run_chunks(man, n_cells, chunk, solve_chunk, resume=True, stop_after=stop_after, prepare=prepare, log=log,
+                     claim=claim())
+    dist.barrier()
+    if rank == 0:
+        m = ChunkManifest(out_dir, config)
+        m.merge()
+        res["complete"] = all(m.done(k) for k in range(n_all))
+    dist.barrier()
+    del store
+    if rank == 0:
+        shutil.rmtree(qdir[0], ignore_errors=True)
+    res["claimed"] = mine
+    return res
 
 
 def load_output(manifest_dir: str) -> np.ndarray:
@@ -261,13 +388,33 @@ def main(argv=None):
     ap.add_argument("--stop-after", type=int, default=None)
     args = ap.parse_args(argv)
     t0 = time.perf_counter()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    device, rank = 0, 0
+    if world > 1:  # one process per GPU (torchrun); the process group only coordinates
+        import torch.distributed as dist
+
+        dist.init_process_group("gloo")
+        device, rank = int(os.environ.get("LOCAL_RANK", "0")), dist.get_rank()
     vol = W.rt_volume(tuple(args.shape), radii_per_composition=args.radii, nbins=args.bins, n_lambda=args.n_lambda)
-    solver = VolumeSolver(vol, args.chunk, emis=args.emis)
+    solver = VolumeSolver(vol, args.chunk, device=device, emis=args.emis)
     setup_s = time.perf_counter() - t0
-    man = ChunkManifest(args.out, volume_config(vol, args.chunk, args.emis))
-    res = run_chunks(man, vol.n_cells, args.chunk, solver.solve_chunk, resume=not args.no_resume,
-                     stop_after=args.stop_after, prepare=solver.prepare, log=print)
+    config = volume_config(vol, args.chunk, args.emis)
+    log = (lambda m: print(f"[rank {rank}] {m}")) if world > 1 else print
+    if world > 1:
+        res = run_distributed(args.out, config, vol.n_cells, args.chunk, solver.solve_chunk, resume=not args.no_resume,
+                              stop_after=args.stop_after, prepare=solver.prepare, log=log)
+    else:
+        res = run_chunks(ChunkManifest(args.out, config), vol.n_cells, args.chunk, solver.solve_chunk,
+                         resume=not args.no_resume, stop_after=args.stop_after, prepare=solver.prepare, log=log)
     solver.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+        if rank != 0:
+            return
+    man = ChunkManifest(args.out, config)
+    man.load(resume=True)
     ch = [man.chunks[k] for k in sorted(man.chunks, key=int)]
     gpu_s = sum(c["gpu_ms"] for c in ch) / 1e3
     spectra = sum(c["spectra"] for c in ch)

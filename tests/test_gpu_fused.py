@@ -74,7 +74,7 @@ def test_fused_full_size_bitwise_and_against_oracle():
         lib.set_fields(wl.u)
         st = torch.cuda.current_stream().cuda_stream
         out = []
-        for fused in (1, 0):
+        for fused in (1, 2):
             P = torch.empty(wl.n_cells, wl.total_bins, dtype=torch.float64, device="cuda")
             j = torch.empty(wl.n_cells, wl.n_grains, wl.n_lambda, dtype=torch.float32, device="cuda")
             heat.heat_solve(lib.ctx, heat.heat_default_opts(fused_build=fused, **MIXED), P, j, st)
@@ -94,5 +94,5 @@ def test_fused_full_size_bitwise_and_against_oracle():
 def test_fused_build_option_checks(sub):
     _, lib = sub
     with pytest.raises(heat.HeatError) as e:
-        lib.solve(fused_build=2, **MIXED)
+        lib.solve(fused_build=3, **MIXED)
     assert e.value.status == heat.HEAT_EINVAL

@@ -76,8 +76,18 @@ def test_autotune_choice_is_used_and_exact(wl_lib):
                                                              j_dtype=heat.HEAT_F32), None, j, st)
     heat.heat_sync(lib.ctx)
     assert 1 <= s <= 4 and c >= 0 and c % 32 == 0
+    t = heat.heat_get_tuning(lib.ctx)
+    assert (t["streams"], t["chunk_cells"]) == (s, c)
+    assert t["recur_blocks_per_sm"] in (0, 2, 3) and t["emis_n_tile"] in (0, 128) and t["fused_build"] in (0, 1)
     got = lib.solve(build=heat.HEAT_BUILD_F32, emis=heat.HEAT_EMIS_BF16X3, j_dtype=heat.HEAT_F32)
-    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+    # the tuned solve is the solve with the chosen knobs given explicitly, bit for bit ...
+    explicit = lib.solve(build=heat.HEAT_BUILD_F32, emis=heat.HEAT_EMIS_BF16X3, j_dtype=heat.HEAT_F32, streams=s,
+                         chunk_cells=c, recur_blocks_per_sm=t["recur_blocks_per_sm"],
+                         emis_n_tile=t["emis_n_tile"] or 256, fused_build=2 - t["fused_build"])
+    assert np.array_equal(got[0], explicit[0]) and np.array_equal(got[1], explicit[1])
+    # ... and P does not depend on the configuration; j only through the tensor-core tiling
+    assert np.array_equal(got[0], ref[0])
+    np.testing.assert_allclose(got[1], ref[1], rtol=1e-6, atol=0.0)
 
 
 def test_pipelined_mixed_path_against_oracle(wl_lib):

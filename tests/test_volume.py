@@ -105,3 +105,84 @@ def test_write_chunk_hashes_what_it_writes(tmp_path):
     assert np.array_equal(np.load(p), J)
     assert sha == V.sha256_file(p)
     assert not [f for f in os.listdir(tmp_path) if f.endswith(".tmp")]
+
+
+class OracleChunkSolver:
+    """Stand-in for the GPU solver of a volume run: a chunk's size-integrated J from the FP64
+    oracle (real spectra, so that a wrong or reordered chunk shows), optionally slow."""
+
+    def __init__(self, vol, delay=0.0):
+        import oracle
+
+        self.vol, self.delay = vol, delay
+        self.Cf = oracle.grain_cooling(vol.grains)
+
+    def solve(self, k, b, e, prepared):
+        import time
+
+        import oracle
+
+        if self.delay:
+            time.sleep(self.delay)
+        u = prepared[1] if prepared is not None else self.vol.fields(b, e)
+        _, j, _, st = oracle.solve_batch(self.vol.grains, self.Cf, u=u, n_threads=1)
+        assert st == oracle.OK
+        J = oracle.size_integrate(self.vol.grains.size_weight, j).astype(np.float32)
+        return J, {"gpu_ms": 0.0, "spectra": (e - b) * self.vol.grains.n_grains, "energy": {"weighted_ratio": 1.0}}
+
+    def prepare(self, b, e):
+        return (b, e), self.vol.fields(b, e)
+
+
+def _tiny_volume():
+    return W.rt_volume((8, 8, 4), corr_cells=2.0, radii_per_composition=1, nbins=32, n_lambda=64)
+
+
+def _dist_volume_worker(rank, world, port, out_dir, stop_after):
+    import torch.distributed as dist
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    vol = _tiny_volume()
+    solver = OracleChunkSolver(vol, delay=1.0 if rank == 0 else 0.0)  # rank 0: a slow device
+    res = V.run_distributed(out_dir, _cfg(), vol.n_cells, 16, solver.solve, prepare=solver.prepare,
+                            stop_after=stop_after)
+    np.save(os.path.join(out_dir, f"claimed{rank}.npy"), np.array(res["claimed"], dtype=np.int64))
+    dist.destroy_process_group()
+
+
+def test_distributed_volume_run_with_a_chunk_queue(tmp_path):
+    """Three gloo ranks of unequal speed run the volume driver with dynamic chunk claiming:
+    first an interrupted run (one chunk per rank), then a resumed one.  Every chunk is solved
+    exactly once, the slow rank solves fewer, the merged manifest is complete and the volume
+    equals a single-process run's bit for bit."""
+    import torch.multiprocessing as mp
+
+    from .test_shard import _free_port
+
+    out = str(tmp_path / "dist")
+    os.makedirs(out)
+    mp.spawn(_dist_volume_worker, args=(3, _free_port(), out, 1), nprocs=3, join=True)
+    first = [np.load(os.path.join(out, f"claimed{r}.npy")) for r in range(3)]
+    m = V.ChunkManifest(out, _cfg())
+    m.load(resume=True)
+    done_first = set(int(k) for k in m.chunks)
+    assert done_first == set(int(k) for c in first for k in c) and len(done_first) == 3
+    assert not [p for p in os.listdir(out) if p.startswith("manifest.r")]  # shards merged
+    mp.spawn(_dist_volume_worker, args=(3, _free_port(), out, None), nprocs=3, join=True)
+    second = [np.load(os.path.join(out, f"claimed{r}.npy")) for r in range(3)]
+    m.load(resume=True)
+    assert sorted(int(k) for k in m.chunks) == list(range(16))
+    # the queue hands every chunk to exactly one rank; chunks the first run finished are
+    # claimed and skipped, the others solved once
+    assert np.array_equal(np.sort(np.concatenate(second)), np.arange(16))
+    solved = [set(int(k) for k in c) - done_first for c in second]
+    assert sum(len(x) for x in solved) == 13 and set().union(*solved) | done_first == set(range(16))
+    assert len(solved[0]) < (len(solved[1]) + len(solved[2])) / 2  # the slow rank takes fewer
+    # the output equals one process's
+    ref = str(tmp_path / "single")
+    vol = _tiny_volume()
+    s = OracleChunkSolver(vol)
+    r = V.run_chunks(V.ChunkManifest(ref, _cfg()), vol.n_cells, 16, s.solve, prepare=s.prepare)
+    assert r["complete"]
+    assert np.array_equal(V.load_output(out), V.load_output(ref))
