@@ -15,6 +15,11 @@ marshals numpy arrays through ctypes.  Functions and the passages they follow:
 * ``cooling``, ``emitted_power`` -- T_{f-1,f} (Eq. cooling)
 * ``emissivity``          -- j_lambda (Eq. emission, Eq. emission-lambda)
 * ``ledger``              -- absorbed vs emitted power of the discrete model (follows from Eq. bequation)
+* ``cooling_discrete``    -- thermal-discrete downward rates T_lu (the approximation named beside Eq. adjacent;
+                             read as Eq. cooling's integrand restricted to each downward photon-energy window)
+* ``solve_full``          -- stationary P of the full rate matrix (Eq. steady-state, Eq. level-sum) by state
+                             reduction (Grassmann-Taksar-Heyman), for any downward rates
+* ``solve_batch_discrete`` -- cells x grains with thermal-discrete cooling
 * ``solve_batch``         -- all of the above over cells x grains (either heating form)
 * ``size_integrate``      -- Eq. convolution, discretised
 """
@@ -69,6 +74,17 @@ def lib():
         L.orc_size_integrate.restype = None
         L.orc_size_integrate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D]
         L.orc_max_threads.restype = ctypes.c_int
+        L.orc_emitted_power_window.restype = ctypes.c_double
+        L.orc_emitted_power_window.argtypes = [ctypes.c_int, _D, _D, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        L.orc_cooling_discrete.restype = ctypes.c_int
+        L.orc_cooling_discrete.argtypes = [ctypes.c_int, _D, _D, ctypes.c_int, _D, _D, _D]
+        L.orc_solve_full.restype = ctypes.c_int
+        L.orc_solve_full.argtypes = [ctypes.c_int, _D, _D, _D]
+        L.orc_ledger_full.restype = None
+        L.orc_ledger_full.argtypes = [ctypes.c_int, _D, _D, _D, _D, _D]
+        L.orc_solve_batch_discrete.restype = ctypes.c_int
+        L.orc_solve_batch_discrete.argtypes = [ctypes.c_int, _D, ctypes.c_int, _D, _I, _D, _D, _D, ctypes.c_int, _D,
+                                               _D, _D, _D, ctypes.c_int]
         _lib = L
     return _lib
 
@@ -232,3 +248,74 @@ def size_integrate(w, j):
 
 def max_threads():
     return lib().orc_max_threads()
+
+
+def emitted_power_window(lam, cabs, T, Emin, Emax):
+    lam, pl = _d(lam)
+    cabs, pc = _d(cabs)
+    return lib().orc_emitted_power_window(lam.size, pl, pc, float(T), float(Emin), float(Emax))
+
+
+def cooling_discrete(lam, cabs, T, E):
+    """Thermal-discrete downward rates D[l, u] = T_lu (l < u), one grain."""
+    lam, pl = _d(lam)
+    cabs, pc = _d(cabs)
+    T, pt = _d(T)
+    E, pe = _d(E)
+    D = np.zeros((E.size, E.size))
+    st = lib().orc_cooling_discrete(lam.size, pl, pc, E.size, pt, pe, D.ctypes.data_as(_D))
+    if st != OK:
+        raise RuntimeError(f"orc_cooling_discrete status {st}")
+    return D
+
+
+def solve_full(A, D, return_status=False):
+    """Stationary P of the full rate matrix: upward A[u, l] = T_ul, downward D[l, u] = T_lu."""
+    A, pa = _d(A)
+    D, pd = _d(D)
+    nb = A.shape[0]
+    P = np.zeros(nb)
+    st = lib().orc_solve_full(nb, pa, pd, P.ctypes.data_as(_D))
+    if return_status:
+        return P, st
+    if st != OK:
+        raise RuntimeError(f"orc_solve_full status {st}")
+    return P
+
+
+def ledger_full(A, D, E, P):
+    A, pa = _d(A)
+    D, pd = _d(D)
+    E, pe = _d(E)
+    P, pp = _d(P)
+    out = np.zeros(2)
+    lib().orc_ledger_full(E.size, pa, pd, pe, pp, out.ctypes.data_as(_D))
+    return out
+
+
+def grain_cooling_discrete(wl):
+    """Thermal-discrete rates of every grain of a workload: a list of nb_g x nb_g arrays."""
+    return [cooling_discrete(wl.lam, wl.cabs[g], wl.T[wl.grain_slice(g)], wl.E[wl.grain_slice(g)])
+            for g in range(wl.n_grains)]
+
+
+def solve_batch_discrete(wl, Dg=None, want_j=True, want_ledger=False, n_threads=0, u=None):
+    """As solve_batch with thermal-discrete cooling (Dg: grain_cooling_discrete(wl))."""
+    if Dg is None:
+        Dg = grain_cooling_discrete(wl)
+    u = wl.u if u is None else u
+    lam, pl = _d(wl.lam)
+    cabs, pc = _d(wl.cabs)
+    off = np.ascontiguousarray(wl.bin_off, dtype=np.int32)
+    T, pt = _d(wl.T)
+    E, pe = _d(wl.E)
+    Dall, pd = _d(np.concatenate([np.ascontiguousarray(d, dtype=np.float64).ravel() for d in Dg]))
+    u, pu = _d(u)
+    cells = u.shape[0]
+    G, N = wl.n_grains, wl.n_lambda
+    P = np.zeros((cells, wl.total_bins))
+    j, pj = _dnull(np.zeros((cells, G, N)) if want_j else None)
+    led, pld = _dnull(np.zeros((cells, G, 2)) if want_ledger else None)
+    st = lib().orc_solve_batch_discrete(N, pl, G, pc, off.ctypes.data_as(_I), pt, pe, pd, cells, pu,
+                                        P.ctypes.data_as(_D), pj, pld, int(n_threads))
+    return P, j, led, st

@@ -11,6 +11,8 @@
  *   Omega(lambda) = W(lambda) sigma(lambda) with log-log interpolation (Eq. interpolation),
  *   heating elements T_ul, u > l (Eq. heating), in the wavelength-integral form,
  *   thermal-continuous cooling T_{f-1,f} (Eq. adjacent, Eq. cooling),
+ *   thermal-discrete cooling T_lu, l < u (the approximation named beside Eq. adjacent)
+ *   and the stationary solve of the full rate matrix (Eq. steady-state, Eq. level-sum),
  *   B_fj suffix sums (Eq. bmatrix, via the recurrence Eq. brecurrence),
  *   X recursion and renormalisation (Eq. xf, Eq. renormalization),
  *   emissivity (Eq. emission, Eq. emission-lambda),
@@ -307,23 +309,25 @@ static double adapt(const cool_ctx* c, double a, double b, double whole, double 
     return adapt(c, a, m, left, 0.5 * tol, depth + 1) + adapt(c, m, b, right, 0.5 * tol, depth + 1);
 }
 
-/* int_0^xmax C(lambda(x)) x^3/(e^x-1) dx, split at the grid nodes. */
-static double cool_x_integral(const cool_ctx* c, double xmax)
+/* int_xmin^xmax C(lambda(x)) x^3/(e^x-1) dx, split at the grid nodes. */
+static double cool_x_window(const cool_ctx* c, double xmin, double xmax)
 {
     const int N = c->N;
     if (xmax > 800.0) xmax = 800.0;     /* integrand < 1e-340 relative beyond */
-    /* breakpoints: x_n = hc/(lam_n k T) (descending in n), plus geometric
-     * panels towards x -> 0 (lambda -> infinity).                            */
+    if (xmin < 0.0) xmin = 0.0;
+    if (!(xmax > xmin)) return 0.0;
+    /* breakpoints: x_n = hc/(lam_n k T) (descending in n) inside the window, plus
+     * geometric panels towards x -> 0 (lambda -> infinity) below the grid's end. */
     int cap = N + 200;
     double* pts = (double*)malloc(sizeof(double) * (size_t)cap);
     int np = 0;
     double xlast = hc() / (c->lam[N - 1] * K_B * c->T);
     double g = (xlast < xmax ? xlast : xmax);
-    for (int k = 0; k < 120 && np < cap - N - 2; ++k) { pts[np++] = g; g *= 0.5; }
-    pts[np++] = 0.0;
+    for (int k = 0; k < 120 && np < cap - N - 3 && g > xmin; ++k) { pts[np++] = g; g *= 0.5; }
+    pts[np++] = xmin;
     for (int n = N - 1; n >= 0; --n) {
         double xn = hc() / (c->lam[n] * K_B * c->T);
-        if (xn > xlast && xn < xmax) pts[np++] = xn;
+        if (xn > xlast && xn < xmax && xn > xmin) pts[np++] = xn;
     }
     pts[np++] = xmax;
     /* sort ascending (insertion sort, small) */
@@ -347,6 +351,8 @@ static double cool_x_integral(const cool_ctx* c, double xmax)
     return total;
 }
 
+static double cool_x_integral(const cool_ctx* c, double xmax) { return cool_x_window(c, 0.0, xmax); }
+
 /* Emitted power P_emit(T; Emax) in erg/s (Eq. cooling numerator). */
 double orc_emitted_power(int N, const double* lam, const double* cabs, double T, double Emax)
 {
@@ -354,6 +360,15 @@ double orc_emitted_power(int N, const double* lam, const double* cabs, double T,
     cool_ctx c = {N, lam, cabs, T};
     double pref = 4.0 * M_PI * 2.0 * pow(K_B * T, 4.0) / (pow(H_PL, 3.0) * C_LI * C_LI);
     return pref * cool_x_integral(&c, Emax / (K_B * T));
+}
+
+/* The same power restricted to photon energies in [Emin, Emax]. */
+double orc_emitted_power_window(int N, const double* lam, const double* cabs, double T, double Emin, double Emax)
+{
+    gl_init();
+    cool_ctx c = {N, lam, cabs, T};
+    double pref = 4.0 * M_PI * 2.0 * pow(K_B * T, 4.0) / (pow(H_PL, 3.0) * C_LI * C_LI);
+    return pref * cool_x_window(&c, Emin / (K_B * T), Emax / (K_B * T));
 }
 
 /* Cf[f] = T_{f-1,f} for f = 1..M; Cf[0] = 0. */
@@ -368,6 +383,91 @@ int orc_cooling(int N, const double* lam, const double* cabs, int nb, const doub
     for (int f = 1; f < nb; ++f)
         Cf[f] = orc_emitted_power(N, lam, cabs, T[f], E[f]) / (E[f] - E[f - 1]);
     return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Thermal-discrete cooling (the approximation the paper names next to Eq. adjacent; its
+ * source's formulas are not in the paper, so this is the reading): a grain in bin u emits
+ * as a body at T_u, with the power per unit photon energy of Eq. cooling's integrand, and a
+ * photon of energy e leaves it in the bin l with Elo_l <= E_u - e < Ehi_l.  The rate to l is
+ * the power emitted in that window of photon energies divided by the transition's energy:
+ *   D[l][u] = P_emit(T_u; window of l) / (E_u - E_l),   window of l = [E_u - Ehi_l, E_u - Elo_l]
+ * for l < u - 1, and for l = u - 1 the window [0, E_u - Elo_{u-1}]: photons too soft to
+ * leave bin u are carried by the adjacent transition, as the heating's intra-bin term is.
+ * The windows tile [0, E_u], so sum_l D[l][u] (E_u - E_l) = P_emit(T_u; E_u), the power the
+ * thermal-continuous rate T_{u-1,u} carries (Eq. cooling); with all power in the adjacent
+ * window the two treatments coincide.  D is row-major nb x nb, D[l*nb + u], zero for l >= u. */
+int orc_cooling_discrete(int N, const double* lam, const double* cabs, int nb, const double* T, const double* E,
+                         double* D)
+{
+    if (N < 2 || nb < 2) return ORC_EINVAL;
+    gl_init();
+    for (size_t k = 0; k < (size_t)nb * nb; ++k) D[k] = 0.0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int u = 1; u < nb; ++u) {
+        for (int l = 0; l < u; ++l) {
+            double elo_l = l == 0 ? 0.0 : 0.5 * (E[l - 1] + E[l]);
+            double ehi_l = 0.5 * (E[l] + E[l + 1]);  /* l < u <= nb - 1, so E[l+1] exists */
+            double emin = l == u - 1 ? 0.0 : E[u] - ehi_l;
+            double emax = E[u] - elo_l;
+            D[(size_t)l * nb + u] = orc_emitted_power_window(N, lam, cabs, T[u], emin, emax) / (E[u] - E[l]);
+        }
+    }
+    return ORC_OK;
+}
+
+/* Stationary distribution of the full rate matrix (Eq. steady-state with Eq. level-sum):
+ * upward rates A[u*nb + l] = T_ul (u > l), downward rates D[l*nb + u] = T_lu (l < u).  By
+ * state reduction (Grassmann, Taksar and Heyman): states n = nb-1 .. 1 are removed in turn;
+ * the rates of n are redistributed over the remaining states, q_ij += q_in q_nj / s_n with
+ * s_n = sum_{j<n} q_nj, every term a sum or product of non-negative numbers, so that small
+ * probabilities keep their relative accuracy.  Then X_0 = 1, X_n = sum_{i<n} X_i q_in / s_n,
+ * rescaled by 2^-800 whenever X_n > 2^800 (exact), and P = X / sum X.  A state with no
+ * downward rate and non-zero inflow has no steady state (ORC_ENUMERIC).  O(nb^3).          */
+int orc_solve_full(int nb, const double* A, const double* D, double* P)
+{
+    size_t nn = (size_t)nb * nb;
+    double* q = (double*)malloc(sizeof(double) * nn);  /* q[i*nb + j]: rate from i to j */
+    double* s = (double*)malloc(sizeof(double) * (size_t)nb);
+    if (!q || !s) { free(q); free(s); return ORC_ENOMEM; }
+    for (int i = 0; i < nb; ++i)
+        for (int j = 0; j < nb; ++j)
+            q[(size_t)i * nb + j] = i == j ? 0.0 : (j > i ? A[(size_t)j * nb + i] : D[(size_t)j * nb + i]);
+    int st = ORC_OK;
+    for (int n = nb - 1; n >= 1; --n) {
+        double sn = 0.0;
+        for (int j = 0; j < n; ++j) sn += q[(size_t)n * nb + j];
+        s[n] = sn;
+        if (sn == 0.0) continue;  /* nothing leaves n downward: X_n is 0 or undefined (below) */
+        for (int i = 0; i < n; ++i) {
+            double qin = q[(size_t)i * nb + n];
+            if (qin == 0.0) continue;
+            for (int j = 0; j < n; ++j)
+                if (j != i) q[(size_t)i * nb + j] += qin * q[(size_t)n * nb + j] / sn;
+        }
+    }
+    double total = 1.0;
+    P[0] = 1.0;
+    for (int n = 1; n < nb; ++n) {
+        double in = 0.0;
+        for (int i = 0; i < n; ++i) in += P[i] * q[(size_t)i * nb + n];
+        if (s[n] == 0.0) {
+            if (in != 0.0) st = ORC_ENUMERIC;
+            P[n] = 0.0;
+            continue;
+        }
+        P[n] = in / s[n];
+        total += P[n];
+        if (P[n] > 0x1p800) {
+            for (int i = 0; i <= n; ++i) P[i] *= 0x1p-800;
+            total *= 0x1p-800;
+        }
+    }
+    for (int n = 0; n < nb; ++n) P[n] /= total;
+    free(q); free(s);
+    return st;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -397,6 +497,79 @@ void orc_ledger(int nb, const double* A, const double* E, const double* Cf, cons
     for (int f = 1; f < nb; ++f) em += P[f] * Cf[f] * (E[f] - E[f - 1]);
     out[0] = ab;
     out[1] = em;
+}
+
+/* The same ledger with thermal-discrete cooling: out[1] = sum_u P_u sum_{l<u} D_lu (E_u - E_l). */
+void orc_ledger_full(int nb, const double* A, const double* D, const double* E, const double* P, double* out)
+{
+    double ab = 0.0, em = 0.0;
+    for (int l = 0; l < nb; ++l)
+        for (int u = l + 1; u < nb; ++u) {
+            ab += P[l] * A[(size_t)u * nb + l] * (E[u] - E[l]);
+            em += P[u] * D[(size_t)l * nb + u] * (E[u] - E[l]);
+        }
+    out[0] = ab;
+    out[1] = em;
+}
+
+/* One (cell, grain) spectrum with thermal-discrete cooling: heating matrix (integral form),
+ * the full stationary solve with the grain's downward rates D, emissivity and ledger. */
+int orc_solve_spectrum_discrete(int N, const double* lam, const double* cabs, int nb, const double* T,
+                                const double* E, const double* D, const double* u, double* P, double* j,
+                                double* ledger)
+{
+    size_t nn = (size_t)nb * (size_t)nb;
+    double* om = (double*)malloc(sizeof(double) * (size_t)N);
+    double* A = (double*)malloc(sizeof(double) * nn);
+    if (!om || !A) { free(om); free(A); return ORC_ENOMEM; }
+    for (int n = 0; n < N; ++n) om[n] = u[n] * cabs[n];
+    int st = orc_heating_matrix(N, lam, om, nb, E, A);
+    if (st == ORC_OK) {
+        st = orc_solve_full(nb, A, D, P);
+        if (j) orc_emissivity(N, lam, cabs, nb, T, E, P, j);
+        if (ledger) orc_ledger_full(nb, A, D, E, P, ledger);
+    }
+    free(om); free(A);
+    return st;
+}
+
+/* Batch of thermal-discrete solves: as orc_solve_batch, with the grains' downward rates
+ * D_g (nb_g x nb_g each, back to back in grain order) in Dall. */
+int orc_solve_batch_discrete(int N, const double* lam, int G, const double* cabs, const int* bin_off,
+                             const double* T, const double* E, const double* Dall, int cells, const double* u,
+                             double* P, double* j, double* ledger, int n_threads)
+{
+    int status = ORC_OK;
+    const long total = (long)cells * G;
+    const int nbt = bin_off[G];
+    size_t* doff = (size_t*)malloc(sizeof(size_t) * (size_t)(G + 1));
+    if (!doff) return ORC_ENOMEM;
+    doff[0] = 0;
+    for (int g = 0; g < G; ++g) {
+        size_t nb = (size_t)(bin_off[g + 1] - bin_off[g]);
+        doff[g + 1] = doff[g] + nb * nb;
+    }
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (long s = 0; s < total; ++s) {
+        int c = (int)(s / G), g = (int)(s % G);
+        int off = bin_off[g], nb = bin_off[g + 1] - bin_off[g];
+        int st = orc_solve_spectrum_discrete(N, lam, cabs + (size_t)g * N, nb, T + off, E + off, Dall + doff[g],
+                                             u + (size_t)c * N, P + (size_t)c * nbt + off,
+                                             j ? j + ((size_t)c * G + g) * N : NULL,
+                                             ledger ? ledger + ((size_t)c * G + g) * 2 : NULL);
+        if (st != ORC_OK) {
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+            { if (status == ORC_OK) status = st; }
+        }
+    }
+    free(doff);
+    (void)n_threads;
+    return status;
 }
 
 /* One (cell, grain) spectrum end to end.  P[nb], j[N] (may be NULL),
