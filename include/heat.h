@@ -70,6 +70,23 @@ enum {
                                   down each column (Eq. brecurrence).  Exact build only          */
 };
 
+/* cooling transitions (Sec. 2.1: the thermal approximations beside Eq. adjacent) */
+enum {
+    HEAT_COOLING_CONTINUOUS = 0, /* thermal-continuous: only the adjacent downward transition, rate
+                                    Eq. cooling; P by the Guhathakurta-Draine recursion (Eq. xf)   */
+    HEAT_COOLING_DISCRETE = 1    /* thermal-discrete: a grain in bin u emits as a body at T_u and a
+                                    photon of energy e takes it to the bin l holding E_u - e; the
+                                    rate to l is the power of Eq. cooling's integrand in that photon-
+                                    energy window divided by E_u - E_l (photons too soft to leave
+                                    bin u go with the adjacent transition), so that the rates carry
+                                    Eq. cooling's power.  P by the stationary solve of the full rate
+                                    matrix (Eq. steady-state, Eq. level-sum; state reduction,
+                                    O(M^3) per spectrum: meant for few cells).  Needs the exact
+                                    build (HEAT_BUILD_F64) and the integral heating form; the
+                                    downward rates are computed on the first such solve after
+                                    heat_set_grains                                              */
+};
+
 /* emissivity contraction (Eq. emission) */
 enum {
     HEAT_EMIS_NONE = -1,  /* no emissivity */
@@ -147,6 +164,7 @@ typedef struct heat_opts {
     int emis_n_tile;    /* wavelength columns of a tensor-core emissivity tile: 256 or 128 (tiles are
                            128 cells x this; the operand ring holds 4 or 6 k-stages); 0 =
                            heat_autotune's choice, else 256.  Results do not depend on it        */
+    int cooling;        /* HEAT_COOLING_CONTINUOUS (default) or HEAT_COOLING_DISCRETE          */
 } heat_opts;
 
 /* kernel classes reported by heat_get_timing */
@@ -286,6 +304,12 @@ const char* heat_last_error(const heat_ctx* ctx);
 /* Copy the cooling rates T_{f-1,f} (Eq. cooling) of all grains to host Cf[bin_offset[n_grains]]
  * (Cf[bin_offset[g]] = 0 for every grain).  Errors: HEAT_ESTATE, HEAT_ECUDA. */
 heat_status heat_get_cooling(heat_ctx* ctx, double* Cf_host);
+
+/* Copy the thermal-discrete downward rates (HEAT_COOLING_DISCRETE) to host D_host: grain by
+ * grain an nb_g x nb_g block, row l, column u, holding T_lu for l < u (0 elsewhere), blocks
+ * back to back (sum_g nb_g^2 doubles).  Computes them first if no discrete solve has.
+ * Errors: HEAT_ESTATE (grains not set), HEAT_ENOMEM, HEAT_ECUDA. */
+heat_status heat_get_cooling_discrete(heat_ctx* ctx, double* D_host);
 
 /* Number of band elements (f, j), j < f, that a photon on the grid can reach, summed over
  * grains: the FP64 FMAs of one spectrum set's recursion.  Errors: HEAT_ESTATE. */

@@ -550,8 +550,8 @@ int orc_solve_batch_discrete(int N, const double* lam, int G, const double* cabs
         doff[g + 1] = doff[g] + nb * nb;
     }
 #ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
-#pragma omp parallel for schedule(dynamic, 1)
+    const int nt = n_threads > 0 ? n_threads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
 #endif
     for (long s = 0; s < total; ++s) {
         int c = (int)(s / G), g = (int)(s % G);
@@ -607,8 +607,9 @@ int orc_solve_batch(int N, const double* lam, int G, const double* cabs, const i
     const long total = (long)cells * G;
     const int nbt = bin_off[G];
 #ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
-#pragma omp parallel for schedule(dynamic, 1)
+    /* a thread count for this call only (the process-wide setting is left as it was) */
+    const int nt = n_threads > 0 ? n_threads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
 #endif
     for (long s = 0; s < total; ++s) {
         int c = (int)(s / G), g = (int)(s % G);

@@ -284,6 +284,7 @@ void heat_default_opts(heat_opts* o) {
     o->fused_build = 0;
     o->recur_blocks_per_sm = 0;
     o->emis_n_tile = 0;
+    o->cooling = HEAT_COOLING_CONTINUOUS;
 }
 
 heat_status heat_create_grid(heat_ctx** out, int device, int n_lambda, const double* lambda_cm) {
@@ -320,6 +321,11 @@ heat_status heat_create_grid(heat_ctx** out, int device, int n_lambda, const dou
     double glx[kGLPoints], glw[kGLPoints];
     gauss_legendre(kGLPoints, glx, glw);
     if (set_gauss_legendre(glx, glw) != cudaSuccess) return cleanup(HEAT_ECUDA);
+    {
+        std::vector<double> gl(glx, glx + kGLPoints);
+        gl.insert(gl.end(), glw, glw + kGLPoints);
+        if (upload(ctx->d_gl, gl) != cudaSuccess) return cleanup(HEAT_ENOMEM);
+    }
     *out = ctx;
     return HEAT_OK;
 }
@@ -365,6 +371,7 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
     ctx->tail_NG = -1;
     ctx->tuned_streams = ctx->tuned_chunk = 0;
     ctx->row_weight = 30;
+    ctx->td_built = false;
     for (auto* modes : {ctx->tc, ctx->tc_si})
         for (int m = 0; m < 5; ++m) {
             modes[m].built = false;
@@ -635,6 +642,29 @@ heat_status heat_set_fields(heat_ctx* ctx, int n_cells, const void* u, int dtype
     return HEAT_OK;
 }
 
+// Thermal-discrete downward rates of every grain (once per grain set, on first use).
+static heat_status ensure_discrete(heat_ctx* ctx, cudaStream_t st) {
+    if (ctx->td_built) return HEAT_OK;
+    const int G = ctx->G;
+    std::vector<long long> doff(G + 1, 0), woff(G + 1, 0);
+    for (int g = 0; g < G; ++g) {
+        const long long nb = ctx->bin_off[g + 1] - ctx->bin_off[g];
+        doff[g + 1] = doff[g] + nb * nb;
+        woff[g + 1] = woff[g] + nb * (nb - 1) / 2;
+    }
+    if (ctx->d_Dtd.ensure(sizeof(double) * (size_t)std::max(1LL, doff[G])) || upload(ctx->d_Dtd_off, doff) ||
+        upload(ctx->d_Dtd_woff, woff))
+        return ctx->fail(HEAT_ENOMEM, "heat_solve: allocation of thermal-discrete rates failed");
+    CKR(cudaMemsetAsync(ctx->d_Dtd.p, 0, sizeof(double) * (size_t)doff[G], st));
+    const double* gl = ctx->d_gl.as<double>();
+    CKR(launch_cooling_window(ctx->N, ctx->d_lam.as<double>(), ctx->d_cabs.as<double>(), ctx->d_bin_off.as<int>(), G,
+                              ctx->d_T.as<double>(), ctx->d_E.as<double>(), ctx->d_Dtd_woff.as<long long>(), woff[G],
+                              ctx->d_Dtd_off.as<long long>(), ctx->d_Dtd.as<double>(), gl, gl + kGLPoints, st));
+    CKR(cudaStreamSynchronize(st));
+    ctx->td_built = true;
+    return HEAT_OK;
+}
+
 // Smallest default chunk worth pipelining host copies against.
 constexpr int kHostIoMinChunk = 1024;
 
@@ -696,6 +726,11 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
         return ctx->fail(HEAT_EINVAL, "heat_solve: recur_blocks_per_sm must be in 0..4");
     if (o.emis_n_tile != 0 && o.emis_n_tile != 128 && o.emis_n_tile != 256)
         return ctx->fail(HEAT_EINVAL, "heat_solve: emis_n_tile must be 0, 128 or 256");
+    if (o.cooling != HEAT_COOLING_CONTINUOUS && o.cooling != HEAT_COOLING_DISCRETE)
+        return ctx->fail(HEAT_EINVAL, "heat_solve: bad cooling option");
+    const bool discrete = o.cooling == HEAT_COOLING_DISCRETE;
+    if (discrete && (o.build != HEAT_BUILD_F64 || o.heating != HEAT_HEATING_INTEGRAL))
+        return ctx->fail(HEAT_EINVAL, "heat_solve: thermal-discrete cooling needs the exact build and integral heating");
     const int emis_nt = o.emis_n_tile ? o.emis_n_tile : (ctx->tuned_emis_nt ? ctx->tuned_emis_nt : 256);
     int c_begin = o.cell_begin, count = o.cell_count > 0 ? o.cell_count : ctx->n_cells - o.cell_begin;
     if (c_begin < 0 || count < 0 || c_begin + count > ctx->n_cells)
@@ -764,9 +799,17 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
         if ((hs = prepare_tc_rows(ctx, o.emis, si, Cc)) != HEAT_OK) return hs;
     }
 
+    // thermal-discrete: spectra solved per launch, their rate matrices within about 1 GB
+    long long td_batch = 0;
+    if (discrete) {
+        heat_status hs = ensure_discrete(ctx, st);
+        if (hs != HEAT_OK) return hs;
+        const long long per = (long long)ctx->max_bins * ctx->max_bins * (long long)sizeof(double);
+        td_batch = std::max(1LL, std::min((long long)span * G, (1LL << 30) / per));
+    }
     // the recursion's epilogue packs the tensor-core operand (per-grain output, lane-per-cell
     // kernels); P then goes to memory only where the caller asked for it
-    const bool pack_in_recur = tc && !si && !fused && count > kSmallCells;
+    const bool pack_in_recur = tc && !si && !fused && count > kSmallCells && !discrete;
     // scratch of every slot in use
     bool internal_P = (P_out == nullptr) || o.host_io;
     const bool async_io = o.host_io == 2;
@@ -777,7 +820,8 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
         if (build == 0) {
             ok &= !sl.ua64.ensure(sizeof(double) * (size_t)N * Cc);
             ok &= !sl.su64.ensure(sizeof(double) * (size_t)N * Cc);
-            ok &= !sl.Bb64.ensure(sizeof(double) * (size_t)NG * std::max(1LL, ctx->band_per_cell) * 32);
+            if (!discrete)  // the thermal-discrete solve builds its own rate matrices
+                ok &= !sl.Bb64.ensure(sizeof(double) * (size_t)NG * std::max(1LL, ctx->band_per_cell) * 32);
         } else {
             ok &= !sl.ua32.ensure(sizeof(float2) * (size_t)N * Cc);  // (u, slope) pairs
             if (fused)
@@ -786,6 +830,7 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
                 ok &= !sl.Bb32.ensure(sizeof(float) * (size_t)NG * std::max(1LL, ctx->band_per_cell) * 32);
         }
         ok &= !sl.xs.ensure(sizeof(double) * (size_t)NG * nbt * 32);
+        if (discrete) ok &= !sl.tdq.ensure(sizeof(double) * (size_t)td_batch * ctx->max_bins * ctx->max_bins);
         ok &= !sl.ep.ensure(sizeof(unsigned short) * (size_t)NG * nbt * 32);
         ok &= !sl.pabs.ensure(sizeof(double) * (size_t)Cc * G);
         ok &= !sl.work.ensure(sizeof(int) * 2);
@@ -834,6 +879,7 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
     gd.invC = ctx->d_invC.as<double>();
     gd.invdE = ctx->d_invdE.as<double>();
     gd.cde = ctx->d_cde.as<double>();
+    gd.E = ctx->d_E.as<double>();
     gd.rowptr = ctx->d_rowptr.as<int>();
     gd.wmax = ctx->d_wmax.as<int>();
     gd.band_total = ctx->band_per_cell;
@@ -904,7 +950,11 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
         ch.blocks_per_sm = o.recur_blocks_per_sm > 0 ? o.recur_blocks_per_sm : ctx->tuned_recur_bps;
         CKR(cudaMemsetAsync(ch.work, 0, sizeof(int) * 2, cs));
         TIMED(HEAT_T_FIELD, launch_field(gd, ctx->u_dev, ctx->u_dtype, cell0, ch, build, cs));
-        if (fused) {
+        if (discrete) {  // field tables, then the full stationary solve (timed as the recursion)
+            TIMED(HEAT_T_RECUR, launch_discrete_solve(gd, ch, ctx->d_Dtd.as<double>(), ctx->d_Dtd_off.as<long long>(),
+                                                      sl.tdq.as<double>(), (long long)ctx->max_bins * ctx->max_bins,
+                                                      td_batch, cs));
+        } else if (fused) {
             ch.phs = sl.phs.as<float>();
             TIMED(HEAT_T_RECUR, launch_fused(gd, ch, cs));
         } else {
@@ -1222,6 +1272,21 @@ heat_status heat_get_cooling(heat_ctx* ctx, double* Cf) {
     return HEAT_OK;
 }
 
+heat_status heat_get_cooling_discrete(heat_ctx* ctx, double* D) {
+    if (!ctx || !D) return HEAT_EINVAL;
+    if (ctx->G == 0) return ctx->fail(HEAT_ESTATE, "heat_get_cooling_discrete: grains not set");
+    CKR(cudaSetDevice(ctx->device));
+    heat_status h = ensure_discrete(ctx, 0);
+    if (h != HEAT_OK) return h;
+    size_t n = 0;
+    for (int g = 0; g < ctx->G; ++g) {
+        const size_t nb = (size_t)(ctx->bin_off[g + 1] - ctx->bin_off[g]);
+        n += nb * nb;
+    }
+    CKR(cudaMemcpy(D, ctx->d_Dtd.p, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    return HEAT_OK;
+}
+
 heat_status heat_get_timing(heat_ctx* ctx, double* ms, long long* launches, int reset) {
     if (!ctx) return HEAT_EINVAL;
     CKR(cudaSetDevice(ctx->device));
@@ -1262,12 +1327,12 @@ void heat_destroy(heat_ctx* ctx) {
                       &ctx->d_T, &ctx->d_E, &ctx->d_Cf, &ctx->d_invC, &ctx->d_invdE, &ctx->d_invdE32, &ctx->d_Cact,
                       &ctx->d_sC, &ctx->d_ca32, &ctx->d_ce32, &ctx->d_sC32, &ctx->d_rowptr, &ctx->d_wmax, &ctx->d_seg_ptr,
                       &ctx->d_pat64, &ctx->d_pat32, &ctx->d_soft, &ctx->d_soft_off, &ctx->d_K, &ctx->d_Kw, &ctx->d_w,
-                      &ctx->d_koff_all, &ctx->d_cde, &ctx->d_pent, &ctx->d_pcol, &ctx->d_kexp, &ctx->d_rent, &ctx->d_u_own, &ctx->s_tasks, &ctx->s_tasks_tail, &ctx->d_status};
+                      &ctx->d_koff_all, &ctx->d_cde, &ctx->d_pent, &ctx->d_pcol, &ctx->d_kexp, &ctx->d_rent, &ctx->d_gl, &ctx->d_Dtd, &ctx->d_Dtd_off, &ctx->d_Dtd_woff, &ctx->d_u_own, &ctx->s_tasks, &ctx->s_tasks_tail, &ctx->d_status};
     for (DevBuf* b : bufs) b->release();
     for (auto& sl : ctx->slots) {
         DevBuf* sb[] = {&sl.ua64, &sl.su64, &sl.ua32, &sl.Bb64, &sl.Bb32, &sl.xs, &sl.ep,   &sl.pabs,
                         &sl.P,    &sl.j,    &sl.led,  &sl.A,    &sl.rowscale, &sl.work, &sl.P_alt, &sl.j_alt,
-                        &sl.led_alt, &sl.phs};
+                        &sl.led_alt, &sl.phs, &sl.tdq};
         for (DevBuf* b : sb) b->release();
         if (sl.stream) cudaStreamDestroy(sl.stream);
         if (sl.done) cudaEventDestroy(sl.done);
@@ -1320,6 +1385,7 @@ __attribute__((visibility("hidden"))) heat_status heat_internal_grain_view(heat_
     gd->invC = ctx->d_invC.as<double>();
     gd->invdE = ctx->d_invdE.as<double>();
     gd->cde = ctx->d_cde.as<double>();
+    gd->E = ctx->d_E.as<double>();
     gd->rowptr = ctx->d_rowptr.as<int>();
     gd->wmax = ctx->d_wmax.as<int>();
     gd->band_total = ctx->band_per_cell;

@@ -39,6 +39,7 @@ struct GrainDev {
     const float* invdE32;   // [nbt]
     const double* invC;     // [nbt] 1/T_{f-1,f} (0 where the cooling rate is 0 and for f = 0)
     const double* cde;      // [nbt] T_{f-1,f} (E_f - E_{f-1}) (0 for f = 0): emitted power of bin f
+    const double* E;        // [nbt] bin enthalpies
     const double* invdE;    // [nbt] 1/(E_{j+1}-E_j) (0 for the last bin)
     const int* rowptr;      // [nbt + G] per grain, rows f = 0..M: band elements of row f at
                             //   rowptr[off_g + g + f] .. rowptr[off_g + g + f + 1] (global indices)
@@ -113,6 +114,18 @@ cudaError_t launch_recur(const GrainDev& g, const ChunkDev& ch, int build, cudaS
 // ch.work and ch.phs sized for fused_warps() warps.
 int fused_warps(int n_tasks);  // resident warps of the persistent launch for n_tasks tasks
 cudaError_t launch_fused(const GrainDev& g, const ChunkDev& ch, cudaStream_t st);
+
+// ---- thermal-discrete cooling (k_discrete.cu)
+// Downward rates of every grain, D_g [nb_g][nb_g] (row l, column u) at D + doff[g]; windows
+// of grain g numbered from woff[g] (u(u-1)/2 + l); glx/glw: Gauss-Legendre nodes, weights.
+cudaError_t launch_cooling_window(int N, const double* lam, const double* cabs, const int* bin_off, int G,
+                                  const double* T, const double* E, const long long* woff, long long n_windows,
+                                  const long long* doff, double* D, const double* glx, const double* glw,
+                                  cudaStream_t st);
+// P (and the ledger) of the chunk's cells x grains by the full stationary solve, `batch`
+// spectra at a time, each with an nb x nb rate matrix at q + k * qstride.
+cudaError_t launch_discrete_solve(const GrainDev& g, const ChunkDev& ch, const double* D, const long long* doff,
+                                  double* q, long long qstride, long long batch, cudaStream_t st);
 
 // ---- emissivity (k_emis.cu)
 // C[z][m][n] = sum_{k in [koff[z], koff[z+1])} A[m][k] B[k][n] for z < nz, m < M, n < N;

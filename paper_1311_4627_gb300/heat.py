@@ -22,6 +22,7 @@ HEAT_OK, HEAT_EINVAL, HEAT_ENOMEM, HEAT_ECUDA, HEAT_ENUMERIC, HEAT_ETIMEOUT, HEA
 HEAT_F64, HEAT_F32 = 0, 1
 HEAT_BUILD_F64, HEAT_BUILD_F32 = 0, 1
 HEAT_HEATING_INTEGRAL, HEAT_HEATING_POINT = 0, 1
+HEAT_COOLING_CONTINUOUS, HEAT_COOLING_DISCRETE = 0, 1
 HEAT_EMIS_NONE, HEAT_EMIS_F64, HEAT_EMIS_BF16X3, HEAT_EMIS_TF32X3, HEAT_EMIS_BF16, HEAT_EMIS_TF32 = -1, 0, 1, 2, 3, 4
 EMIS_NAMES = {HEAT_EMIS_F64: "f64", HEAT_EMIS_BF16X3: "bf16x3", HEAT_EMIS_TF32X3: "tf32x3", HEAT_EMIS_BF16: "bf16",
               HEAT_EMIS_TF32: "tf32"}
@@ -44,7 +45,8 @@ class heat_opts(ctypes.Structure):
                 ("chunk_cells", ctypes.c_int), ("host_io", ctypes.c_int), ("timing", ctypes.c_int),
                 ("ledger_out", ctypes.c_void_p), ("streams", ctypes.c_int), ("heating", ctypes.c_int),
                 ("prune_eps", ctypes.c_double), ("fused_build", ctypes.c_int),
-                ("recur_blocks_per_sm", ctypes.c_int), ("emis_n_tile", ctypes.c_int)]
+                ("recur_blocks_per_sm", ctypes.c_int), ("emis_n_tile", ctypes.c_int),
+                ("cooling", ctypes.c_int)]
 
 
 class heat_tuning(ctypes.Structure):
@@ -99,6 +101,8 @@ def lib():
                                     ctypes.POINTER(ctypes.c_int)]
         L.heat_get_timing.restype = ctypes.c_int
         L.heat_get_timing.argtypes = [_vp, _vp, _vp, ctypes.c_int]
+        L.heat_get_cooling_discrete.restype = ctypes.c_int
+        L.heat_get_cooling_discrete.argtypes = [_vp, _vp]
         L.heat_get_tuning.restype = ctypes.c_int
         L.heat_get_tuning.argtypes = [_vp, ctypes.POINTER(heat_tuning)]
         L.heat_set_wait_limit.restype = ctypes.c_int
@@ -182,6 +186,20 @@ def heat_set_grains(ctx, radius_cm, c_abs_cm2, bin_offset, T_bins_K, H_bins_erg,
     st = lib().heat_set_grains(ctx, r.size, r.ctypes.data, c.ctypes.data, o.ctypes.data, t.ctypes.data,
                                e.ctypes.data, None if w is None else w.ctypes.data)
     _check(ctx, st)
+
+
+def heat_get_cooling_discrete(ctx, bins) -> list:
+    """The thermal-discrete downward rates, one nb x nb array (row l, column u) per grain;
+    bins: the bins of each grain."""
+    n = int(sum(int(b) * int(b) for b in bins))
+    D = np.zeros(n)
+    _check(ctx, lib().heat_get_cooling_discrete(ctx, D.ctypes.data))
+    out, k = [], 0
+    for b in bins:
+        b = int(b)
+        out.append(D[k:k + b * b].reshape(b, b))
+        k += b * b
+    return out
 
 
 def heat_get_tuning(ctx) -> dict:
