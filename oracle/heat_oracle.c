@@ -397,6 +397,49 @@ int orc_cooling(int N, const double* lam, const double* cabs, int nb, const doub
  * The windows tile [0, E_u], so sum_l D[l][u] (E_u - E_l) = P_emit(T_u; E_u), the power the
  * thermal-continuous rate T_{u-1,u} carries (Eq. cooling); with all power in the adjacent
  * window the two treatments coincide.  D is row-major nb x nb, D[l*nb + u], zero for l >= u. */
+/* Power of Eq. cooling's integrand at T over a narrow window of photon energies written in
+ * the grain's energy after the emission, e in [e0, e0 + de] (photon energy E_u - e): its
+ * limits are bin edges, so the window's width de is exact even where it is a tiny fraction
+ * of the photon energy (a hot bin's photon that leaves the grain near the bottom), which the
+ * difference of two photon-energy limits would lose.  Gauss-Legendre pieces between the
+ * grid nodes that fall inside (the cross-section's log-log kinks).  Over a window narrower
+ * than 1e-2 of the photon energy the Planck factor changes by at most e^7.45 (x <= 745), which
+ * 16 Gauss-Legendre nodes integrate to rounding.                                            */
+static double emitted_power_narrow(int N, const double* lam, const double* cabs, double T, double Eu, double e0,
+                                   double de)
+{
+    cool_ctx c = {N, lam, cabs, T};
+    double cut[64];
+    int nc = 0;
+    cut[nc++] = 0.0;
+    for (int n = 0; n < N && nc < 62; ++n) {  /* node offsets inside (0, de) */
+        double o = (Eu - hc() / lam[n]) - e0;
+        if (o > 0.0 && o < de) cut[nc++] = o;
+    }
+    cut[nc++] = de;
+    for (int i = 1; i < nc; ++i) {  /* ascending */
+        double v = cut[i];
+        int k = i - 1;
+        while (k >= 0 && cut[k] > v) { cut[k + 1] = cut[k]; --k; }
+        cut[k + 1] = v;
+    }
+    double pref = 8.0 * M_PI / (pow(H_PL, 3.0) * C_LI * C_LI);
+    double acc = 0.0;
+    for (int i = 0; i + 1 < nc; ++i) {
+        double r = 0.5 * (cut[i + 1] - cut[i]), m = cut[i] + r;
+        if (!(r > 0.0)) continue;
+        double s = 0.0;
+        for (int k = 0; k < GL_N; ++k) {
+            double eps = Eu - (e0 + m + r * gl_x[k]);  /* photon energy */
+            double x = eps / (K_B * T);
+            if (!(eps > 0.0) || x > 745.0) continue;
+            s += gl_w[k] * cabs_at(&c, hc() / eps) * eps * eps * eps / expm1(x);
+        }
+        acc += s * r;
+    }
+    return pref * acc;
+}
+
 int orc_cooling_discrete(int N, const double* lam, const double* cabs, int nb, const double* T, const double* E,
                          double* D)
 {
@@ -412,7 +455,12 @@ int orc_cooling_discrete(int N, const double* lam, const double* cabs, int nb, c
             double ehi_l = 0.5 * (E[l] + E[l + 1]);  /* l < u <= nb - 1, so E[l+1] exists */
             double emin = l == u - 1 ? 0.0 : E[u] - ehi_l;
             double emax = E[u] - elo_l;
-            D[(size_t)l * nb + u] = orc_emitted_power_window(N, lam, cabs, T[u], emin, emax) / (E[u] - E[l]);
+            double p;
+            if (l < u - 1 && ehi_l - elo_l < 1e-2 * emin)  /* narrow: in the grain's final energy */
+                p = emitted_power_narrow(N, lam, cabs, T[u], E[u], elo_l, ehi_l - elo_l);
+            else
+                p = orc_emitted_power_window(N, lam, cabs, T[u], emin, emax);
+            D[(size_t)l * nb + u] = p / (E[u] - E[l]);
         }
     }
     return ORC_OK;

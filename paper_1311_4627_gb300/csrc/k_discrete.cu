@@ -28,8 +28,8 @@ constexpr double kPi = 3.141592653589793;
 
 // Gauss-Legendre (the set-up's nodes, shared with k_cooling) over [ya, yb] in ln(lambda) of
 // C(lambda) B_lambda(T) lambda with C = c0 (lambda/lam0)^s.
-__device__ double window_panel(double ya, double yb, double c0, double lam0, double s, double T,
-                               const double* glx, const double* glw) {
+__device__ double gl_panel(double ya, double yb, double c0, double lam0, double s, double T, const double* glx,
+                           const double* glw) {
     double m = 0.5 * (ya + yb), r = 0.5 * (yb - ya), acc = 0.0;
     for (int k = 0; k < kGLPoints; ++k) {
         const double lam = exp(m + r * glx[k]);
@@ -40,6 +40,82 @@ __device__ double window_panel(double ya, double yb, double c0, double lam0, dou
         acc += glw[k] * c0 * pow(lam / lam0, s) * bl * lam;
     }
     return acc * r;
+}
+
+// The same over [ya, yb] in sub-panels short enough for the Wien factor: d ln(integrand) /
+// d ln(lambda) is about x - 4 + s with x = hc/(lambda k T), so a step of 2/max(x, 4) in
+// ln(lambda) keeps each sub-panel within a few e-folds, and every window, however far into the
+// tail, is integrated to its own relative accuracy.
+__device__ double window_panel(double ya, double yb, double c0, double lam0, double s, double T,
+                               const double* glx, const double* glw) {
+    double acc = 0.0;
+    for (double y = ya; y < yb;) {
+        const double x = kHC / (exp(y) * kK * T);
+        double h = 2.0 / fmax(x, 4.0);
+        if (h > 0.25) h = 0.25;
+        const double y1 = y + h < yb ? y + h : yb;
+        acc += gl_panel(y, y1, c0, lam0, s, T, glx, glw);
+        y = y1;
+    }
+    return acc;
+}
+
+// C(lambda): the log-log interpolant of the nodes, continued beyond the grid with the end
+// segments' power laws (as the cooling integral takes it).
+__device__ double cabs_at(int N, const double* lam, const double* C, double x) {
+    int n;
+    if (x < lam[0]) {
+        n = 0;
+    } else {
+        int lo = 0, hi = N - 2;  // last segment with lam[n] <= x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (lam[mid] <= x) lo = mid; else hi = mid - 1;
+        }
+        n = lo;
+    }
+    if (!(C[n] > 0.0 && C[n + 1] > 0.0)) return 0.0;
+    return C[n] * pow(x / lam[n], log(C[n + 1] / C[n]) / log(lam[n + 1] / lam[n]));
+}
+
+// A narrow window written in the grain's energy after the emission, e in [e0, e0 + de]
+// (photon energy E_u - e): its width is exact where it is a tiny fraction of the photon
+// energy, which a difference of photon-energy limits would lose.  Gauss-Legendre pieces
+// between the grid nodes inside.  Returns int C(E) E^3 / (e^(E/kT) - 1) dE over the window.
+__device__ double narrow_window(int N, const double* lam, const double* C, double T, double Eu, double e0, double de,
+                                const double* glx, const double* glw) {
+    // nodes inside: photon energies hc/lam_n in (Eu - e0 - de, Eu - e0)
+    double cuts[6];
+    int nc = 0;
+    cuts[nc++] = 0.0;
+    for (int n = 0; n < N && nc < 5; ++n) {
+        const double o = (Eu - kHC / lam[n]) - e0;
+        if (o > 0.0 && o < de) cuts[nc++] = o;
+    }
+    cuts[nc++] = de;
+    for (int i = 1; i < nc; ++i) {  // ascending
+        const double v = cuts[i];
+        int k = i - 1;
+        while (k >= 0 && cuts[k] > v) {
+            cuts[k + 1] = cuts[k];
+            --k;
+        }
+        cuts[k + 1] = v;
+    }
+    double acc = 0.0;
+    for (int i = 0; i + 1 < nc; ++i) {
+        const double r = 0.5 * (cuts[i + 1] - cuts[i]), m = cuts[i] + r;
+        if (!(r > 0.0)) continue;
+        double s = 0.0;
+        for (int k = 0; k < kGLPoints; ++k) {
+            const double eps = Eu - (e0 + m + r * glx[k]);
+            const double x = eps / (kK * T);
+            if (!(eps > 0.0) || x > 745.0) continue;
+            s += glw[k] * cabs_at(N, lam, C, kHC / eps) * eps * eps * eps / expm1(x);
+        }
+        acc += s * r;
+    }
+    return acc;
 }
 
 }  // namespace
@@ -83,6 +159,14 @@ __global__ void k_cooling_window(int N, const double* __restrict__ lam, const do
     if (lo < lmin) lo = lmin;
     const double hi = emin > 0.0 ? kHC / emin : INFINITY;
     const double* C = cabs + (size_t)g * N;
+    if (l < u - 1 && ehi_l - elo_l < 1e-2 * emin) {  // narrow: in the grain's final energy
+        if (lane == 0) {
+            const double p = 8.0 * kPi / (kH * kH * kH * kC * kC) *
+                             narrow_window(N, lam, C, Tu, Eg[u], elo_l, ehi_l - elo_l, glx, glw);
+            D[doff[g] + (size_t)l * nb + u] = p / (Eg[u] - Eg[l]);
+        }
+        return;
+    }
     double acc = 0.0;
     if (hi > lo) {
         for (int n = lane; n < N - 1; n += 32) {  // grid segments

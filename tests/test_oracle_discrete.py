@@ -144,3 +144,28 @@ def test_blackbody_width_moves_towards_canonical():
     m_d, v_d = width(P_d)
     assert v_c < 0.7 and abs(v_d - 1.0) < 0.15 and abs(v_d - 1.0) < abs(v_c - 1.0)
     assert abs(m_d / H - 1.0) < 0.1
+
+
+def test_narrow_windows_against_extended_precision(grain):
+    """A hot bin's photon that leaves the grain near the bottom: its photon-energy window is
+    ~1e-9 of the photon energy wide.  The rates against a 40-digit quadrature of the same
+    integral written in the grain's final energy (the window's limits are bin edges)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    lam, cabs, T, E, _ = grain
+    D = oracle.cooling_discrete(lam, cabs, T, E)
+    h, c, k = mp.mpf(W.H_PLANCK), mp.mpf(W.C_LIGHT), mp.mpf(W.K_BOLTZ)
+
+    def c_at(x):
+        x = float(x)
+        n = 0 if x < lam[0] else min(max(int(np.searchsorted(lam, x, side="right")) - 1, 0), lam.size - 2)
+        s = mp.log(mp.mpf(cabs[n + 1]) / cabs[n]) / mp.log(mp.mpf(lam[n + 1]) / lam[n])
+        return mp.mpf(cabs[n]) * (mp.mpf(x) / lam[n]) ** s
+
+    for u, l in ((127, 0), (127, 5), (113, 5), (99, 5)):
+        Eu, Tu = mp.mpf(E[u]), mp.mpf(T[u])
+        elo = mp.mpf(0) if l == 0 else (mp.mpf(E[l - 1]) + mp.mpf(E[l])) / 2
+        ehi = (mp.mpf(E[l]) + mp.mpf(E[l + 1])) / 2
+        f = lambda e: c_at(h * c / (Eu - e)) * (Eu - e) ** 3 / mp.expm1((Eu - e) / (k * Tu))  # noqa: E731
+        ref = 8 * mp.pi / (h**3 * c**2) * mp.quad(f, [elo, ehi]) / (Eu - mp.mpf(E[l]))
+        assert abs(float(mp.mpf(D[l, u]) / ref - 1)) < 1e-12, (u, l)
