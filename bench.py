@@ -76,6 +76,7 @@ def parse():
     ap.add_argument("--no-emis-heavy", action="store_true",
                     help="skip the emissivity-heavy workload (65536 cells x 32 grains x 512 bins x 2048 wavelengths)")
     ap.add_argument("--no-rt-volume", action="store_true", help="skip the RT-volume chunks section")
+    ap.add_argument("--no-discrete", action="store_true", help="skip the thermal-discrete cooling section")
     ap.add_argument("--emis-heavy-oracle-cells", type=int, default=256,
                     help="cells of the emissivity-heavy workload checked against the oracle")
     return ap.parse_args()
@@ -331,6 +332,95 @@ def single_cell_section(dev, stream):
         g.close()
     heat.heat_sync(ctx)
     heat.heat_destroy(ctx)
+    return out
+
+
+# ---------------------------------------------------------------------------- thermal-discrete cooling
+def thermal_discrete_section(dev):
+    """Thermal-discrete cooling (heat_opts.cooling = HEAT_COOLING_DISCRETE, exact FP64 path):
+    the single cell (8 grains x 128 bins, latency), 32 cells of the batched workload (64
+    grains, 128-1024 bins; their rate matrices are banded for the larger grains) and a dense
+    case for the state reduction's roofline (the 3.5 A grain, 128 bins, 87 % of its upward and
+    all its downward rates non-zero, dense after fill-in; 1216 cells = 8 spectra per SM).  Each solve is timed with CUDA events, the kernels with the
+    library's per-class events (build = rate matrices, recur = state reduction); P and j are
+    compared with the FP64 oracle's thermal-discrete solve on every spectrum of the single cell
+    and on 2 cells x 4 grains of the batched case."""
+    import torch
+
+    import oracle
+    from paper_1311_4627_gb300 import heat
+    from paper_1311_4627_gb300 import workloads as W
+
+    def solve(wl, reps):
+        ctx = heat.heat_create_grid(dev.index, wl.lam)
+        heat.heat_set_grains(ctx, wl.radius, wl.cabs, wl.bin_off, wl.T, wl.E, wl.size_weight)
+        s = torch.cuda.Stream(dev)
+        sh = s.cuda_stream
+        u = torch.from_numpy(wl.u).to(dev)  # the library keeps this pointer: u lives until the ctx is gone
+        heat.heat_set_fields(ctx, wl.n_cells, u, heat.HEAT_F64, 1, sh)
+        P = torch.empty(wl.n_cells, wl.total_bins, dtype=torch.float64, device=dev)
+        j = torch.empty(wl.n_cells, wl.n_grains, wl.n_lambda, dtype=torch.float64, device=dev)
+        kw = dict(build=heat.HEAT_BUILD_F64, emis=heat.HEAT_EMIS_F64, j_dtype=heat.HEAT_F64,
+                  cooling=heat.HEAT_COOLING_DISCRETE)
+        for _ in range(3):
+            heat.heat_solve(ctx, heat.heat_default_opts(**kw), P, j, sh)
+        heat.heat_sync(ctx)
+        heat.heat_get_timing(ctx, reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(s)
+        for _ in range(reps):
+            heat.heat_solve(ctx, heat.heat_default_opts(timing=1, **kw), P, j, sh)
+        e1.record(s)
+        torch.cuda.synchronize(dev)
+        heat.heat_sync(ctx)
+        ms = e0.elapsed_time(e1) / reps
+        kt = heat.heat_get_timing(ctx, reset=True)
+        out = P.cpu().numpy(), j.cpu().numpy()
+        heat.heat_destroy(ctx)
+        return ms, {k: v[0] / reps for k, v in kt.items() if v[1]}, out
+
+    def errors(wl_ref, Pg, jg):
+        P_ref, j_ref = oracle.solve_batch_discrete(wl_ref)[:2]
+        okP = P_ref > 1e-280
+        okj = np.abs(j_ref) > 1e-280
+        return {"P": float(np.max(np.abs(Pg[okP] - P_ref[okP]) / P_ref[okP])),
+                "j": float(np.max(np.abs(jg[okj] - j_ref[okj]) / np.abs(j_ref[okj])))}
+
+    out = {"path": "exact FP64 (FP64 rate matrices, state reduction, FP64 emissivity)"}
+    wl = W.single_cell()
+    ms, kt, (Pg, jg) = solve(wl, 20)
+    out["single_cell"] = {"workload": f"single cell x {wl.n_grains} grains, 128 bins, {wl.n_lambda} wavelengths",
+                          "us_per_solve": ms * 1e3, "kernels_us_per_solve": {k: v * 1e3 for k, v in kt.items()},
+                          "max_rel_err": errors(wl, Pg, jg),
+                          "err_sample": "all 8 spectra vs the FP64 oracle (P > 1e-280, |j| > 1e-280)"}
+
+    full = W.batched(cells=32)
+    ms, kt, (Pg, jg) = solve(full, 2)
+    cells, grains = [0, 31], [0, 21, 42, 63]
+    sub = W.grain_subset(W.field_subset(full, cells), grains)
+    cols = np.concatenate([np.arange(full.bin_off[g], full.bin_off[g + 1]) for g in grains])
+    out["batched_32_cells"] = {
+        "workload": "32 cells x 64 grains (3.5 A - 1 um), 128-1024 bins, 1024 wavelengths",
+        "ms_per_solve": ms, "spectra_per_s": 32 * full.n_grains / (ms * 1e-3),
+        "kernels_ms_per_solve": kt,
+        "max_rel_err": errors(sub, Pg[cells][:, cols], jg[cells][:, grains]),
+        "err_sample": "cells 0 and 31 x grains 0, 21, 42, 63 (128, 416, 704, 1024 bins) vs the FP64 oracle"}
+
+    dense = W.grain_subset(W.batched(cells=1216, n_lambda=256), [0])
+    M = dense.bins(0)
+    ms, kt, (Pg, jg) = solve(dense, 5)
+    fma_red = (M - 2) * (M - 1) * M / 3.0  # removing state n updates n(n-1) rates, n = 1..M-1
+    work = 2.0 * dense.n_cells * (fma_red + M * (M - 1) / 2.0)
+    ach = work / (kt["recur"] * 1e-3) / 1e12
+    out["dense_roofline"] = {
+        "workload": f"{dense.n_cells} cells x the 3.5 A grain ({M} bins, dense after fill-in), 256 wavelengths",
+        "ms_per_solve": ms, "kernels_ms_per_solve": kt,
+        "roofline": {"kernel": "state reduction (k_gth)", "bound": "alu", "unit": "TFLOP/s",
+                     "achieved": ach, "peak": FP64_PEAK_TFLOPS, "frac": ach / FP64_PEAK_TFLOPS,
+                     "peak_source": "nominal dense FP64 1.25 TFLOP/s (profiling recipe table)",
+                     "algorithmic_work": f"2 x cells x ((M-2)(M-1)M/3 + M(M-1)/2) = {work:.3e} FP64 flop per solve "
+                                         "(reduction updates + back substitution)"}}
     return out
 
 
@@ -790,6 +880,8 @@ def main():
         line["point_rule"] = point_rule_section(args, wl, ctx, heat, timed_run, opts_for, dev, sh, Cf_oracle)
     if rank == 0 and ws == 1 and not args.no_single_cell:
         line["single_cell"] = single_cell_section(dev, stream)
+    if rank == 0 and ws == 1 and not args.no_discrete:
+        line["thermal_discrete"] = thermal_discrete_section(dev)
     if rank == 0 and ws == 1 and not args.no_rt_volume:
         line["rt_volume"] = rt_volume_section(dev)
     if rank == 0 and ws == 1 and not args.no_emis_heavy:

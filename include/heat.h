@@ -81,10 +81,11 @@ enum {
                                     bin u go with the adjacent transition), so that the rates carry
                                     Eq. cooling's power.  P by the stationary solve of the full rate
                                     matrix (Eq. steady-state, Eq. level-sum; state reduction,
-                                    O(M^3) per spectrum: meant for few cells).  Needs the exact
-                                    build (HEAT_BUILD_F64) and the integral heating form; the
-                                    downward rates are computed on the first such solve after
-                                    heat_set_grains                                              */
+                                    up to M^3/3 multiply-adds per spectrum, fewer where the rates
+                                    span few bins).  Needs the exact build (HEAT_BUILD_F64), the
+                                    integral heating form, at most 2048 bins per grain and 6456
+                                    wavelengths (HEAT_EINVAL otherwise); the downward rates are
+                                    computed on the first such solve after heat_set_grains       */
 };
 
 /* emissivity contraction (Eq. emission) */
@@ -170,8 +171,10 @@ typedef struct heat_opts {
 /* kernel classes reported by heat_get_timing */
 enum {
     HEAT_T_FIELD = 0, /* field transpose and u slopes                     */
-    HEAT_T_BUILD = 1, /* matrix build: B band (Eq. bmatrix) and intra-bin terms */
-    HEAT_T_RECUR = 2, /* band-limited recursion and renormalisation (Eq. xf) */
+    HEAT_T_BUILD = 1, /* matrix build: B band (Eq. bmatrix) and intra-bin terms; with
+                         thermal-discrete cooling, the full rate matrices                */
+    HEAT_T_RECUR = 2, /* band-limited recursion and renormalisation (Eq. xf); with
+                         thermal-discrete cooling, the state reduction and normalisation */
     HEAT_T_EMIS = 3,  /* emissivity contraction (Eq. emission)              */
     HEAT_T_COUNT = 4
 };

@@ -58,7 +58,7 @@ struct heat_ctx {
     int row_weight = 30;                              // recursion order: band + row_weight x rows
     DevBuf d_bin_off, d_cabs, d_T, d_E, d_Cf, d_invC, d_invdE, d_invdE32, d_Cact, d_sC, d_ca32, d_ce32, d_sC32,
         d_rowptr, d_wmax, d_seg_ptr, d_pat64, d_pat32, d_soft, d_soft_off, d_K, d_Kw, d_w, d_koff_all, d_cde,
-        d_pent, d_pcol, d_kexp, d_rent, d_gl, d_Dtd, d_Dtd_off, d_Dtd_woff;
+        d_pent, d_pcol, d_kexp, d_rent, d_gl, d_Dtd, d_Dtd_off, d_Dtd_woff, d_Dtd_order;
     bool td_built = false;  // thermal-discrete downward rates computed
     // fields
     int n_cells = 0;

@@ -652,8 +652,13 @@ static heat_status ensure_discrete(heat_ctx* ctx, cudaStream_t st) {
         doff[g + 1] = doff[g] + nb * nb;
         woff[g + 1] = woff[g] + nb * (nb - 1) / 2;
     }
+    std::vector<int> order(G);  // grains with the most bins first (the solve's launch order)
+    for (int g = 0; g < G; ++g) order[g] = g;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return ctx->bin_off[a + 1] - ctx->bin_off[a] > ctx->bin_off[b + 1] - ctx->bin_off[b];
+    });
     if (ctx->d_Dtd.ensure(sizeof(double) * (size_t)std::max(1LL, doff[G])) || upload(ctx->d_Dtd_off, doff) ||
-        upload(ctx->d_Dtd_woff, woff))
+        upload(ctx->d_Dtd_woff, woff) || upload(ctx->d_Dtd_order, order))
         return ctx->fail(HEAT_ENOMEM, "heat_solve: allocation of thermal-discrete rates failed");
     CKR(cudaMemsetAsync(ctx->d_Dtd.p, 0, sizeof(double) * (size_t)doff[G], st));
     const double* gl = ctx->d_gl.as<double>();
@@ -731,6 +736,9 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
     const bool discrete = o.cooling == HEAT_COOLING_DISCRETE;
     if (discrete && (o.build != HEAT_BUILD_F64 || o.heating != HEAT_HEATING_INTEGRAL))
         return ctx->fail(HEAT_EINVAL, "heat_solve: thermal-discrete cooling needs the exact build and integral heating");
+    if (discrete && (ctx->max_bins > kDiscreteMaxBins || td_fill_smem_bytes(ctx->N) > kMaxSmemPerBlock))
+        return ctx->fail(HEAT_EINVAL, "heat_solve: thermal-discrete cooling takes at most 2048 bins per grain and "
+                                      "6456 wavelengths");
     const int emis_nt = o.emis_n_tile ? o.emis_n_tile : (ctx->tuned_emis_nt ? ctx->tuned_emis_nt : 256);
     int c_begin = o.cell_begin, count = o.cell_count > 0 ? o.cell_count : ctx->n_cells - o.cell_begin;
     if (c_begin < 0 || count < 0 || c_begin + count > ctx->n_cells)
@@ -799,13 +807,14 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
         if ((hs = prepare_tc_rows(ctx, o.emis, si, Cc)) != HEAT_OK) return hs;
     }
 
-    // thermal-discrete: spectra solved per launch, their rate matrices within about 1 GB
+    // thermal-discrete: spectra solved per launch, their rate matrices within about 4 GB (two
+    // resident spectra per SM at 1024 bins)
     long long td_batch = 0;
     if (discrete) {
         heat_status hs = ensure_discrete(ctx, st);
         if (hs != HEAT_OK) return hs;
         const long long per = (long long)ctx->max_bins * ctx->max_bins * (long long)sizeof(double);
-        td_batch = std::max(1LL, std::min((long long)span * G, (1LL << 30) / per));
+        td_batch = std::max(1LL, std::min((long long)span * G, (4LL << 30) / per));
     }
     // the recursion's epilogue packs the tensor-core operand (per-grain output, lane-per-cell
     // kernels); P then goes to memory only where the caller asked for it
@@ -950,10 +959,16 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
         ch.blocks_per_sm = o.recur_blocks_per_sm > 0 ? o.recur_blocks_per_sm : ctx->tuned_recur_bps;
         CKR(cudaMemsetAsync(ch.work, 0, sizeof(int) * 2, cs));
         TIMED(HEAT_T_FIELD, launch_field(gd, ctx->u_dev, ctx->u_dtype, cell0, ch, build, cs));
-        if (discrete) {  // field tables, then the full stationary solve (timed as the recursion)
-            TIMED(HEAT_T_RECUR, launch_discrete_solve(gd, ch, ctx->d_Dtd.as<double>(), ctx->d_Dtd_off.as<long long>(),
-                                                      sl.tdq.as<double>(), (long long)ctx->max_bins * ctx->max_bins,
-                                                      td_batch, cs));
+        if (discrete) {  // field tables, then per batch the rate matrices (timed as the build) and their solve
+            const long long qst = (long long)ctx->max_bins * ctx->max_bins;
+            for (long long s0 = 0, nsp = (long long)ch.cells * G; s0 < nsp; s0 += td_batch) {
+                const long long n = discrete_batch_spectra(gd, ch, s0, td_batch);
+                TIMED(HEAT_T_BUILD, launch_discrete_fill(gd, ch, ctx->d_Dtd.as<double>(), ctx->d_Dtd_off.as<long long>(),
+                                                         ctx->d_Dtd_order.as<int>(), sl.tdq.as<double>(), qst, s0, n,
+                                                         cs));
+                TIMED(HEAT_T_RECUR, launch_discrete_gth(gd, ch, ctx->d_Dtd_order.as<int>(), sl.tdq.as<double>(), qst, s0,
+                                                        n, cs));
+            }
         } else if (fused) {
             ch.phs = sl.phs.as<float>();
             TIMED(HEAT_T_RECUR, launch_fused(gd, ch, cs));
@@ -1283,7 +1298,15 @@ heat_status heat_get_cooling_discrete(heat_ctx* ctx, double* D) {
         const size_t nb = (size_t)(ctx->bin_off[g + 1] - ctx->bin_off[g]);
         n += nb * nb;
     }
-    CKR(cudaMemcpy(D, ctx->d_Dtd.p, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    std::vector<double> Dt(n);  // the device keeps each block by source bin (row u, column l)
+    CKR(cudaMemcpy(Dt.data(), ctx->d_Dtd.p, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    size_t o = 0;
+    for (int g = 0; g < ctx->G; ++g) {
+        const size_t nb = (size_t)(ctx->bin_off[g + 1] - ctx->bin_off[g]);
+        for (size_t l = 0; l < nb; ++l)
+            for (size_t u = 0; u < nb; ++u) D[o + l * nb + u] = Dt[o + u * nb + l];
+        o += nb * nb;
+    }
     return HEAT_OK;
 }
 
@@ -1327,7 +1350,7 @@ void heat_destroy(heat_ctx* ctx) {
                       &ctx->d_T, &ctx->d_E, &ctx->d_Cf, &ctx->d_invC, &ctx->d_invdE, &ctx->d_invdE32, &ctx->d_Cact,
                       &ctx->d_sC, &ctx->d_ca32, &ctx->d_ce32, &ctx->d_sC32, &ctx->d_rowptr, &ctx->d_wmax, &ctx->d_seg_ptr,
                       &ctx->d_pat64, &ctx->d_pat32, &ctx->d_soft, &ctx->d_soft_off, &ctx->d_K, &ctx->d_Kw, &ctx->d_w,
-                      &ctx->d_koff_all, &ctx->d_cde, &ctx->d_pent, &ctx->d_pcol, &ctx->d_kexp, &ctx->d_rent, &ctx->d_gl, &ctx->d_Dtd, &ctx->d_Dtd_off, &ctx->d_Dtd_woff, &ctx->d_u_own, &ctx->s_tasks, &ctx->s_tasks_tail, &ctx->d_status};
+                      &ctx->d_koff_all, &ctx->d_cde, &ctx->d_pent, &ctx->d_pcol, &ctx->d_kexp, &ctx->d_rent, &ctx->d_gl, &ctx->d_Dtd, &ctx->d_Dtd_off, &ctx->d_Dtd_woff, &ctx->d_Dtd_order, &ctx->d_u_own, &ctx->s_tasks, &ctx->s_tasks_tail, &ctx->d_status};
     for (DevBuf* b : bufs) b->release();
     for (auto& sl : ctx->slots) {
         DevBuf* sb[] = {&sl.ua64, &sl.su64, &sl.ua32, &sl.Bb64, &sl.Bb32, &sl.xs, &sl.ep,   &sl.pabs,

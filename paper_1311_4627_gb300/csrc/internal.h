@@ -124,8 +124,23 @@ cudaError_t launch_cooling_window(int N, const double* lam, const double* cabs, 
                                   cudaStream_t st);
 // P (and the ledger) of the chunk's cells x grains by the full stationary solve, `batch`
 // spectra at a time, each with an nb x nb rate matrix at q + k * qstride.
-cudaError_t launch_discrete_solve(const GrainDev& g, const ChunkDev& ch, const double* D, const long long* doff,
-                                  double* q, long long qstride, long long batch, cudaStream_t st);
+// State reduction: states removed per panel, threads per spectrum, and the largest grain whose
+// rate matrix is kept in shared memory (row stride nb + 1; 218,880 B at 160 bins).
+constexpr int kGthB = 8;
+constexpr int kGthThreads = 256;
+constexpr int kGthSmemBins = 160;
+size_t gth_smem_bytes(int max_bins);
+size_t td_fill_smem_bytes(int N);
+constexpr int kDiscreteMaxBins = 2048;                // the state reduction's vectors in shared memory
+constexpr size_t kMaxSmemPerBlock = 227 * 1024;       // opt-in dynamic shared memory per block
+// Spectra are solved in launches of `batch` (rate matrices at q + k * qstride): the k-th
+// spectrum from s0 is grain gorder[(s0 + k) / cells], cell (s0 + k) % cells.
+long long discrete_batch_spectra(const GrainDev& g, const ChunkDev& ch, long long s0, long long batch);
+cudaError_t launch_discrete_fill(const GrainDev& g, const ChunkDev& ch, const double* D, const long long* doff,
+                                 const int* gorder, double* q, long long qstride, long long s0, long long n,
+                                 cudaStream_t st);
+cudaError_t launch_discrete_gth(const GrainDev& g, const ChunkDev& ch, const int* gorder, double* q, long long qstride,
+                                long long s0, long long n, cudaStream_t st);
 
 // ---- emissivity (k_emis.cu)
 // C[z][m][n] = sum_{k in [koff[z], koff[z+1])} A[m][k] B[k][n] for z < nz, m < M, n < N;

@@ -15,8 +15,10 @@
 //   k_gth  (per spectrum): state reduction (Grassmann, Taksar, Heyman): states n = M..1 are
 //       removed, their rates redistributed, q_ij += q_in q_nj / s_n with s_n = sum_{j<n} q_nj
 //       (sums and products of non-negative numbers only); then X_0 = 1,
-//       X_n = sum_{i<n} X_i q_in / s_n, power-of-two rescales, P = X / sum X.  O(M^3) per
-//       spectrum: meant for solves of few cells (one block per spectrum, q in device memory).
+//       X_n = sum_{i<n} X_i q_in / s_n, power-of-two rescales, P = X / sum X.  About M^3/3
+//       fused multiply-adds per spectrum, on the FP64 unit: one block per spectrum, states
+//       removed eight at a time with one delayed rank-8 update of the rest (q in shared memory
+//       up to 160 bins, else in device memory, read and written once per eight states).
 #include "common.cuh"
 #include "internal.h"
 
@@ -163,7 +165,7 @@ __global__ void k_cooling_window(int N, const double* __restrict__ lam, const do
         if (lane == 0) {
             const double p = 8.0 * kPi / (kH * kH * kH * kC * kC) *
                              narrow_window(N, lam, C, Tu, Eg[u], elo_l, ehi_l - elo_l, glx, glw);
-            D[doff[g] + (size_t)l * nb + u] = p / (Eg[u] - Eg[l]);
+            D[doff[g] + (size_t)u * nb + l] = p / (Eg[u] - Eg[l]);
         }
         return;
     }
@@ -196,7 +198,7 @@ __global__ void k_cooling_window(int N, const double* __restrict__ lam, const do
         }
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) D[doff[g] + (size_t)l * nb + u] = 4.0 * kPi * acc / (Eg[u] - Eg[l]);
+    if (lane == 0) D[doff[g] + (size_t)u * nb + l] = 4.0 * kPi * acc / (Eg[u] - Eg[l]);
 }
 
 namespace {
@@ -210,64 +212,144 @@ __device__ __forceinline__ double seg_part(double om, double s, double lamn, int
     return om * lp * exp(q * tx) * dt * e1d(q * dt);
 }
 
-// Integral of Omega lambda^p over [a, b] (clipped to the grid) for one cell and grain.
-__device__ double range_integral(const GrainDev& gd, const ChunkDev& ch, int g, int cell, int p, double a, double b) {
-    const int N = gd.N;
-    const double* lam = gd.lam;
-    if (a < lam[0]) a = lam[0];
-    if (b > lam[N - 1]) b = lam[N - 1];
-    if (!(b > a)) return 0.0;
-    int n = 0;
-    {
-        int lo = 0, hi = N - 2;  // last segment with lam[n] <= a
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (lam[mid] <= a) lo = mid; else hi = mid - 1;
-        }
-        n = lo;
+// Segment n (0 .. N-2) holding x in [lam_0, lam_{N-1}]: lam_n <= x < lam_{n+1} (x = lam_{N-1} in
+// the last).  Searched in FP32, then moved by at most one node with the FP64 grid.
+__device__ __forceinline__ int seg_of(const float* l32, const double* lam, int N, double x) {
+    const float xf = (float)x;
+    int lo = 0, hi = N - 2;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (l32[mid] <= xf) lo = mid; else hi = mid - 1;
     }
-    double acc = 0.0;
-    for (; n < N - 1 && lam[n] < b; ++n) {
-        const double om = ch.ua64[(size_t)n * ch.Cc + cell] * gd.Cact[(size_t)g * N + n];
-        if (!(om > 0.0)) continue;
-        const double s = ch.su64[(size_t)n * ch.Cc + cell] + gd.sC[(size_t)g * N + n];
-        const double x = lam[n] > a ? lam[n] : a, y = lam[n + 1] < b ? lam[n + 1] : b;
-        if (y > x) acc += seg_part(om, s, lam[n], p, x, y);
-    }
-    return acc;
+    if (lo < N - 2 && lam[lo + 1] <= x) ++lo;
+    else if (lo > 0 && lam[lo] > x) --lo;
+    return lo;
 }
 
 }  // namespace
 
-// One block per spectrum (cell, grain) of the chunk's cells: q [nb][nb] (row-major, rate from
-// row to column) at q + spectrum * qstride; the absorbed power c int Omega on the grid.
-__global__ void __launch_bounds__(256) k_td_fill(GrainDev gd, ChunkDev ch, const double* __restrict__ D,
-                                                 const long long* __restrict__ doff, long long s0, double* q,
-                                                 long long qstride) {
+// Shared memory of k_td_fill for a grid of N wavelengths: per segment the cell's Omega_n and
+// log-log slope, the segment's integral of Omega lambda, the suffix sums of the integrals of
+// Omega, and the grid in FP32.
+size_t td_fill_smem_bytes(int N) { return sizeof(double) * 4 * (size_t)N + sizeof(float) * (size_t)N; }
+
+// Spectrum of block b of a launch that starts at spectrum s0: grains in the order `gorder`
+// (most bins first), every cell of the chunk for each grain in turn, so that the spectra of one
+// launch have similar cost and the largest start first.
+__device__ __forceinline__ void td_spectrum(const ChunkDev& ch, const int* gorder, long long s0, int& cell, int& g) {
     const long long sp = s0 + blockIdx.x;
-    const int cell = (int)(sp / gd.G), g = (int)(sp % gd.G);
+    cell = (int)(sp % ch.cells);
+    g = gorder[sp / ch.cells];
+}
+
+// One block per spectrum (cell, grain) of the chunk's cells: q [nb][nb] (row-major, rate from
+// row to column) at q + block * qstride, and the absorbed power c int Omega on the grid.
+// Downward rates are copied from the grain's table (Dt[u][l], from u to l).  The heating
+// rate from i into bin j > i is (1/h) int Omega lambda over the photon wavelengths that end in
+// bin j, [hc/(Ehi_j - E_i), hc/(Elo_j - E_i)] (Ehi_M = infinity), plus on j = i + 1 the
+// power of the photons too soft to leave bin i, c int_{lambda > hc/(Elo_j - E_i)} Omega,
+// over E_j - E_i.  A row's windows tile the grid: each is the closed-form integral of its
+// partial end segments plus the segment integrals between them (summed, not differenced);
+// the soft term is its partial segment plus a suffix sum.  A warp per row, a lane per j;
+// neighbouring lanes share their window edge, and the row ends where the window leaves the
+// short-wavelength end of the grid.
+__global__ void __launch_bounds__(256) k_td_fill(GrainDev gd, ChunkDev ch, const double* __restrict__ Dt,
+                                                 const long long* __restrict__ doff, const int* __restrict__ gorder,
+                                                 long long s0, double* q, long long qstride) {
+    extern __shared__ double fsm[];
+    int cell, g;
+    td_spectrum(ch, gorder, s0, cell, g);
+    const int N = gd.N;
+    const double* lam = gd.lam;
+    double* om = fsm;
+    double* sl = om + N;
+    double* I1 = sl + N;
+    double* S0 = I1 + N;
+    float* l32 = (float*)(S0 + N);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    for (int n = tid; n < N; n += blockDim.x) {
+        l32[n] = gd.lam32[n];
+        double o = 0.0, sv = 0.0, i0 = 0.0, i1 = 0.0;
+        if (n < N - 1) {
+            o = ch.ua64[(size_t)n * ch.Cc + cell] * gd.Cact[(size_t)g * N + n];
+            sv = ch.su64[(size_t)n * ch.Cc + cell] + gd.sC[(size_t)g * N + n];
+            if (o > 0.0) {
+                i0 = seg_part(o, sv, lam[n], 0, lam[n], lam[n + 1]);
+                i1 = seg_part(o, sv, lam[n], 1, lam[n], lam[n + 1]);
+            } else {
+                o = 0.0;
+            }
+        }
+        om[n] = o;
+        sl[n] = sv;
+        I1[n] = i1;
+        S0[n] = i0;
+    }
+    __syncthreads();
+    if (warp == 0) {  // suffix sums of the segment integrals of Omega, S0[n] = sum_{m >= n}
+        const int per = (N + 31) / 32, b0 = lane * per, b1 = min(N, b0 + per);
+        double part = 0.0;
+        for (int n = b1 - 1; n >= b0; --n) part += S0[n];
+        double above = 0.0;  // sum over the lanes after this one
+        for (int o = 1; o < 32; o <<= 1) {
+            const double t = __shfl_down_sync(0xffffffffu, part + above, o);
+            if (lane + o < 32) above += t;
+        }
+        for (int n = b1 - 1; n >= b0; --n) {
+            above += S0[n];
+            S0[n] = above;
+        }
+    }
+    __syncthreads();
     const int off = gd.bin_off[g], nb = gd.bin_off[g + 1] - off;
     const double* E = gd.E + off;
-    const double* Dg = D + doff[g];
+    const double* Dg = Dt + doff[g];
     double* qs = q + (size_t)blockIdx.x * qstride;
-    for (long long idx = threadIdx.x; idx < (long long)nb * nb; idx += blockDim.x) {
-        const int i = (int)(idx / nb), j = (int)(idx % nb);
-        double v = 0.0;
-        if (j < i) {
-            v = Dg[(size_t)j * nb + i];
-        } else if (j > i) {  // heating from i into bin j: photons of [Elo_j - E_i, Ehi_j - E_i)
-            const int M = nb - 1;
-            const double elo = 0.5 * (E[j - 1] + E[j]);
-            const double la = j == M ? 0.0 : kHC / (0.5 * (E[j] + E[j + 1]) - E[i]);
-            const double lb = kHC / (elo - E[i]);
-            v = range_integral(gd, ch, g, cell, 1, la, lb) / kH;
-            if (j == i + 1)  // photons too soft to leave bin i (their power, per transition energy)
-                v += kC * range_integral(gd, ch, g, cell, 0, lb, gd.lam[gd.N - 1]) / (E[j] - E[i]);
+    const double lam0 = lam[0], lamN = lam[N - 1];
+    const int M = nb - 1;
+    for (int i = warp; i < nb; i += nw) {
+        double* qi = qs + (size_t)i * nb;
+        const double* di = Dg + (size_t)i * nb;
+        for (int j = lane; j <= i; j += 32) qi[j] = j < i ? di[j] : 0.0;
+        const double Ei = E[i];
+        int jb = i + 1;
+        for (; jb < nb; jb += 32) {
+            const int j = jb + lane;
+            double lb = 0.0, la = 0.0;
+            if (j < nb) lb = kHC / (0.5 * (E[j - 1] + E[j]) - Ei);
+            const double nxt = __shfl_down_sync(0xffffffffu, lb, 1);
+            if (j < nb) la = j == M ? 0.0 : (lane < 31 ? nxt : kHC / (0.5 * (E[j] + E[j + 1]) - Ei));
+            double v = 0.0;
+            if (j < nb) {
+                const double a = la > lam0 ? la : lam0, b = lb < lamN ? lb : lamN;
+                if (b > a) {
+                    const int na = seg_of(l32, lam, N, a), nz = seg_of(l32, lam, N, b);
+                    if (na == nz) {
+                        if (om[na] > 0.0) v = seg_part(om[na], sl[na], lam[na], 1, a, b);
+                    } else {
+                        if (om[na] > 0.0) v = seg_part(om[na], sl[na], lam[na], 1, a, lam[na + 1]);
+                        for (int n = na + 1; n < nz; ++n) v += I1[n];
+                        if (om[nz] > 0.0 && b > lam[nz]) v += seg_part(om[nz], sl[nz], lam[nz], 1, lam[nz], b);
+                    }
+                    v /= kH;
+                }
+                if (j == i + 1 && lb < lamN) {  // photons too soft to leave bin i
+                    const double x = lb > lam0 ? lb : lam0;
+                    const int n = seg_of(l32, lam, N, x);
+                    double w = S0[n + 1];
+                    if (om[n] > 0.0) w += seg_part(om[n], sl[n], lam[n], 0, x, lam[n + 1]);
+                    v += kC * w / (E[j] - Ei);
+                }
+                qi[j] = v;
+            }
+            if (__all_sync(0xffffffffu, j >= nb || lb <= lam0)) {  // every later window is shortward of the grid
+                jb += 32;
+                break;
+            }
         }
-        qs[idx] = v;
+        for (int j = jb + lane; j < nb; j += 32) qi[j] = 0.0;
     }
-    if (threadIdx.x == 0 && ch.pabs)
-        ch.pabs[(size_t)cell * gd.G + g] = kC * range_integral(gd, ch, g, cell, 0, gd.lam[0], gd.lam[gd.N - 1]);
+    if (tid == 0 && ch.pabs) ch.pabs[(size_t)cell * gd.G + g] = kC * S0[0];
 }
 
 namespace {
@@ -290,70 +372,192 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 
 }  // namespace
 
+// Exit rate of state k, s_k = sum_{j < k} q_kj, its reciprocal, and the lowest column with a
+// rate out of k (k if none), by one warp; lane 0 stores them.  The lanes read the row as
+// j = lane + 32 t, so a warp that has just written the row calls __syncwarp first.
+__device__ __forceinline__ void row_exit(const double* qk, int k, double* s, double* rs, int* jlo, int lane) {
+    double part = 0.0;
+    int jl = k;
+    for (int j = lane; j < k; j += 32) {
+        const double v = qk[j];
+        part += v;
+        if (v != 0.0 && j < jl) jl = j;
+    }
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    jl = __reduce_min_sync(0xffffffffu, jl);
+    if (lane == 0) {
+        s[k] = part;
+        rs[k] = part > 0.0 ? 1.0 / part : 0.0;  // s_k = 0: nothing leaves k downward
+        jlo[k] = jl;
+    }
+}
+
 // One block per spectrum: state reduction of q, back substitution, P and the energy check.
-// Shared memory: s[nb] (exit rates), r[nb] (the removed state's rates / s_n), X[nb].
-__global__ void __launch_bounds__(256) k_gth(GrainDev gd, ChunkDev ch, long long s0, double* q, long long qstride) {
+//
+// States are removed kGthB at a time (a panel [p0, hi]).  Removing state k adds
+// q_ik q_kj / s_k to q_ij for i, j < k.  Inside the panel, step by step, for the rows of the
+// panel's remaining states; after the panel, for the rows below it, first their panel columns
+// (a sweep over the panel's states in removal order, in registers) and then the block below
+// the panel in one pass: sum over the panel's k of q_ik (q_kj / s_k), a rank-kGthB product
+// in which q_ik is column k as it stood when k was removed (final from then on: it is the
+// column the back substitution reads) and q_kj / s_k is row k at that time, kept in U.  Every
+// term stays a sum of products of non-negative numbers; only the order of the additions
+// differs from removing the states one by one.  The diagonal of q is never read (s_k sums
+// the off-diagonal row), so the updates do not skip it.  The warp that updates the row of the
+// next state to be removed also sums it (row_exit), so a step waits on no block-wide sum.
+// The fill-in of removing k stays inside the rows that reach k and the columns k reaches:
+// rows with no rate into the panel are skipped and columns start at the panel's lowest.
+//
+// Back substitution, right-looking: X_0 = 1, and once X_i is final every column n > i
+// (owned by a fixed thread) takes X_i q_in; X_{i+1} is then complete and its owner divides by
+// s_{i+1}.  Past 2^800 every X is scaled by 2^-800 (exact).  P = X / sum X.
+//
+// SMQ: q is copied into shared memory (row stride nb + 1), for grains of up to kGthSmemBins
+// bins; otherwise it is updated in place in device memory, where each panel reads and writes
+// the block below it once for kGthB fused multiply-adds per element.
+// Shared memory: s, 1/s, X [nb] each, U [kGthB][nb], the lowest columns [nb] (ints, padded
+// to doubles), then q (SMQ).
+template <bool SMQ>
+__global__ void __launch_bounds__(kGthThreads, 1) k_gth(GrainDev gd, ChunkDev ch, const int* __restrict__ gorder,
+                                                        long long s0, double* q, long long qstride) {
     extern __shared__ double smd[];
-    __shared__ double red[8];
-    const long long sp = s0 + blockIdx.x;
-    const int cell = (int)(sp / gd.G), g = (int)(sp % gd.G);
+    __shared__ double red[kGthThreads / 32];
+    __shared__ int rescale;
+    int cell, g;
+    td_spectrum(ch, gorder, s0, cell, g);
     const int off = gd.bin_off[g], nb = gd.bin_off[g + 1] - off;
-    double* qs = q + (size_t)blockIdx.x * qstride;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kGthThreads / 32;
     double* s = smd;
-    double* r = smd + nb;
-    double* X = smd + 2 * nb;
-    for (int n = nb - 1; n >= 1; --n) {
-        double part = 0.0;
-        for (int j = threadIdx.x; j < n; j += blockDim.x) part += qs[(size_t)n * nb + j];
-        const double sn = block_sum(part, red);
-        if (threadIdx.x == 0) s[n] = sn;
-        if (sn == 0.0) continue;  // uniform: nothing leaves n downward
-        for (int j = threadIdx.x; j < n; j += blockDim.x) r[j] = qs[(size_t)n * nb + j] / sn;
-        __syncthreads();
-        for (long long idx = threadIdx.x; idx < (long long)n * n; idx += blockDim.x) {
-            const int i = (int)(idx / n), j = (int)(idx % n);
-            const double qin = qs[(size_t)i * nb + n];
-            if (i != j && qin != 0.0) qs[(size_t)i * nb + j] = fma(qin, r[j], qs[(size_t)i * nb + j]);
-        }
+    double* rs = s + nb;
+    double* X = rs + nb;
+    double* U = X + nb;
+    int* jlo = (int*)(U + kGthB * nb);
+    double* qg = q + (size_t)blockIdx.x * qstride;
+    double* qs = qg;
+    int ld = nb;
+    if (SMQ) {
+        qs = U + kGthB * nb + (nb + 1) / 2;
+        ld = nb + 1;
+        for (int i = warp; i < nb; i += nw)
+            for (int j = lane; j < nb; j += 32) qs[(size_t)i * ld + j] = qg[(size_t)i * nb + j];
         __syncthreads();
     }
-    // back substitution (X in shared memory), rescaled by 2^-800 past 2^800
-    if (threadIdx.x == 0) X[0] = 1.0;
+    if (warp == 0) row_exit(qs + (size_t)(nb - 1) * ld, nb - 1, s, rs, jlo, lane);
+    if (tid == 0) rescale = 0;
     __syncthreads();
-    double total = 1.0;
-    bool bad = false;
-    for (int n = 1; n < nb; ++n) {
-        double part = 0.0;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) part += X[i] * qs[(size_t)i * nb + n];
-        const double in = block_sum(part, red);
-        const double sn = s[n];
-        double xn = 0.0;
-        if (sn == 0.0) {
-            if (in != 0.0) bad = true;
-        } else {
-            xn = in / sn;
+    for (int hi = nb - 1; hi >= 1; hi -= kGthB) {
+        const int p0 = hi - kGthB + 1 > 1 ? hi - kGthB + 1 : 1;
+        const int nk = hi - p0 + 1;
+        for (int k = hi; k >= p0; --k) {
+            double* Uk = U + (size_t)(hi - k) * nb;
+            const double* qk = qs + (size_t)k * ld;
+            const double r = rs[k];
+            const int jk = jlo[k];
+            for (int j = tid; j < k; j += kGthThreads) Uk[j] = j < jk ? 0.0 : qk[j] * r;
+            __syncthreads();
+            for (int i = p0 + warp; i < k; i += nw) {  // the panel's rows below k, columns from jk
+                double* qi = qs + (size_t)i * ld;
+                const double qik = qi[k];
+                if (qik != 0.0)
+                    for (int j = jk + lane; j < k; j += 32) qi[j] = fma(qik, Uk[j], qi[j]);
+                if (i == k - 1) {  // the next state to be removed
+                    __syncwarp();
+                    row_exit(qi, k - 1, s, rs, jlo, lane);
+                }
+            }
+            __syncthreads();
         }
-        total += xn;
-        if (xn > 0x1p800) {
-            for (int i = threadIdx.x; i < n; i += blockDim.x) X[i] *= 0x1p-800;
-            xn *= 0x1p-800;
-            total *= 0x1p-800;
+        if (nk > 1)  // rows below the panel: the panel's columns, state by state in removal order
+            for (int i = tid; i < p0; i += kGthThreads) {
+                double* qi = qs + (size_t)i * ld;
+                double x[kGthB];
+                bool any = false;
+#pragma unroll
+                for (int kk = 0; kk < kGthB; ++kk) {
+                    const double v = qi[hi - kk > 0 ? hi - kk : 0];
+                    x[kk] = kk < nk ? v : 0.0;
+                    any |= x[kk] != 0.0;
+                }
+                if (!any) continue;
+#pragma unroll
+                for (int kk = 0; kk < kGthB - 1; ++kk) {
+                    if (kk < nk - 1 && x[kk] != 0.0) {
+                        const double* Uk = U + (size_t)kk * nb;
+#pragma unroll
+                        for (int k2 = kk + 1; k2 < kGthB; ++k2)
+                            if (k2 < nk) x[k2] = fma(x[kk], Uk[hi - k2], x[k2]);
+                    }
+                }
+#pragma unroll
+                for (int kk = 1; kk < kGthB; ++kk)
+                    if (kk < nk) qi[hi - kk] = x[kk];
+            }
+        int jp = nb;
+        for (int k = p0; k <= hi; ++k) jp = jlo[k] < jp ? jlo[k] : jp;
+        __syncthreads();
+        for (int i = warp; i < p0; i += nw) {  // the block below the panel: rows with a rate into it
+            double* qi = qs + (size_t)i * ld;
+            const double lv = lane < nk ? qi[hi - lane] : 0.0;
+            if (__ballot_sync(0xffffffffu, lv != 0.0) != 0u) {
+                double l[kGthB];
+#pragma unroll
+                for (int kk = 0; kk < kGthB; ++kk) l[kk] = __shfl_sync(0xffffffffu, lv, kk);
+                for (int j = jp + lane; j < p0; j += 32) {
+                    double v = qi[j];
+#pragma unroll
+                    for (int kk = 0; kk < kGthB; ++kk) v = fma(l[kk], U[kk * nb + j], v);
+                    qi[j] = v;
+                }
+            }
+            if (i == p0 - 1 && i > 0) {  // the first state of the next panel
+                __syncwarp();
+                row_exit(qi, i, s, rs, jlo, lane);
+            }
         }
-        if (threadIdx.x == 0) X[n] = xn;
         __syncthreads();
     }
-    const double inv = 1.0 / total;
-    double emit = 0.0;
-    if (cell < ch.cells) {
-        double* prow = ch.P + (size_t)cell * ch.ldP + off;
-        for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-            const double p = X[i] * inv;
-            prow[i] = p;
-            emit = fma(p, gd.cde[off + i], emit);
+    // back substitution
+    for (int n = tid; n < nb; n += kGthThreads) X[n] = n == 0 ? 1.0 : 0.0;
+    __syncthreads();
+    bool bad = false;
+    for (int i = 0; i + 1 < nb; ++i) {
+        const double xi = X[i];
+        const double* qi = qs + (size_t)i * ld;
+        for (int n = tid; n < nb; n += kGthThreads) {
+            if (n <= i) continue;
+            double a = fma(xi, qi[n], X[n]);
+            if (n == i + 1) {  // every state below n has contributed
+                if (s[n] == 0.0) {
+                    bad |= a != 0.0;
+                    a = 0.0;
+                } else {
+                    a *= rs[n];
+                }
+                if (a > 0x1p800) rescale = 1;
+            }
+            X[n] = a;
         }
+        __syncthreads();
+        if (rescale) {
+            for (int n = tid; n < nb; n += kGthThreads) X[n] *= 0x1p-800;
+            __syncthreads();
+            if (tid == 0) rescale = 0;
+            __syncthreads();
+        }
+    }
+    bad = __syncthreads_or(bad);
+    double part = 0.0;
+    for (int i = tid; i < nb; i += kGthThreads) part += X[i];
+    const double inv = 1.0 / block_sum(part, red);
+    double emit = 0.0;
+    double* prow = ch.P + (size_t)cell * ch.ldP + off;
+    for (int i = tid; i < nb; i += kGthThreads) {
+        const double p = X[i] * inv;
+        prow[i] = p;
+        emit = fma(p, gd.cde[off + i], emit);
     }
     emit = block_sum(emit, red);
-    if (threadIdx.x == 0 && cell < ch.cells) {
+    if (tid == 0) {
         if (ch.ledger) {
             double* lg = ch.ledger + ((size_t)cell * gd.G + g) * 2;
             lg[0] = ch.pabs[(size_t)cell * gd.G + g];
@@ -374,23 +578,44 @@ cudaError_t launch_cooling_window(int N, const double* lam, const double* cabs, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_discrete_solve(const GrainDev& g, const ChunkDev& ch, const double* D, const long long* doff,
-                                  double* q, long long qstride, long long batch, cudaStream_t st) {
+size_t gth_smem_bytes(int max_bins) {
+    const size_t vec = sizeof(double) * ((size_t)(3 + kGthB) * max_bins + (max_bins + 1) / 2);
+    return max_bins <= kGthSmemBins ? vec + sizeof(double) * (size_t)max_bins * (max_bins + 1) : vec;
+}
+
+long long discrete_batch_spectra(const GrainDev& g, const ChunkDev& ch, long long s0, long long batch) {
     const long long spectra = (long long)ch.cells * g.G;
-    const size_t smem = sizeof(double) * 3 * (size_t)g.max_bins;
+    return spectra - s0 < batch ? spectra - s0 : batch;
+}
+
+cudaError_t launch_discrete_fill(const GrainDev& g, const ChunkDev& ch, const double* D, const long long* doff,
+                                 const int* gorder, double* q, long long qstride, long long s0, long long n,
+                                 cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const size_t smem = td_fill_smem_bytes(g.N);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_gth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_td_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    for (long long s0 = 0; s0 < spectra; s0 += batch) {
-        const unsigned n = (unsigned)(spectra - s0 < batch ? spectra - s0 : batch);
-        k_td_fill<<<n, 256, 0, st>>>(g, ch, D, doff, s0, q, qstride);
-        cudaError_t e = cudaGetLastError();
+    k_td_fill<<<(unsigned)n, 256, smem, st>>>(g, ch, D, doff, gorder, s0, q, qstride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_discrete_gth(const GrainDev& g, const ChunkDev& ch, const int* gorder, double* q, long long qstride,
+                                long long s0, long long n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const bool smq = g.max_bins <= kGthSmemBins;
+    const size_t smem = gth_smem_bytes(g.max_bins);
+    if (smem > 48 * 1024) {
+        cudaError_t e = smq ? cudaFuncSetAttribute(k_gth<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                            : cudaFuncSetAttribute(k_gth<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_gth<<<n, 256, smem, st>>>(g, ch, s0, q, qstride);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    if (smq)
+        k_gth<true><<<(unsigned)n, kGthThreads, smem, st>>>(g, ch, gorder, s0, q, qstride);
+    else
+        k_gth<false><<<(unsigned)n, kGthThreads, smem, st>>>(g, ch, gorder, s0, q, qstride);
+    return cudaGetLastError();
 }
 
 }  // namespace heat
