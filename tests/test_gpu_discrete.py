@@ -43,7 +43,17 @@ def ragged():
     c[-1].close()
 
 
-@pytest.mark.parametrize("case", ["single", "ragged"])
+@pytest.fixture(scope="module")
+def banded():
+    """2 cells x the batched workload's grains of 704 and 1024 bins: rates that span few bins
+    (the state reduction in device memory, rows and columns limited to the band)."""
+    full = W.batched(cells=2, n_lambda=256)
+    c = _case(W.grain_subset(full, [42, 63]))
+    yield c
+    c[-1].close()
+
+
+@pytest.mark.parametrize("case", ["single", "ragged", "banded"])
 def test_downward_rates_match_oracle(case, request):
     wl, Dg, _, _, _, lib = request.getfixturevalue(case)
     got = heat.heat_get_cooling_discrete(lib.ctx, [wl.bins(g) for g in range(wl.n_grains)])
@@ -52,7 +62,7 @@ def test_downward_rates_match_oracle(case, request):
         assert ok and r <= 1e-12, (g, r)
 
 
-@pytest.mark.parametrize("case", ["single", "ragged"])
+@pytest.mark.parametrize("case", ["single", "ragged", "banded"])
 def test_discrete_solve_matches_oracle(case, request):
     import torch
 
@@ -110,3 +120,26 @@ def test_discrete_option_checks(single):
         with pytest.raises(heat.HeatError) as e:
             lib.solve(**opts)
         assert e.value.status == heat.HEAT_EINVAL
+
+
+def test_discrete_size_limit():
+    """More than 2048 bins in a grain: thermal-discrete solves are refused (HEAT_EINVAL), the
+    thermal-continuous path still takes the grain."""
+    lam = W.wavelength_grid(64)
+    nb = 2049
+    T = np.geomspace(3.0, 2000.0, nb)
+    cabs = W.cabs_model(1e-5, lam, "silicate")[None, :]
+    E = W.debye_enthalpy(500.0, W.n_atoms(1e-5, "silicate"), T)
+    wl = W.Workload("large grain", lam, np.array([1e-5]), ["silicate"], cabs, np.array([0, nb], dtype=np.int32),
+                    T, E, np.ones(1), u=W.three_bb_fields(lam, np.array([1.0]), np.array([0.0]),
+                                                          np.array([[0.3, 0.5, 0.2]])))
+    lib = Lib(wl)
+    try:
+        lib.set_fields(wl.u)
+        with pytest.raises(heat.HeatError) as e:
+            lib.solve(want_j=False, **DISCRETE)
+        assert e.value.status == heat.HEAT_EINVAL
+        P, _ = lib.solve(want_j=False, build=heat.HEAT_BUILD_F64)
+        assert abs(P.sum() - 1.0) < 1e-12
+    finally:
+        lib.close()
