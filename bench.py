@@ -821,10 +821,26 @@ def main():
         rel = torch.where(msk, (got - ref).abs() / ref.clamp_min(1e-300), torch.zeros_like(ref)).max(dim=1).values
         rel = rel.cpu().numpy()
         spq = spr[: nchk * G].cpu().numpy()
+        # calibration: per tolerance, the cells whose every grain's spread is within it (fallback
+        # is per cell) and the error of the spectra those cells would take from the network
+        cell_sp = spq.reshape(nchk, G).max(axis=1)
+        rel_c = rel.reshape(nchk, G)
+        calib = {}
+        for t in (0.01, 0.03, 0.1, 0.3, 1.0):
+            acc = cell_sp <= t
+            ea = rel_c[acc].ravel()
+            calib[str(t)] = {"accepted_cells": float(np.mean(acc)), "accepted_spectra": float(np.mean(spq <= t)),
+                             "err_accepted_median": float(np.median(ea)) if ea.size else None,
+                             "err_accepted_max": float(np.max(ea)) if ea.size else None}
+        mixed_ms = paths["mixed"]["ms_per_step"] if "mixed" in paths else ms
         raw = {"inference_spectra_per_s": nsm / (ms_inf / 1e3), "inference_ms": ms_inf,
                "max_rel_err_per_spectrum_quantiles": {q: float(np.quantile(rel, float(q))) for q in ("0.1", "0.5", "0.9")},
                "spread_quantiles": {q: float(np.quantile(spq, float(q))) for q in ("0.1", "0.5", "0.9")},
                "accepted_fraction_at_tol": float(np.mean(spq <= args.sur_tol)),
+               "calibration_by_tol": calib,
+               "break_even_accepted_cells": ms_inf / mixed_ms,
+               "break_even_note": "the surrogate path beats the mixed path only if the accepted fraction of cells "
+                                  "exceeds network time / mixed time (above 1: never)",
                "sample": f"{nchk} cells x {G} grains vs the mixed path"}
         del Xs, lnp, lnj, spr, jm
         paths["surrogate"] = {"spectra_per_s": cells * G / (ms_s / 1e3), "ms_per_step": ms_s,
