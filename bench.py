@@ -326,10 +326,17 @@ def single_cell_section(dev, stream):
         e1.record(s)
         torch.cuda.synchronize(dev)
         graph_us = e0.elapsed_time(e1) * 1e3 / reps
-        out["paths"][name] = {"eager_us_per_solve": eager_us, "graph_us_per_solve": graph_us,
-                              "graph_kernel_nodes": g.kernel_nodes(),
-                              "spectra_per_s_graph": wl.n_grains / (graph_us * 1e-6)}
+        nodes = g.kernel_nodes()
         g.close()
+        heat.heat_get_timing(ctx, reset=True)  # per-kernel-class times of eager solves
+        for _ in range(reps):
+            heat.heat_solve(ctx, heat.heat_default_opts(build=b, emis=e, j_dtype=heat.HEAT_F32, timing=1), P, j, sh)
+        heat.heat_sync(ctx)
+        kt = heat.heat_get_timing(ctx, reset=True)
+        out["paths"][name] = {"eager_us_per_solve": eager_us, "graph_us_per_solve": graph_us,
+                              "graph_kernel_nodes": nodes,
+                              "spectra_per_s_graph": wl.n_grains / (graph_us * 1e-6),
+                              "kernels_us_per_solve": {k: v[0] * 1e3 / reps for k, v in kt.items() if v[1]}}
     heat.heat_sync(ctx)
     heat.heat_destroy(ctx)
     return out

@@ -52,6 +52,8 @@ struct heat_ctx {
     bool has_w = false;
     long long band_per_cell = 0;
     int max_bins = 0;
+    int band_max = 0;  // largest band (elements per cell) of one grain
+    int wmax_all = 1;  // widest band row over the grains
     std::vector<int> grain_order, grain_order_build;  // task orders of the recursion and the build
     std::vector<long long> grain_band;                // band elements per cell of each grain
     std::vector<int> grain_rows;                      // bins of each grain

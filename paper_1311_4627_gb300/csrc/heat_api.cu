@@ -446,6 +446,8 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
             if (!diag_in_band) jlo = f - 1;
             row_e[f] = (int)(band_total + band);
             row_jlo[f] = jlo;
+            if (f > 1 && jlo < row_jlo[f - 1])  // the recursion kernels rely on band starts never decreasing
+                return ctx->fail(HEAT_EINVAL, "heat_set_grains: band starts decrease (non-monotonic enthalpies?)");
             wmax[g] = std::max(wmax[g], f - jlo);
             diag_e[off + f - 1] = (int)(band_total + band + (f - 1 - jlo));
             diag_ok[off + f - 1] = diag_in_band ? 1 : 0;
@@ -569,6 +571,9 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
         rent.insert(rent.end(), 128, pad);
     }
     ctx->band_per_cell = band_total;
+    ctx->band_max = 0;
+    ctx->wmax_all = *std::max_element(wmax.begin(), wmax.end());
+    for (int g = 0; g < G; ++g) ctx->band_max = std::max(ctx->band_max, (int)ctx->grain_band[g]);
     ctx->max_bins = 0;
     for (int g = 0; g < G; ++g) ctx->max_bins = std::max(ctx->max_bins, bin_offset[g + 1] - bin_offset[g]);
     order_grains(ctx);
@@ -893,6 +898,8 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
     gd.wmax = ctx->d_wmax.as<int>();
     gd.band_total = ctx->band_per_cell;
     gd.max_bins = ctx->max_bins;
+    gd.band_max = ctx->band_max;
+    gd.wmax_all = ctx->wmax_all;
     gd.seg_ptr = ctx->d_seg_ptr.as<int>();
     gd.pat64 = ctx->d_pat64.as<PatF64>();
     gd.pat32 = ctx->d_pat32.as<PatF32>();
@@ -1413,6 +1420,8 @@ __attribute__((visibility("hidden"))) heat_status heat_internal_grain_view(heat_
     gd->wmax = ctx->d_wmax.as<int>();
     gd->band_total = ctx->band_per_cell;
     gd->max_bins = ctx->max_bins;
+    gd->band_max = ctx->band_max;
+    gd->wmax_all = ctx->wmax_all;
     gd->seg_ptr = ctx->d_seg_ptr.as<int>();
     gd->pat64 = ctx->d_pat64.as<PatF64>();
     gd->pat32 = ctx->d_pat32.as<PatF32>();

@@ -46,6 +46,8 @@ struct GrainDev {
     const int* wmax;        // [G] widest band row of grain g (selects the recursion's window size)
     long long band_total;   // band elements of all grains (per cell)
     int max_bins;           // largest bins per grain
+    int band_max;           // largest band (elements per cell) of one grain
+    int wmax_all;           // widest band row over the grains
     const int* seg_ptr;     // [G][N+1] pattern entries of grain g in segment n at
                             //   seg_ptr[g*(N+1)+n] .. seg_ptr[g*(N+1)+n+1]
     const PatF64* pat64;    // pattern entries (FP64 build)
@@ -131,6 +133,8 @@ constexpr int kGthThreads = 256;
 constexpr int kGthSmemBins = 160;
 size_t gth_smem_bytes(int max_bins);
 size_t td_fill_smem_bytes(int N);
+// Shared memory per block of the few-cell recursion up to which the band is staged there.
+constexpr size_t kSmallRecurStage = 100 * 1024;
 constexpr int kDiscreteMaxBins = 2048;                // the state reduction's vectors in shared memory
 constexpr size_t kMaxSmemPerBlock = 227 * 1024;       // opt-in dynamic shared memory per block
 // Spectra are solved in launches of `batch` (rate matrices at q + k * qstride): the k-th

@@ -2,7 +2,8 @@
 //   j[c][g][n] = sum_i P[c][off_g + i] K[off_g + i][n],   K = C_abs B_lambda(T_i) [E_i >= hc/lambda_n],
 // and the size-integrated form over the concatenated bins with K scaled by w_g (Eq. convolution).
 // Register-tiled SIMT GEMM on the FP64 FMA pipe: 64 x 64 output tile per block,
-// 16-deep k slices staged in shared memory, 4 x 4 outputs per thread.
+// 16-deep k slices staged in shared memory, 4 x 4 outputs per thread; a thread-per-output
+// form for few rows.
 #include "common.cuh"
 #include "internal.h"
 
@@ -65,9 +66,33 @@ __global__ void __launch_bounds__(256, 2) k_gemm_f64(int M, int N, const int* __
     }
 }
 
+// Few rows (solves of few cells): a thread per output, threads along n (coalesced rows of K),
+// one accumulator in ascending k as in k_gemm_f64, so both give the same bits; the 64-row
+// tile above would spend 64 FMAs per useful one on a single cell.
+template <typename TC>
+__global__ void __launch_bounds__(128) k_gemv_f64(int N, const int* __restrict__ koff, const double* __restrict__ A,
+                                                  long long lda, const double* __restrict__ B, long long ldb,
+                                                  TC* __restrict__ C, long long ldc, long long zs) {
+    const int z = blockIdx.z, m = blockIdx.y, n = blockIdx.x * 128 + threadIdx.x;
+    if (n >= N) return;
+    const int k0 = koff[z], k1 = koff[z + 1];
+    const double* a = A + (size_t)m * lda;
+    double acc = 0.0;
+    for (int k = k0; k < k1; ++k) acc = fma(a[k], B[(size_t)k * ldb + n], acc);
+    C[(size_t)z * zs + (size_t)m * ldc + n] = (TC)acc;
+}
+
 cudaError_t launch_gemm_f64(int M, int N, int nz, const int* koff, const double* A, long long lda, const double* B,
                             long long ldb, void* C, long long ldc, long long zstride_c, int c_is_f32, cudaStream_t st) {
     if (M <= 0 || N <= 0 || nz <= 0) return cudaSuccess;
+    if (M <= kSmallCells) {
+        dim3 g1((N + 127) / 128, M, nz);
+        if (c_is_f32)
+            k_gemv_f64<float><<<g1, 128, 0, st>>>(N, koff, A, lda, B, ldb, (float*)C, ldc, zstride_c);
+        else
+            k_gemv_f64<double><<<g1, 128, 0, st>>>(N, koff, A, lda, B, ldb, (double*)C, ldc, zstride_c);
+        return cudaGetLastError();
+    }
     dim3 grid((N + 63) / 64, (M + 63) / 64, nz);
     if (c_is_f32)
         k_gemm_f64<float><<<grid, 256, 0, st>>>(M, N, koff, A, lda, B, ldb, (float*)C, ldc, zstride_c);

@@ -1,7 +1,9 @@
 // The Guhathakurta-Draine recursion (Eq. xf) and renormalisation (Eq. renormalization) over
 // the B band that the build wrote: a persistent lane-per-cell kernel (warp = grain x 32 cells,
-// one FP64 FMA per band element and cell, no divergence, no cross-lane reductions) and an
-// element-parallel kernel for solves of few cells.
+// one FP64 FMA per band element and cell, no divergence, no cross-lane reductions) and a
+// warp-per-spectrum column sweep for solves of few cells.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 #include "pack.cuh"
@@ -408,89 +410,209 @@ __global__ void __launch_bounds__(128, 4) k_recur(GrainDev gd, ChunkDev ch) {
 }
 
 // ---------------------------------------------------------------------------
-// Element-parallel recursion for solves of few cells (ChunkDev::small): the same recursion,
-// rescale, normalisation and pruning as k_recur; each row is summed across lanes, so its
-// rounding differs from the lane-per-cell kernel's.
+// Recursion for solves of few cells (ChunkDev::small), one block per spectrum: a column
+// sweep.  Once X_j is final, every later row f whose band holds j takes B_fj X_j into its
+// accumulator, so each row's sum runs in ascending j as in k_recur, and the chain from one X
+// to the next is one FMA, the multiply by 1/T_{f-1,f} and a broadcast instead of a row's dot
+// product and a cross-lane reduction.  Thread t of the T threads owns rows t, t + T, ...; a
+// thread has up to K rows in progress (T above the grain's widest band row and K = 1, one warp
+// needing no barrier; or T = 1024 and K = 4); each row in progress keeps in registers its accumulator, its band start
+// and element offset, 1/T_{f-1,f} and the B value of the next column (loaded a step ahead),
+// and the thread's following rows are loaded a run of 32 columns ahead (off the column chain).
+// The thread that completes row j + 1 multiplies, stores X_{j+1} and broadcasts it (a shuffle
+// when T = 32, else a shared slot, double-buffered, and one barrier per column).  Rescales
+// apply at once to the history, the accumulators and the running sum (exact powers of two);
+// normalisation, pruning and the energy check as in k_recur.  The band is staged in shared
+// memory when the launch gives room for the largest grain's (`staged`).
+template <int BUILD>
+struct SmallRow {
+    int f, jl, rs;  // row, band start, element of column j at rs + j
+    double ic, acc, b;
+};
+struct SmallRowRaw {  // a row's loads, not yet used (so that nothing waits on them)
+    int f, p0, p1;
+    double ic;
+};
 
-// Warp per spectrum, lanes over each row's band; X history in shared memory
-// (dynamic: max_bins doubles per warp).  Same recursion (Eq. xf), rescale, normalisation and
-// tail pruning as k_recur; each row's sum is reduced across lanes.
-template <int BUILD, bool PRUNE>
-__global__ void __launch_bounds__(128) k_recur_small(GrainDev gd, ChunkDev ch) {
+template <int BUILD, bool PRUNE, int K, bool WARP>
+__global__ void __launch_bounds__(WARP ? 32 : 1024, 1) k_recur_small(GrainDev gd, ChunkDev ch, int staged) {
+    using Raw = BandRaw<BUILD>;
     extern __shared__ double smx[];
-    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (w >= ch.cells * gd.G) return;
-    double* xs = smx + (size_t)(threadIdx.x >> 5) * gd.max_bins;
-    const int cell = w / gd.G, g = w % gd.G;
+    __shared__ double bc[2];  // broadcast: X_{j+1} and the width of its row (double-buffered)
+    __shared__ int bcw[2];
+    const int T = WARP ? 32 : blockDim.x, tid = threadIdx.x;
+    const bool one_warp = WARP;
+    const int sp = blockIdx.x;
+    const int cell = sp / gd.G, g = sp % gd.G;
     const int grp = cell >> 5, lc = cell & 31;
     const int off = gd.bin_off[g];
     const int M = gd.bin_off[g + 1] - off - 1;
+    double* xs = smx;  // X history [max_bins]
+    typename Raw::T* bs = (typename Raw::T*)(xs + gd.max_bins);
     const int* rp = gd.rowptr + off + g;
     const double* ic_row = gd.invC + off;
     const size_t bb = (size_t)grp * gd.band_total * 32 + lc;
     const float* B32 = ch.Bb32 + (BUILD ? bb : 0);
     const double* B64 = ch.Bb64 + (BUILD ? 0 : bb);
+    const int ebeg = rp[1];
+    if (staged) {  // eight independent loads in flight per thread
+        const int nel = rp[M + 1] - ebeg;
+        for (int e0 = tid; e0 < nel; e0 += 8 * T) {
+            typename Raw::T v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = e0 + u * T < nel ? Raw::load(B32, B64, ebeg + e0 + u * T) : 0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (e0 + u * T < nel) bs[e0 + u * T] = v[u];
+        }
+    }
+    if (tid == 0) xs[0] = 1.0;
+    __syncthreads();
+    auto bval = [&](int e) -> double { return staged ? Raw::wide(bs[e]) : band_b<BUILD>(B32, B64, e); };
+    auto load_row = [&](int f) {  // row f's loads (unconditional: rows past M load row M's, unused)
+        SmallRowRaw r;
+        const int fc = f <= M ? f : M;
+        r.f = f;
+        r.p0 = rp[fc];
+        r.p1 = rp[fc + 1];
+        r.ic = ic_row[fc];
+        return r;
+    };
+    auto open_row = [&](const SmallRowRaw& q) {  // the row in progress, from its loads
+        SmallRow<BUILD> r;
+        r.f = q.f;
+        r.acc = 0.0;
+        r.b = 0.0;
+        r.ic = q.f <= M ? q.ic : 0.0;
+        r.jl = q.f <= M ? q.f - (q.p1 - q.p0) : 1 << 30;
+        r.rs = q.p0 - (q.f - (q.p1 - q.p0)) - (staged ? ebeg : 0);
+        return r;
+    };
+    // Rows: row[] in progress, nxt the one after them (opened), raw the one after that (its
+    // loads in flight).  A warp completes rows in runs of 32 columns (lane 0 .. 31); at the end
+    // of its run every lane opens raw as nxt and loads the next raw, so no lane reads a
+    // register whose load another lane of the warp has just issued (the scoreboard is per warp).
+    SmallRow<BUILD> row[K];
+    int fnext = tid == 0 ? T : tid;  // row 0 is given (X_0 = 1)
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        row[k] = open_row(load_row(fnext));
+        fnext += T;
+    }
+    SmallRow<BUILD> nxt = open_row(load_row(fnext));
+    fnext += T;
+    SmallRowRaw raw = load_row(fnext);
+    fnext += T;
+    const int warp = tid >> 5;
+    bool used = false;  // nxt was taken in this run
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        if (row[k].jl <= 0 && 0 < row[k].f) row[k].b = bval(row[k].rs);
     bool numeric_bad = false;
-    if (lane == 0) xs[0] = 1.0;
-    double total = 1.0;
+    // X = X_j, the value being spread (uniform); the running sum of X is kept by thread 0 alone
+    // (the same additions in the same order as k_recur), off the other warps' FP64 units
+    double total = 1.0, X = 1.0;
     const int* kx = gd.kexp + off;
     const int L = ch.prune;
     int xmax = 1023, cmax = PRUNE ? 1023 + kx[0] : 0, last_big = 0, f_last = M, shift = 0;
-    __syncwarp();
-    for (int f = 1; f <= M; ++f) {
-        const int e0 = rp[f], width = rp[f + 1] - e0, j0 = f - width;
-        double s = 0.0;
-        for (int k = lane; k < width; k += 32) s = fma(band_b<BUILD>(B32, B64, e0 + k), xs[j0 + k], s);
-        if (width > 1)
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        const double S = __shfl_sync(0xffffffffu, s, 0);
-        const double ic = ic_row[f];
-        double X = S * ic;
-        if (__double2hiint(ic) == 0 && __double2loint(ic) == 0) {
-            X = 0.0;
-            if (__double_as_longlong(S) != 0) numeric_bad = true;  // S >= 0
+    for (int j = 0; j < M; ++j) {
+        const int f1 = j + 1;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            SmallRow<BUILD>& r = row[k];
+            const bool act = r.jl <= j && j < r.f;
+            const bool act_next = r.jl <= j + 1 && j + 1 < r.f;
+            if (K == 1 || __any_sync(0xffffffffu, act || act_next)) {  // no predicated-off FMA on the FP64 unit
+                if (act) r.acc = fma(r.b, X, r.acc);
+                if (act_next) r.b = bval(r.rs + j + 1);
+            }
         }
-        if (lane == 0) xs[f] = X;
-        total += X;
+        double Xn = 0.0;
+        int wn = 0;
+        if (row[0].f == f1) {  // this thread completes row j + 1
+            const double S = row[0].acc;
+            Xn = S * row[0].ic;
+            if (__double2hiint(row[0].ic) == 0 && __double2loint(row[0].ic) == 0) {
+                Xn = 0.0;
+                if (__double_as_longlong(S) != 0) numeric_bad = true;  // S >= 0
+            }
+            wn = f1 - row[0].jl;
+            xs[f1] = Xn;
+            if (!one_warp) {
+                bc[j & 1] = Xn;
+                bcw[j & 1] = wn;
+            }
+#pragma unroll
+            for (int k = 0; k + 1 < K; ++k) row[k] = row[k + 1];
+            row[K - 1] = nxt;
+            used = true;
+            if (row[K - 1].jl <= j + 1 && j + 1 < row[K - 1].f) row[K - 1].b = bval(row[K - 1].rs + j + 1);
+        }
+        if ((f1 & 31) == 31 && ((f1 % T) >> 5) == warp && used) {  // this warp's run ends: refresh
+            nxt = open_row(raw);
+            raw = load_row(fnext);
+            fnext += T;
+            used = false;
+        }
+        if (one_warp) {
+            Xn = __shfl_sync(0xffffffffu, Xn, f1 & 31);
+            wn = __shfl_sync(0xffffffffu, wn, f1 & 31);
+        } else {
+            __syncthreads();
+            Xn = bc[j & 1];
+            wn = bcw[j & 1];
+        }
+        if (tid == 0) total += Xn;
         bool stop = false;
-        if (PRUNE) {  // the same test as k_recur, on lane-uniform values
-            const int xe = ((__double2hiint(X) >> 20) & 0x7ff) + shift;
-            const int ce = xe + kx[f];
+        if (PRUNE) {  // the same test as k_recur, on uniform values
+            const int xe = ((__double2hiint(Xn) >> 20) & 0x7ff) + shift;
+            const int ce = xe + kx[f1];
             xmax = max(xmax, xe);
             cmax = max(cmax, ce);
-            if (!(xe < xmax - L && ce < cmax - L)) last_big = f;
-            stop = last_big < f - width;
+            if (!(xe < xmax - L && ce < cmax - L)) last_big = f1;
+            stop = last_big < f1 - wn;
         }
-        if (above_rescale(X)) {
-            __syncwarp();
-            for (int i = lane; i <= f; i += 32) xs[i] = scale_down_800(xs[i], 1);
-            total = scale_down_800(total, 1);
+        if (above_rescale(Xn)) {
+            if (one_warp) __syncwarp(); else __syncthreads();  // xs[f1] is stored
+            for (int i = tid; i <= f1; i += T) xs[i] = scale_down_800(xs[i], 1);
+#pragma unroll
+            for (int k = 0; k < K; ++k) row[k].acc = scale_down_800(row[k].acc, 1);
+            if (tid == 0) total = scale_down_800(total, 1);
+            Xn = scale_down_800(Xn, 1);
             shift += 800;
         }
-        __syncwarp();
+        X = Xn;
         if (stop) {
-            f_last = f;
+            f_last = f1;
             break;
         }
     }
-    const double inv = 1.0 / total;
+    __shared__ double total_s;
+    if (tid == 0) total_s = total;
+    __syncthreads();
+    const double inv = 1.0 / total_s;
     double* prow = ch.P + (size_t)cell * ch.ldP + off;
     double emit = 0.0;
-    for (int i = lane; i <= M; i += 32) {
+    for (int i = tid; i <= M; i += T) {
         const double p = i <= f_last ? xs[i] * inv : 0.0;
         prow[i] = p;
         emit = fma(p, gd.cde[off + i], emit);
     }
     if (ch.ledger) {
         for (int o = 16; o > 0; o >>= 1) emit += __shfl_xor_sync(0xffffffffu, emit, o);
-        if (lane == 0) {
+        __shared__ double wsum[32];
+        if ((tid & 31) == 0) wsum[tid >> 5] = emit;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < (T >> 5); ++w) t += wsum[w];
             double* lg = ch.ledger + ((size_t)cell * gd.G + g) * 2;
             lg[0] = ch.pabs[(size_t)cell * gd.G + g];
-            lg[1] = emit;
+            lg[1] = t;
         }
     }
-    if (numeric_bad && lane == 0) atomicOr(ch.status, kStatNumeric);
+    numeric_bad = __syncthreads_or(numeric_bad);
+    if (numeric_bad && tid == 0) atomicOr(ch.status, kStatNumeric);
 }
 
 // Blocks of 128 threads (a warp per task) for the task-list kernels: one per 4 tasks, or, for
@@ -511,17 +633,37 @@ static unsigned task_grid(K kernel, const ChunkDev& ch) {
 
 cudaError_t launch_recur(const GrainDev& g, const ChunkDev& ch, int build, cudaStream_t st) {
     if (ch.small) {
-        const long long warps = (long long)ch.cells * g.G;
-        if (warps == 0) return cudaSuccess;
-        const size_t smem = sizeof(double) * 4 * (size_t)g.max_bins;  // 4 warps per block
-        auto kern = build == 0 ? (ch.prune ? k_recur_small<0, true> : k_recur_small<0, false>)
-                               : (ch.prune ? k_recur_small<1, true> : k_recur_small<1, false>);
+        const long long spectra = (long long)ch.cells * g.G;
+        if (spectra == 0) return cudaSuccess;
+        // a multiple of 32 threads above the widest band row (one row in progress per thread;
+        // one warp needs no block barrier per column), at most 1024 (then up to four rows per
+        // thread).  Measured on the single cell (rows up to 127 wide): one warp with four rows
+        // per lane, 97 us; four warps with one, 57 us (the FP64 unit of one sub-partition would
+        // carry every row's FMA)
+        const int wm = g.wmax_all;
+        const int T1 = (wm + 1 + 31) / 32 * 32;
+        const bool warp = T1 == 32;
+        const int T = std::min(1024, T1);
+        const int K = T1 > 1024 ? 4 : 1;
+        const size_t base = sizeof(double) * (size_t)g.max_bins;
+        const size_t band = (build == 0 ? sizeof(double) : sizeof(float)) * (size_t)g.band_max;
+        const int staged = base + band <= kSmallRecurStage ? 1 : 0;
+        const size_t smem = base + (staged ? band : 0);
+        using KernT = void (*)(GrainDev, ChunkDev, int);
+        KernT kern = nullptr;
+#define HEAT_SMALL_PICK(B, P) \
+    kern = warp ? k_recur_small<B, P, 1, true> : (K == 1 ? k_recur_small<B, P, 1, false> : k_recur_small<B, P, 4, false>)
+        if (build == 0) {
+            if (ch.prune) HEAT_SMALL_PICK(0, true); else HEAT_SMALL_PICK(0, false);
+        } else {
+            if (ch.prune) HEAT_SMALL_PICK(1, true); else HEAT_SMALL_PICK(1, false);
+        }
+#undef HEAT_SMALL_PICK
         if (smem > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
-        const unsigned blocks = (unsigned)((warps + 3) / 4);
-        kern<<<blocks, 128, smem, st>>>(g, ch);
+        kern<<<(unsigned)spectra, T, smem, st>>>(g, ch, staged);
         return cudaGetLastError();
     }
     if (ch.n_tasks == 0) return cudaSuccess;
