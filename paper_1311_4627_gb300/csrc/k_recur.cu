@@ -266,40 +266,42 @@ __device__ __forceinline__ void recur_task(const GrainDev& gd, const ChunkDev& c
         double S = 0.0;
         if (e < e_mem) {
             int j = f - width;
-            // batches of 8 elements, two register sets: the loads of the next batch are in
-            // flight while this batch's FMAs run (no register copy waits on a load)
-            const int nb = (e_mem - e) >> 3;
+            // batches of 4 elements, two register sets: the loads of the next batch are in
+            // flight while this batch's FMAs run (no register copy waits on a load).  Batches of
+            // 4 leave room for 5 resident blocks per SM (20 warps): 6.36 -> 6.27 ms on the
+            // batched workload against batches of 8 at 4 blocks (8 at 5 blocks spills: 7.45 ms)
+            const int nb = (e_mem - e) >> 2;
             if (nb > 0) {
-                typename Raw::T bA[8], bB[8];
-                double xA[8], xB[8];
+                typename Raw::T bA[4], bB[4];
+                double xA[4], xB[4];
 #pragma unroll
-                for (int k = 0; k < 8; ++k) bA[k] = Raw::load(B32, B64, e + k);
+                for (int k = 0; k < 4; ++k) bA[k] = Raw::load(B32, B64, e + k);
 #pragma unroll
-                for (int k = 0; k < 8; ++k) xA[k] = xl[(j + k) * 32];
+                for (int k = 0; k < 4; ++k) xA[k] = xl[(j + k) * 32];
                 int i = 0;
                 for (; i + 2 <= nb; i += 2) {
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) bB[k] = Raw::load(B32, B64, e + 8 + k);
+                    for (int k = 0; k < 4; ++k) bB[k] = Raw::load(B32, B64, e + 4 + k);
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) xB[k] = xl[(j + 8 + k) * 32];
+                    for (int k = 0; k < 4; ++k) xB[k] = xl[(j + 4 + k) * 32];
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) S = fma(Raw::wide(bA[k]), xA[k], S);
+                    for (int k = 0; k < 4; ++k) S = fma(Raw::wide(bA[k]), xA[k], S);
                     if (i + 2 < nb) {
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) bA[k] = Raw::load(B32, B64, e + 16 + k);
+                        for (int k = 0; k < 4; ++k) bA[k] = Raw::load(B32, B64, e + 8 + k);
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) xA[k] = xl[(j + 16 + k) * 32];
+                        for (int k = 0; k < 4; ++k) xA[k] = xl[(j + 8 + k) * 32];
                     }
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) S = fma(Raw::wide(bB[k]), xB[k], S);
-                    e += 16;
-                    j += 16;
+                    for (int k = 0; k < 4; ++k) S = fma(Raw::wide(bB[k]), xB[k], S);
+                    e += 8;
+                    j += 8;
                 }
                 if (i < nb) {
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) S = fma(Raw::wide(bA[k]), xA[k], S);
-                    e += 8;
-                    j += 8;
+                    for (int k = 0; k < 4; ++k) S = fma(Raw::wide(bA[k]), xA[k], S);
+                    e += 4;
+                    j += 4;
                 }
             }
             for (; e < e_mem; ++e, ++j) S = fma(band_b<BUILD>(B32, B64, e), xl[j * 32], S);
@@ -396,7 +398,7 @@ __device__ __forceinline__ void recur_task(const GrainDev& gd, const ChunkDev& c
 }
 
 template <int BUILD, bool PRUNE>
-__global__ void __launch_bounds__(128, 4) k_recur(GrainDev gd, ChunkDev ch) {
+__global__ void __launch_bounds__(128, 5) k_recur(GrainDev gd, ChunkDev ch) {
     for_each_task(ch, 1, [&](int task, int lane) {
         const int g = ch.tasks[task].x, grp = ch.tasks[task].y;
         const int wm = gd.wmax[g];  // warp-uniform
