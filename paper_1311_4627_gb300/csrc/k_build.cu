@@ -2,6 +2,8 @@
 // build (B band, Eq. bmatrix telescoped, intra-bin terms; or the point rule of Eq. heating
 // with the suffix sums of Eq. brecurrence), as lane-per-cell kernels (warp = grain x 32 cells)
 // and element-parallel kernels for solves of few cells.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -267,16 +269,22 @@ __device__ __forceinline__ SegF64 seg64(const GrainDev& gd, int g, int n, double
     return r;
 }
 
-// Block per (cell, grain): 256 threads, dynamic shared memory 2 N doubles.
+// Blocks per (cell, grain): S parts (256 threads each, dynamic shared memory 2 N doubles).
+// Every part forms the segment increments and the cumulative sums; part q writes the
+// elements of the segments n = q (mod S), and the intra-bin terms whose diagonal element it
+// wrote: the diagonal (j+1, j) and bin j's soft-photon edge are the same wavelength,
+// hc/(Elo_{j+1} - E_j), so both fall in segment sf.n (sf.n < 0: the diagonal is not in the
+// band, part 0).  Few spectra (a single cell) then spread over many SMs.
 template <int BUILD>
-__global__ void __launch_bounds__(256) k_build_small(GrainDev gd, ChunkDev ch) {
+__global__ void __launch_bounds__(256) k_build_small(GrainDev gd, ChunkDev ch, int S) {
     extern __shared__ double sm[];
     double* sPhi = sm;          // [N]: Phi before segment n (exclusive prefix), then Phi at the end
     double* sPsi = sm + gd.N;   // [N]: Psi after the segments above n (exclusive suffix)
     __shared__ double sPhiEnd, sPsiTot;
     __shared__ float sPsiEnd32;  // FP32 build: the FP32 value of the compensated total
     const int N = gd.N, Cc = ch.Cc;
-    const int cell = blockIdx.x / gd.G, g = blockIdx.x % gd.G;
+    const int spec = blockIdx.x / S, part = blockIdx.x % S;
+    const int cell = spec / gd.G, g = spec % gd.G;
     if (cell >= ch.cells) return;
     const int grp = cell >> 5, lc = cell & 31;
     const int off = gd.bin_off[g];
@@ -348,8 +356,8 @@ __global__ void __launch_bounds__(256) k_build_small(GrainDev gd, ChunkDev ch) {
         }
     }
     __syncthreads();
-    // 3. band elements: warp per segment, lanes over its pattern entries
-    for (int n = warp; n < N - 1; n += blockDim.x >> 5) {
+    // 3. band elements: warp per segment (this part's), lanes over its pattern entries
+    for (int n = part + S * warp; n < N - 1; n += S * (blockDim.x >> 5)) {
         const int k0 = sp[n], k1 = sp[n + 1];
         if (k0 == k1) continue;
         if (BUILD == 0) {
@@ -375,16 +383,18 @@ __global__ void __launch_bounds__(256) k_build_small(GrainDev gd, ChunkDev ch) {
             }
         }
     }
-    for (int k = sp[N - 1] + tid; k < sp[N]; k += blockDim.x) {
-        if (BUILD == 0)
-            ch.Bb64[bb + (size_t)gd.pat64[k].e * 32] = sPhiEnd;
-        else
-            ch.Bb32[bb + (size_t)gd.pat32[k].e * 32] = __double2float_rn(sPhiEnd);
-    }
-    __syncthreads();  // the intra-bin terms add to diagonal elements written above
+    if ((N - 1) % S == part)
+        for (int k = sp[N - 1] + tid; k < sp[N]; k += blockDim.x) {
+            if (BUILD == 0)
+                ch.Bb64[bb + (size_t)gd.pat64[k].e * 32] = sPhiEnd;
+            else
+                ch.Bb32[bb + (size_t)gd.pat32[k].e * 32] = __double2float_rn(sPhiEnd);
+        }
+    __syncthreads();  // the intra-bin terms add to diagonal elements written above (by this part)
     // 4. intra-bin terms, one per soft entry (each has its own diagonal element)
     for (int p = gd.soft_off[g] + tid; p < gd.soft_off[g + 1]; p += blockDim.x) {
         const SoftF64 sf = gd.soft[p];
+        if ((sf.n < 0 ? 0 : sf.n % S) != part) continue;
         if (BUILD == 0) {
             double v = 0.0;
             if (sf.n == N - 1) {
@@ -426,7 +436,7 @@ __global__ void __launch_bounds__(256) k_build_small(GrainDev gd, ChunkDev ch) {
             *q = (sf.diag_in_band ? *q : 0.0f) + v;
         }
     }
-    if (tid == 0 && ch.pabs) ch.pabs[(size_t)cell * gd.G + g] = BUILD == 0 ? kC * sPsiTot : sPsiTot;
+    if (tid == 0 && part == 0 && ch.pabs) ch.pabs[(size_t)cell * gd.G + g] = BUILD == 0 ? kC * sPsiTot : sPsiTot;
 }
 
 // ---------------------------------------------------------------------------
@@ -538,8 +548,13 @@ cudaError_t launch_build(const GrainDev& g, const ChunkDev& ch, int build, cudaS
     }
     if (ch.small) {
         const size_t smem = sizeof(double) * 2 * (size_t)g.N;
-        const unsigned blocks = (unsigned)(ch.cells * g.G);
-        if (blocks == 0) return cudaSuccess;
+        const long long spectra = (long long)ch.cells * g.G;
+        if (spectra == 0) return cudaSuccess;
+        // parts per spectrum: about two blocks per SM in all (one part when spectra suffice)
+        int dev = 0, sms = 152;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int S = (int)std::max(1LL, std::min(16LL, 2LL * sms / spectra));
+        const unsigned blocks = (unsigned)(spectra * S);
         if (smem > 48 * 1024) {
             cudaError_t e = build == 0 ? cudaFuncSetAttribute(k_build_small<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                               (int)smem)
@@ -548,9 +563,9 @@ cudaError_t launch_build(const GrainDev& g, const ChunkDev& ch, int build, cudaS
             if (e != cudaSuccess) return e;
         }
         if (build == 0)
-            k_build_small<0><<<blocks, 256, smem, st>>>(g, ch);
+            k_build_small<0><<<blocks, 256, smem, st>>>(g, ch, S);
         else
-            k_build_small<1><<<blocks, 256, smem, st>>>(g, ch);
+            k_build_small<1><<<blocks, 256, smem, st>>>(g, ch, S);
         return cudaGetLastError();
     }
     if (ch.n_tasks == 0) return cudaSuccess;
