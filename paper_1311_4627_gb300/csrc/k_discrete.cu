@@ -19,6 +19,8 @@
 //       fused multiply-adds per spectrum, on the FP64 unit: one block per spectrum, states
 //       removed eight at a time with one delayed rank-8 update of the rest (q in shared memory
 //       up to 160 bins, else in device memory, read and written once per eight states).
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -236,14 +238,16 @@ size_t td_fill_smem_bytes(int N) { return sizeof(double) * 4 * (size_t)N + sizeo
 // Spectrum of block b of a launch that starts at spectrum s0: grains in the order `gorder`
 // (most bins first), every cell of the chunk for each grain in turn, so that the spectra of one
 // launch have similar cost and the largest start first.
-__device__ __forceinline__ void td_spectrum(const ChunkDev& ch, const int* gorder, long long s0, int& cell, int& g) {
-    const long long sp = s0 + blockIdx.x;
+__device__ __forceinline__ void td_spectrum(const ChunkDev& ch, const int* gorder, long long s0, int& cell, int& g,
+                                            int b = -1) {
+    const long long sp = s0 + (b < 0 ? (int)blockIdx.x : b);
     cell = (int)(sp % ch.cells);
     g = gorder[sp / ch.cells];
 }
 
-// One block per spectrum (cell, grain) of the chunk's cells: q [nb][nb] (row-major, rate from
-// row to column) at q + block * qstride, and the absorbed power c int Omega on the grid.
+// S blocks per spectrum (cell, grain) of the chunk's cells, each the rows i = part (mod S): q
+// [nb][nb] (row-major, rate from row to column) at q + spectrum * qstride, and the absorbed
+// power c int Omega on the grid (part 0).
 // Downward rates are copied from the grain's table (Dt[u][l], from u to l).  The heating
 // rate from i into bin j > i is (1/h) int Omega lambda over the photon wavelengths that end in
 // bin j, [hc/(Ehi_j - E_i), hc/(Elo_j - E_i)] (Ehi_M = infinity), plus on j = i + 1 the
@@ -255,10 +259,11 @@ __device__ __forceinline__ void td_spectrum(const ChunkDev& ch, const int* gorde
 // short-wavelength end of the grid.
 __global__ void __launch_bounds__(256) k_td_fill(GrainDev gd, ChunkDev ch, const double* __restrict__ Dt,
                                                  const long long* __restrict__ doff, const int* __restrict__ gorder,
-                                                 long long s0, double* q, long long qstride) {
+                                                 long long s0, double* q, long long qstride, int S) {
     extern __shared__ double fsm[];
+    const int bsp = blockIdx.x / S, part = blockIdx.x % S;  // spectrum of the launch, part of its rows
     int cell, g;
-    td_spectrum(ch, gorder, s0, cell, g);
+    td_spectrum(ch, gorder, s0, cell, g, bsp);
     const int N = gd.N;
     const double* lam = gd.lam;
     double* om = fsm;
@@ -304,10 +309,10 @@ __global__ void __launch_bounds__(256) k_td_fill(GrainDev gd, ChunkDev ch, const
     const int off = gd.bin_off[g], nb = gd.bin_off[g + 1] - off;
     const double* E = gd.E + off;
     const double* Dg = Dt + doff[g];
-    double* qs = q + (size_t)blockIdx.x * qstride;
+    double* qs = q + (size_t)bsp * qstride;
     const double lam0 = lam[0], lamN = lam[N - 1];
     const int M = nb - 1;
-    for (int i = warp; i < nb; i += nw) {
+    for (int i = part + S * warp; i < nb; i += S * nw) {
         double* qi = qs + (size_t)i * nb;
         const double* di = Dg + (size_t)i * nb;
         for (int j = lane; j <= i; j += 32) qi[j] = j < i ? di[j] : 0.0;
@@ -349,7 +354,7 @@ __global__ void __launch_bounds__(256) k_td_fill(GrainDev gd, ChunkDev ch, const
         }
         for (int j = jb + lane; j < nb; j += 32) qi[j] = 0.0;
     }
-    if (tid == 0 && ch.pabs) ch.pabs[(size_t)cell * gd.G + g] = kC * S0[0];
+    if (tid == 0 && part == 0 && ch.pabs) ch.pabs[(size_t)cell * gd.G + g] = kC * S0[0];
 }
 
 namespace {
@@ -597,7 +602,11 @@ cudaError_t launch_discrete_fill(const GrainDev& g, const ChunkDev& ch, const do
         cudaError_t e = cudaFuncSetAttribute(k_td_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_td_fill<<<(unsigned)n, 256, smem, st>>>(g, ch, D, doff, gorder, s0, q, qstride);
+    // parts per spectrum (rows by residue): about two blocks per SM when the launch has few spectra
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int S = (int)(n >= 2LL * sms ? 1 : std::min(16LL, std::max(1LL, 2LL * sms / n)));
+    k_td_fill<<<(unsigned)(n * S), 256, smem, st>>>(g, ch, D, doff, gorder, s0, q, qstride, S);
     return cudaGetLastError();
 }
 
