@@ -425,6 +425,7 @@ def thermal_discrete_section(dev):
         "ms_per_solve": ms, "kernels_ms_per_solve": kt,
         "roofline": {"kernel": "state reduction (k_gth)", "bound": "alu", "unit": "TFLOP/s",
                      "achieved": ach, "peak": FP64_PEAK_TFLOPS, "frac": ach / FP64_PEAK_TFLOPS,
+                     "frac_of_measured": ach / heat.heat_measure_fma_peak(dev.index, True),
                      "peak_source": "nominal dense FP64 1.25 TFLOP/s (profiling recipe table)",
                      "algorithmic_work": f"2 x cells x ((M-2)(M-1)M/3 + M(M-1)/2) = {work:.3e} FP64 flop per solve "
                                          "(reduction updates + back substitution)"}}
@@ -633,9 +634,12 @@ def main():
     # packed by the recursion's epilogue, so its region holds the GEMM alone)
     gpu_launches = int(sum(n for _, (_, n) in kt.items()))
 
-    # roofline of every kernel class, the dominant one as "roofline"
+    # roofline of every kernel class, the dominant one as "roofline"; the FP64-bound ones also
+    # against the FP64 FMA rate measured on this device now (the peaks file has none)
     nbt = wl.total_bins
     peaks, peaks_src = measured_peaks()
+    fp64_measured = heat.heat_measure_fma_peak(dev.index, True)
+    fp32_measured = heat.heat_measure_fma_peak(dev.index, False)
     rooflines = {}
     for name, (tot_ms, n_launch) in kt.items():
         if n_launch == 0:
@@ -665,6 +669,9 @@ def main():
             continue
         ach = work / per_step / (launch_ms / 1e3) / 1e12
         r.update({"kernel": name, "achieved": ach, "frac": ach / r["peak"], "traffic": None})
+        if r["bound"] == "alu" and fp64_measured:
+            r.update({"measured_peak": fp64_measured, "frac_of_measured": ach / fp64_measured,
+                      "measured_peak_source": "heat_measure_fma_peak: independent DFMA chains on every SM, this run"})
         rooflines[name] = r
     dom = max(rooflines, key=lambda k: kt[k][0])
     roofline = dict(rooflines[dom])
@@ -678,7 +685,10 @@ def main():
                            band_elements_per_cell=band, grain_setup_s=round(setup_s, 3)),
             "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
             "roofline": roofline, "kernel_rooflines": rooflines, "clocks": clocks, "gpu_launches": gpu_launches,
-            "wall_s_timed_region": wall}
+            "wall_s_timed_region": wall,
+            "measured_fma_peaks_tflops": {"fp64": fp64_measured, "fp32": fp32_measured,
+                                          "how": "heat_measure_fma_peak (8 independent FMA chains per thread, "
+                                                 "full occupancy, fastest of 4 timed launches)"}}
 
     # the same solve captured once into a CUDA graph and replayed (heat_graph_*), L2 flushed
     # between replays as above

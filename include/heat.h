@@ -216,6 +216,13 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
  * (9/8) n_atoms k theta_D for T >> theta_D. */
 double heat_debye_enthalpy(double theta_D, double n_atoms, double T);
 
+/* Measured FMA throughput of `device` (a diagnostic for rooflines; no ctx): fp64 = 1 for FP64
+ * fused multiply-adds, 0 for FP32.  Runs independent FMA chains on every SM at full
+ * occupancy (a few ms of device time on the legacy stream, after the device's earlier work)
+ * and writes the rate in TFLOP/s (2 flop per FMA) to *tflops (host pointer).
+ * Errors: HEAT_EINVAL (null pointer, negative device), HEAT_ECUDA. */
+heat_status heat_measure_fma_peak(int device, int fp64, double* tflops);
+
 /* Set the radiation fields u_lambda[n_cells][n_lambda] (erg cm^-3 cm^-1, >= 0, finite),
  * element type `dtype` (HEAT_F64 or HEAT_F32).  on_device = 1: `u_lambda` is a device
  * pointer, borrowed until the solves that use it complete; on_device = 0: host memory

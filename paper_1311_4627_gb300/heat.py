@@ -109,6 +109,8 @@ def lib():
         L.heat_set_wait_limit.argtypes = [_vp, ctypes.c_longlong]
         L.heat_debye_enthalpy.restype = ctypes.c_double
         L.heat_debye_enthalpy.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        L.heat_measure_fma_peak.restype = ctypes.c_int
+        L.heat_measure_fma_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
         L.heat_solve_noalloc.restype = ctypes.c_int
         L.heat_solve_noalloc.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]
         for name, args in [
@@ -213,6 +215,15 @@ WAIT_POLLS_DEFAULT = 1 << 22
 
 def heat_set_wait_limit(ctx, polls):
     _check(ctx, lib().heat_set_wait_limit(ctx, int(polls)))
+
+
+def heat_measure_fma_peak(device: int = 0, fp64: bool = True) -> float:
+    """Measured FMA throughput of the device in TFLOP/s (FP64 or FP32)."""
+    v = ctypes.c_double(0.0)
+    st = lib().heat_measure_fma_peak(int(device), int(bool(fp64)), ctypes.byref(v))
+    if st != HEAT_OK:
+        raise HeatError(st, "heat_measure_fma_peak failed")
+    return v.value
 
 
 def heat_debye_enthalpy(theta_D: float, n_atoms: float, T) -> np.ndarray:

@@ -85,3 +85,4 @@ def test_wait_limit_rejects_negative_values(small):
     with pytest.raises(heat.HeatError) as ei:
         heat.heat_set_wait_limit(lib.ctx, -1)
     assert ei.value.status == heat.HEAT_EINVAL
+
