@@ -222,3 +222,28 @@ def test_small_solves_match_the_lane_per_cell_kernels(batched_sub, build):
     if build == heat.HEAT_BUILD_F64:
         r, ok = relerr(P_s, P_ref[5:17])
         assert ok and r <= EXACT_TOL, r
+
+
+def test_exact_single_cell_against_the_stored_oracle_values(single):
+    """The exact single-cell solve against tests/golden/single_cell_exact.txt (the oracle's
+    values, stored): P, j at every 8th wavelength and the emitted power of the energy ledger
+    (its absorbed column is the model's in the oracle, the physical c int u C on the GPU)."""
+    import os
+    import sys
+
+    import torch
+
+    gold = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    sys.path.insert(0, gold)
+    import make_golden
+
+    d = make_golden.read(os.path.join(gold, "single_cell_exact.txt"))
+    wl, _, _, _, lib = single
+    led = torch.zeros(1, wl.n_grains, 2, dtype=torch.float64, device="cuda")
+    Pg, jg = lib.solve(build=heat.HEAT_BUILD_F64, emis=heat.HEAT_EMIS_F64, j_dtype=heat.HEAT_F64,
+                       ledger_out=led.data_ptr())
+    for got, ref in ((Pg.ravel(), d["P"]), (jg[0][:, ::make_golden.J_STRIDE].ravel(), d["j_every8"]),
+                     (led.cpu().numpy()[0, :, 1], d["ledger"].reshape(-1, 2)[:, 1])):
+        r, ok = relerr(got, ref)
+        assert ok and r <= EXACT_TOL, r
+
