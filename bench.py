@@ -70,7 +70,7 @@ def parse():
     ap.add_argument("--sur-cells", type=int, default=16384, help="training cells for the surrogate (x 64 grains)")
     ap.add_argument("--sur-epochs", type=int, default=30)
     ap.add_argument("--sur-tol", type=float, default=1e-2, help="ensemble spread (ln j) above which a cell falls back")
-    ap.add_argument("--oracle-cells", type=int, default=24, help="cells in the oracle sample")
+    ap.add_argument("--oracle-cells", type=int, default=96, help="cells in the oracle sample (about 12 s on 16 cores)")
     ap.add_argument("--no-single-cell", action="store_true", help="skip the single-cell latency section")
     ap.add_argument("--no-point", action="store_true", help="skip the point-rule heating section")
     ap.add_argument("--no-emis-heavy", action="store_true",

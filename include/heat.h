@@ -341,7 +341,7 @@ heat_status heat_get_timing(heat_ctx* ctx, double* ms, long long* launches, int 
  * operands on the tensor cores, FP32 accumulation and FP32 master weights; masked MSE
  * (entries with j < 1e-6 of the spectrum's peak are left out) plus a one-sided square penalty
  * on masked entries predicted above that level; Adam.  Requires n_lambda to be a multiple of
- * 64 and FP64 device fields. */
+ * 64 and at most 4096, and FP64 device fields. */
 
 /* Create (or recreate) the surrogate of ctx: `members` ensemble members (1..8), weights
  * initialised from `seed`; grain_flag[n_grains] (host, or NULL = 0) is the composition input.

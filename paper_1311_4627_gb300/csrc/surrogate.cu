@@ -270,50 +270,70 @@ __global__ void k_ens_final(int rows, int N, int members, const float* __restric
 struct ZoPtrs {
     const float* z[8];
 };
-__global__ void k_ens_stats(int rows, int N, int members, ZoPtrs zo, const float* __restrict__ ym,
-                            const float* __restrict__ ys, const float* __restrict__ lnp, float* __restrict__ lnj,
-                            float* __restrict__ spread) {
-    __shared__ float red[256];
+// A thread holds the members' values of up to kEnsPer wavelengths in registers (one read of
+// the outputs, one write of ln j); the maxima are warp shuffles and one shared-memory pass.
+constexpr int kEnsPer = 4;
+__device__ __forceinline__ float block_max_f(float v, float* red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    float t = lane < nw ? red[lane] : -INFINITY;
+    for (int o = 16; o > 0; o >>= 1) t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, o));
+    return t;
+}
+template <int MAXM>
+__global__ void __launch_bounds__(1024) k_ens_stats(int rows, int N, int members, ZoPtrs zo,
+                                                    const float* __restrict__ ym, const float* __restrict__ ys,
+                                                    const float* __restrict__ lnp, float* __restrict__ lnj,
+                                                    float* __restrict__ spread) {
+    __shared__ float red[32];
     const int s = blockIdx.x;
     if (s >= rows) return;
+    const int T = blockDim.x;
     float* out = lnj + (size_t)s * N;
+    float v[kEnsPer][MAXM], mu[kEnsPer];
     float mx = -INFINITY;
-    for (int n = threadIdx.x; n < N; n += blockDim.x) {
-        float sum = 0.0f;
-        for (int m = 0; m < members; ++m) sum += zo.z[m][(size_t)s * N + n] * ys[n] + ym[n];
-        const float mu = sum / (float)members;
-        out[n] = mu;  // the mean for now; ln P_abs is added below
-        mx = fmaxf(mx, mu);
+#pragma unroll
+    for (int q = 0; q < kEnsPer; ++q) {
+        const int n = threadIdx.x + q * T;
+        mu[q] = 0.0f;
+        if (n < N) {
+            const float a = ys[n], b = ym[n];
+            float sum = 0.0f;
+#pragma unroll
+            for (int m = 0; m < MAXM; ++m)
+                if (m < members) {
+                    v[q][m] = zo.z[m][(size_t)s * N + n] * a + b;
+                    sum += v[q][m];
+                }
+            mu[q] = sum / (float)members;
+            mx = fmaxf(mx, mu[q]);
+        }
     }
-    red[threadIdx.x] = mx;
-    __syncthreads();
-    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
-        if (threadIdx.x < k) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + k]);
-        __syncthreads();
-    }
-    const float thr = red[0] + logf(kMaskRel);
-    __syncthreads();
+    const float thr = block_max_f(mx, red) + logf(kMaskRel);
     const float lp = lnp[s];
     float sp = 0.0f;
-    for (int n = threadIdx.x; n < N; n += blockDim.x) {
-        const float mu = out[n];
-        if (mu > thr && members > 1) {
-            float ss = 0.0f;
-            for (int m = 0; m < members; ++m) {
-                const float d = zo.z[m][(size_t)s * N + n] * ys[n] + ym[n] - mu;
-                ss += d * d;
+#pragma unroll
+    for (int q = 0; q < kEnsPer; ++q) {
+        const int n = threadIdx.x + q * T;
+        if (n < N) {
+            if (mu[q] > thr && members > 1) {
+                float ss = 0.0f;
+#pragma unroll
+                for (int m = 0; m < MAXM; ++m)
+                    if (m < members) {
+                        const float d = v[q][m] - mu[q];
+                        ss += d * d;
+                    }
+                sp = fmaxf(sp, sqrtf(ss / (float)(members - 1)));
             }
-            sp = fmaxf(sp, sqrtf(ss / (float)(members - 1)));
+            out[n] = mu[q] + lp;
         }
-        out[n] = mu + lp;
     }
-    red[threadIdx.x] = sp;
-    __syncthreads();
-    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
-        if (threadIdx.x < k) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + k]);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) spread[s] = red[0];
+    sp = block_max_f(sp, red);
+    if (threadIdx.x == 0) spread[s] = sp;
 }
 
 // j = exp(ln j) for the surrogate output; flags the cells with any grain above tol.
@@ -562,6 +582,7 @@ heat_status heat_surrogate_init(heat_ctx* ctx, int members, const float* grain_f
     if (ctx->G == 0) return ctx->fail(HEAT_ESTATE, "heat_surrogate_init: grains not set");
     if (members < 1 || members > 8) return ctx->fail(HEAT_EINVAL, "heat_surrogate_init: 1..8 members");
     if (ctx->N % 64) return ctx->fail(HEAT_EINVAL, "heat_surrogate_init: n_lambda must be a multiple of 64");
+    if (ctx->N > kEnsPer * 1024) return ctx->fail(HEAT_EINVAL, "heat_surrogate_init: at most 4096 wavelengths");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return HEAT_ECUDA;
     surrogate_free(ctx->sur);
     Surrogate* s = new (std::nothrow) Surrogate();
@@ -729,7 +750,9 @@ heat_status heat_surrogate_predict(heat_ctx* ctx, const float* X, const float* l
     Surrogate* s = ctx->sur;
     if (!s || !s->norm_ready) return ctx->fail(HEAT_ESTATE, "surrogate not trained");
     cudaStream_t st = (cudaStream_t)stream;
-    const int B = 16384;
+    // samples per pass: every pass launches 7 kernels and encodes 8 tensor maps per layer on
+    // the host, so passes are made large (the activations of 4 members: ~1.5 GB at 65536)
+    const int B = (int)std::min<long long>(65536, std::max<long long>(16384, n));
     heat_status h = ensure_batch(ctx, s, B);
     if (h != HEAT_OK) return h;
     // all members at once: per-member hidden activations (ping-pong) and standardised outputs
@@ -762,7 +785,9 @@ heat_status heat_surrogate_predict(heat_ctx* ctx, const float* X, const float* l
         }
         ZoPtrs zp{};
         for (int m = 0; m < s->members; ++m) zp.z[m] = s->Zo[m].as<float>();
-        k_ens_stats<<<cnt, 256, 0, st>>>(cnt, s->N, s->members, zp, s->ymean.as<float>(), s->ystd.as<float>(),
+        const int ens_threads = std::min(1024, ((s->N + kEnsPer - 1) / kEnsPer + 31) / 32 * 32);
+        auto ens = s->members <= 4 ? k_ens_stats<4> : k_ens_stats<8>;
+        ens<<<cnt, ens_threads, 0, st>>>(cnt, s->N, s->members, zp, s->ymean.as<float>(), s->ystd.as<float>(),
                                          lnp + b0, lnj + (size_t)b0 * s->N, spread + b0);
         SCK(cudaGetLastError());
     }
