@@ -336,7 +336,7 @@ heat_status heat_get_timing(heat_ctx* ctx, double* ms, long long* launches, int 
  * spectra the exact path computes, and the exact path stays its fallback.
  * Network per member: 128 inputs (ln of the power the grain absorbs in 64 wavelength bands,
  * ln radius, a composition flag, ln of the total absorbed power, zero padding; standardised
- * with training-set statistics) -> 4 hidden layers of 512 with GELU -> n_lambda outputs
+ * with training-set statistics) -> 4 hidden layers of 512 with GELU (tanh form) -> n_lambda outputs
  * y = ln j - ln P_abs (P_abs = c int u C dlambda, standardised per wavelength).  BF16
  * operands on the tensor cores, FP32 accumulation and FP32 master weights; masked MSE
  * (entries with j < 1e-6 of the spectrum's peak are left out) plus a one-sided square penalty

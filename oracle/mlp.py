@@ -2,7 +2,8 @@
 
 TEST INFRASTRUCTURE: it checks the gradients of the GPU training kernels.  Plain numpy in
 float64; the architecture follows the library's surrogate: layers W_l [out][in], b_l, GELU
-(exact, with erf) after every layer but the last, loss = mean over non-NaN targets of
+(its tanh form, x/2 (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3)))) after every layer but the
+last, loss = mean over non-NaN targets of
 (y - t)^2.  Parameters use the library's flat layout: for each layer W (row-major) then b.
 
 ``quantize`` (optional, e.g. ``bf16_round``) is applied where the GPU stores a value in a
@@ -18,20 +19,19 @@ import math
 
 import numpy as np
 
-try:
-    from scipy.special import erf as _erf
-except ImportError:  # pragma: no cover - scipy is present where the tests run
-    _erf = np.vectorize(math.erf)
-
-SQRT1_2 = 1.0 / math.sqrt(2.0)
+GELU_C = math.sqrt(2.0 / math.pi)
+GELU_A = 0.044715
 
 
 def gelu(x):
-    return 0.5 * x * (1.0 + _erf(x * SQRT1_2))
+    """GELU, tanh form: x/2 (1 + tanh(y)), y = sqrt(2/pi) (x + 0.044715 x^3)."""
+    return 0.5 * x * (1.0 + np.tanh(GELU_C * (x + GELU_A * x ** 3)))
 
 
 def gelu_grad(x):
-    return 0.5 * (1.0 + _erf(x * SQRT1_2)) + x * np.exp(-0.5 * x * x) / math.sqrt(2.0 * math.pi)
+    """d/dx of gelu: (1 + t)/2 + x (1 - t^2) sqrt(2/pi) (1 + 3 * 0.044715 x^2) / 2."""
+    t = np.tanh(GELU_C * (x + GELU_A * x ** 3))
+    return 0.5 * (1.0 + t) + 0.5 * x * (1.0 - t * t) * GELU_C * (1.0 + 3.0 * GELU_A * x * x)
 
 
 def unflatten(flat, dims):

@@ -4,8 +4,10 @@
 //                 z = ensemble member
 //   elementwise   GELU forward/backward, transposes, column sums, masked MSE, Adam
 // The GEMM reuses the warp-specialised layout of the emissivity kernel: warp 0 issues
-// TMA loads into a 6-stage ring, warp 1 issues tcgen05.mma (M = 128, N = 128), warps 2..5
-// drain the double-buffered TMEM accumulators.  Every mbarrier wait is bounded.
+// TMA loads into a 6-stage ring, warp 1 issues tcgen05.mma (M = 128, N = 128), warps 2..9
+// drain the double-buffered TMEM accumulators (two warps per lane quadrant, each half of the
+// columns: the epilogue's GELU and stores, not the MMAs, bound the hidden layers).  Every
+// mbarrier wait is bounded.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -23,7 +25,7 @@ namespace {
 
 constexpr int gM = 128, gN = 128, gStages = 6;
 constexpr int gAStage = gM * 128, gBStage = gN * 128;
-constexpr int gEpiWarps = 4;
+constexpr int gEpiWarps = 8;  // two per TMEM lane quadrant, each half of a tile's columns
 
 __device__ __forceinline__ void gtile(const GemmTcParams& p, int t, int& z, int& mt, int& nt) {
     int per = p.mtiles * p.ntiles;
@@ -35,9 +37,20 @@ __device__ __forceinline__ void gtile(const GemmTcParams& p, int t, int& z, int&
 
 }  // namespace
 
-__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+// GELU in its tanh form, x/2 (1 + tanh(y)), y = sqrt(2/pi) (x + 0.044715 x^3), with
+// tanh(y) = 1 - 2 / (e^{2y} + 1) on the hardware exponential (|y| clamped at 15, where tanh
+// is 1 to FP32 precision): a few instructions per value instead of erf's polynomial, which
+// made the hidden layers' epilogue, not the tensor cores, their bound.
+__device__ __forceinline__ float gelu_tanh_y(float y) {
+    y = fminf(fmaxf(y, -15.0f), 15.0f);
+    return 1.0f - __fdividef(2.0f, __expf(2.0f * y) + 1.0f);
+}
+__device__ __forceinline__ float gelu(float x) {
+    const float t = gelu_tanh_y(0.79788456080286536f * fmaf(0.044715f * x * x, x, x));
+    return 0.5f * x * (1.0f + t);
+}
 
-__global__ void __launch_bounds__(192, 1) k_gemm_bf16(const __grid_constant__ GemmTcParams p) {
+__global__ void __launch_bounds__(64 + 32 * gEpiWarps, 1) k_gemm_bf16(const __grid_constant__ GemmTcParams p) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* sA = smem;
@@ -158,7 +171,8 @@ __global__ void __launch_bounds__(192, 1) k_gemm_bf16(const __grid_constant__ Ge
     } else {
         // epilogue: lane = row of the tile; each chunk of 32 columns gets its bias (broadcast
         // loads), optional GELU for the BF16 output, and 16-byte stores of the row's run
-        const int q = warp & 3;
+        const int q = warp & 3;                          // the TMEM lane quadrant this warp may read
+        const int c0 = ((warp - 2) >> 2) * (gN / 64);    // its half of the tile's 32-column chunks
         int acc = 0;
         uint32_t acc_phase = 0;
         for (int t = blockIdx.x; t < total; t += gridDim.x) {
@@ -178,7 +192,7 @@ __global__ void __launch_bounds__(192, 1) k_gemm_bf16(const __grid_constant__ Ge
             float* C = p.c[z];
             __nv_bfloat16* Cb = p.cb[z];
             const float* bias = p.bias[z];
-            for (int c = 0; c < gN / 32; ++c) {
+            for (int c = c0; c < c0 + gN / 64; ++c) {
                 uint32_t v[32];
                 tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * gN + c * 32), v);
                 const int col0 = nt * gN + c * 32;
@@ -272,17 +286,16 @@ cudaError_t launch_gemm_bf16(const GemmTcParams& p, int sms, cudaStream_t st) {
     size_t smem = gemm_bf16_smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_gemm_bf16<<<total < sms ? total : sms, 192, smem, st>>>(p);
+    k_gemm_bf16<<<total < sms ? total : sms, 64 + 32 * gEpiWarps, smem, st>>>(p);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
 // elementwise kernels
 
-__device__ __forceinline__ float gelu_grad(float x) {
-    const float cdf = 0.5f * (1.0f + erff(x * 0.70710678118654752f));
-    const float pdf = 0.39894228040143268f * __expf(-0.5f * x * x);
-    return cdf + x * pdf;
+__device__ __forceinline__ float gelu_grad(float x) {  // d/dx of gelu above
+    const float t = gelu_tanh_y(0.79788456080286536f * fmaf(0.044715f * x * x, x, x));
+    return 0.5f * (1.0f + t) + 0.5f * x * (1.0f - t * t) * 0.79788456080286536f * fmaf(0.134145f, x * x, 1.0f);
 }
 
 // X = GELU(Z) as BF16 (Z stays FP32 for the backward pass).
