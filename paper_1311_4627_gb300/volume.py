@@ -271,15 +271,19 @@ def run_distributed(out_dir: str, config: dict, n_cells: int, chunk: int, solve_
             mine.append(k)
             yield k
 
+    claims = claim()
     res = run_chunks(man, n_cells, chunk, solve_chunk, resume=True, stop_after=stop_after, prepare=prepare, log=log,
-                     claim=claim())
+                     claim=claims)
     dist.barrier()
     if rank == 0:
         m = ChunkManifest(out_dir, config)
         m.merge()
         res["complete"] = all(m.done(k) for k in range(n_all))
+    # every rank closes its store (the queue iterator of an interrupted run holds it too)
+    # before rank 0 removes the store's directory: a FileStore touches its file when it closes
+    claims.close()
+    del claims, claim, store
     dist.barrier()
-    del store
     if rank == 0:
         shutil.rmtree(qdir[0], ignore_errors=True)
     res["claimed"] = mine
