@@ -570,6 +570,7 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
         pad.t = pad.cat = pad.zt = 0.0f;
         rent.insert(rent.end(), 128, pad);
     }
+    pat32.resize(pat32.size() + 64, PatF32{});  // the FP32 build prefetches 32 entries past a segment's end
     ctx->band_per_cell = band_total;
     ctx->band_max = 0;
     ctx->wmax_all = *std::max_element(wmax.begin(), wmax.end());

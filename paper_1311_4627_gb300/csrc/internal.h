@@ -51,7 +51,7 @@ struct GrainDev {
     const int* seg_ptr;     // [G][N+1] pattern entries of grain g in segment n at
                             //   seg_ptr[g*(N+1)+n] .. seg_ptr[g*(N+1)+n+1]
     const PatF64* pat64;    // pattern entries (FP64 build)
-    const PatF32* pat32;    // pattern entries (FP32 build)
+    const PatF32* pat32;    // pattern entries (FP32 build), then 64 zero entries (prefetch margin)
     const SoftF64* soft;    // [nbt - G] per grain, sorted by segment (descending)
     const int* soft_off;    // [G+1] start of each grain's soft list
     const PointEnt* pent;   // point-rule entries, column by column (u descending within a column)
