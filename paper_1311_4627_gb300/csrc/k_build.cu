@@ -321,39 +321,66 @@ __global__ void __launch_bounds__(256) k_build_small(GrainDev gd, ChunkDev ch, i
     __syncthreads();
     // 2. the cumulative sums, in the lane-per-cell kernel's order and arithmetic (FP64 build:
     // FP64 sums; FP32 build: compensated FP32 sums, whose FP32 values are kept)
+    // (the increments are read eight at a time ahead of the sums, so no shared-memory load
+    // latency sits on the sums' dependent chain)
+    constexpr int R = 8;
     if (tid == 0) {
         if (BUILD == 0) {
             double Phi = 0.0;
-            for (int n = 0; n < N - 1; ++n) {
-                const double d = sPhi[n];
-                sPhi[n] = Phi;
-                Phi += d;
+            for (int n0 = 0; n0 < N - 1; n0 += R) {
+                double d[R];
+#pragma unroll
+                for (int k = 0; k < R; ++k) d[k] = n0 + k < N - 1 ? sPhi[n0 + k] : 0.0;
+#pragma unroll
+                for (int k = 0; k < R; ++k)
+                    if (n0 + k < N - 1) {
+                        sPhi[n0 + k] = Phi;
+                        Phi += d[k];
+                    }
             }
             sPhiEnd = Phi;
         } else {
             Sum32 Phi;
-            for (int n = 0; n < N - 1; ++n) {
-                const float d = (float)sPhi[n];
-                sPhi[n] = Phi.val();
-                Phi.add(d);
+            for (int n0 = 0; n0 < N - 1; n0 += R) {
+                float d[R];
+#pragma unroll
+                for (int k = 0; k < R; ++k) d[k] = n0 + k < N - 1 ? (float)sPhi[n0 + k] : 0.0f;
+#pragma unroll
+                for (int k = 0; k < R; ++k)
+                    if (n0 + k < N - 1) {
+                        sPhi[n0 + k] = Phi.val();
+                        Phi.add(d[k]);
+                    }
             }
             sPhiEnd = Phi.val();
         }
     } else if (tid == 32) {
         if (BUILD == 0) {
             double Psi = 0.0;
-            for (int n = N - 2; n >= 0; --n) {
-                const double d = sPsi[n];
-                sPsi[n] = Psi;
-                Psi += d;
+            for (int n0 = N - 2; n0 >= 0; n0 -= R) {
+                double d[R];
+#pragma unroll
+                for (int k = 0; k < R; ++k) d[k] = n0 - k >= 0 ? sPsi[n0 - k] : 0.0;
+#pragma unroll
+                for (int k = 0; k < R; ++k)
+                    if (n0 - k >= 0) {
+                        sPsi[n0 - k] = Psi;
+                        Psi += d[k];
+                    }
             }
             sPsiTot = Psi;
         } else {
             Sum32 Psi;
-            for (int n = N - 2; n >= 0; --n) {
-                const float d = (float)sPsi[n];
-                sPsi[n] = Psi.val();
-                Psi.add(d);
+            for (int n0 = N - 2; n0 >= 0; n0 -= R) {
+                float d[R];
+#pragma unroll
+                for (int k = 0; k < R; ++k) d[k] = n0 - k >= 0 ? (float)sPsi[n0 - k] : 0.0f;
+#pragma unroll
+                for (int k = 0; k < R; ++k)
+                    if (n0 - k >= 0) {
+                        sPsi[n0 - k] = Psi.val();
+                        Psi.add(d[k]);
+                    }
             }
             sPsiTot = Psi.wide();
             sPsiEnd32 = Psi.val();
