@@ -166,6 +166,13 @@ typedef struct heat_opts {
                            128 cells x this; the operand ring holds 4 or 6 k-stages); 0 =
                            heat_autotune's choice, else 256.  Results do not depend on it        */
     int cooling;        /* HEAT_COOLING_CONTINUOUS (default) or HEAT_COOLING_DISCRETE          */
+    int build_prefetch; /* FP32 matrix build (more than 16 cells, not fused): 1: each segment step
+                           prefetches into L1 the pattern entry 32 entries past the segment's end;
+                           2: no prefetch; 0 (default): heat_autotune's choice if it made one, else
+                           1 on grids of at most 1024 wavelengths and 2 above (measured on a GB300:
+                           4.19 -> 3.89 ms per step of the 4096-cell x 64-grain x 1024-wavelength
+                           workload, 71.4 -> 86.9 ms of the 65536-cell x 32-grain x 2048-wavelength
+                           one).  Results do not depend on it                                 */
 } heat_opts;
 
 /* kernel classes reported by heat_get_timing */
@@ -252,7 +259,8 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
  * keeps the fastest w for all later solves on the ctx (heat_set_grains resets it).  Then, one
  * at a time on the configuration chosen so far, the launch shapes: the persistent recursion's
  * resident blocks per SM (all, 3, 2), for tensor-core emissivity the tile width (256 or 128
- * wavelengths), for the mixed path the fused build + recursion kernel; each kept if faster.
+ * wavelengths), for the mixed path the fused build + recursion kernel and the FP32 build's
+ * pattern prefetch (the other setting than the default); each kept if faster.
  * heat_get_tuning reports the choice; solves whose opts leave a knob at 0 use it.  Results
  * do not depend on any of them.  Runs the candidates on cuda_stream and synchronises; j_out / P_out as in
  * heat_solve (device, with room for the cells), overwritten.  Allocates a temporary buffer
@@ -280,6 +288,7 @@ typedef struct heat_tuning {
     int recur_blocks_per_sm;   /* resident blocks per SM of the persistent recursion              */
     int emis_n_tile;           /* tensor-core emissivity tile width (wavelengths)                 */
     int fused_build;           /* 1: the mixed path's build runs inside the recursion             */
+    int build_prefetch;        /* the FP32 build's pattern prefetch (1 on, 2 off; 0: the default) */
 } heat_tuning;
 heat_status heat_get_tuning(const heat_ctx* ctx, heat_tuning* out);
 

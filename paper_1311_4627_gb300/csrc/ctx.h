@@ -91,6 +91,7 @@ struct heat_ctx {
     int tuned_recur_bps = 0;                 // its resident blocks per SM of the recursion (0: all)
     int tuned_emis_nt = 0;                   // its tensor-core tile width (0: 256)
     int tuned_fused = 0;                     // its choice of the fused mixed-path kernel
+    int tuned_prefetch = 0;                  // its choice of the FP32 build's pattern prefetch (1 on, 2 off)
     int io_parity = 0;  // staging set of the next asynchronous host-I/O solve
     DevBuf d_status;
     long long wait_polls = HEAT_WAIT_POLLS_DEFAULT;  // give-up limit of the tcgen05 kernels' waits

@@ -284,6 +284,7 @@ void heat_default_opts(heat_opts* o) {
     o->fused_build = 0;
     o->recur_blocks_per_sm = 0;
     o->emis_n_tile = 0;
+    o->build_prefetch = 0;
     o->cooling = HEAT_COOLING_CONTINUOUS;
 }
 
@@ -370,6 +371,7 @@ heat_status heat_set_grains(heat_ctx* ctx, int n_grains, const double* radius_cm
     ctx->tasks_NG = -1;
     ctx->tail_NG = -1;
     ctx->tuned_streams = ctx->tuned_chunk = 0;
+    ctx->tuned_prefetch = 0;
     ctx->row_weight = 30;
     ctx->td_built = false;
     for (auto* modes : {ctx->tc, ctx->tc_si})
@@ -737,6 +739,8 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
         return ctx->fail(HEAT_EINVAL, "heat_solve: recur_blocks_per_sm must be in 0..4");
     if (o.emis_n_tile != 0 && o.emis_n_tile != 128 && o.emis_n_tile != 256)
         return ctx->fail(HEAT_EINVAL, "heat_solve: emis_n_tile must be 0, 128 or 256");
+    if (o.build_prefetch < 0 || o.build_prefetch > 2)
+        return ctx->fail(HEAT_EINVAL, "heat_solve: build_prefetch must be 0, 1 or 2");
     if (o.cooling != HEAT_COOLING_CONTINUOUS && o.cooling != HEAT_COOLING_DISCRETE)
         return ctx->fail(HEAT_EINVAL, "heat_solve: bad cooling option");
     const bool discrete = o.cooling == HEAT_COOLING_DISCRETE;
@@ -876,10 +880,16 @@ heat_status heat_solve(heat_ctx* ctx, const heat_opts* opts, double* P_out, void
     }
     if (nslots > 1 && !ctx->ev_fork) CKR(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
 
-    GrainDev gd;
+    GrainDev gd{};
     gd.N = N;
     gd.G = G;
     gd.nbt = nbt;
+    {   // the FP32 build's pattern prefetch: the caller's setting, else the tuned one, else on for
+        // grids of at most 1024 wavelengths
+        const int mode = o.build_prefetch ? o.build_prefetch
+                                          : (ctx->tuned_prefetch ? ctx->tuned_prefetch : (N <= 1024 ? 1 : 2));
+        gd.pat_prefetch = mode == 1 ? 32 : 0;
+    }
     gd.lam = ctx->d_lam.as<double>();
     gd.dln = ctx->d_dln.as<double>();
     gd.bin_off = ctx->d_bin_off.as<int>();
@@ -1062,7 +1072,7 @@ heat_status heat_autotune(heat_ctx* ctx, const heat_opts* opts, double* P_out, v
             cands.push_back({sN, chunk});
         }
     // the launch-shape choices of an earlier tuning do not apply while these are timed
-    ctx->tuned_recur_bps = ctx->tuned_emis_nt = ctx->tuned_fused = 0;
+    ctx->tuned_recur_bps = ctx->tuned_emis_nt = ctx->tuned_fused = ctx->tuned_prefetch = 0;
     ctx->tuned_streams = ctx->tuned_chunk = 0;
     // each timed solve starts with a cold L2 (a write larger than L2 before it), as a solve
     // on fresh fields would
@@ -1151,6 +1161,12 @@ heat_status heat_autotune(heat_ctx* ctx, const heat_opts* opts, double* P_out, v
         float ms = 0.0f;
         if ((hk = time_config(pick, &ms)) != HEAT_OK) return done(hk);
         if (ms < best) best = ms; else ctx->tuned_fused = 0;
+    }
+    if (opts->build == HEAT_BUILD_F32 && opts->build_prefetch == 0 && !ctx->tuned_fused) {
+        ctx->tuned_prefetch = ctx->N <= 1024 ? 2 : 1;  // the other setting than the default
+        float ms = 0.0f;
+        if ((hk = time_config(pick, &ms)) != HEAT_OK) return done(hk);
+        if (ms < best) best = ms; else ctx->tuned_prefetch = 0;
     }
     done(HEAT_OK);
     ctx->tuned_streams = pick.streams;
@@ -1277,6 +1293,7 @@ heat_status heat_get_tuning(const heat_ctx* ctx, heat_tuning* out) {
     out->recur_blocks_per_sm = ctx->tuned_recur_bps;
     out->emis_n_tile = ctx->tuned_emis_nt;
     out->fused_build = ctx->tuned_fused;
+    out->build_prefetch = ctx->tuned_prefetch;
     return HEAT_OK;
 }
 
@@ -1399,6 +1416,7 @@ __attribute__((visibility("hidden"))) heat_status heat_internal_grain_view(heat_
                                                                            int** status) {
     if (!ctx) return HEAT_EINVAL;
     if (ctx->G == 0) return ctx->fail(HEAT_ESTATE, "heat_solve_noalloc: grains not set");
+    *gd = GrainDev{};  // every field set below or left zero (no pattern prefetch)
     gd->N = ctx->N;
     gd->G = ctx->G;
     gd->nbt = ctx->nbt;

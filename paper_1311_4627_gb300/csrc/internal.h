@@ -48,6 +48,7 @@ struct GrainDev {
     int max_bins;           // largest bins per grain
     int band_max;           // largest band (elements per cell) of one grain
     int wmax_all;           // widest band row over the grains
+    int pat_prefetch;       // nonzero: the FP32 build prefetches into L1 the pattern entry 32 past each segment
     const int* seg_ptr;     // [G][N+1] pattern entries of grain g in segment n at
                             //   seg_ptr[g*(N+1)+n] .. seg_ptr[g*(N+1)+n+1]
     const PatF64* pat64;    // pattern entries (FP64 build)

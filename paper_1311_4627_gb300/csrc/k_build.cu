@@ -80,7 +80,7 @@ __global__ void k_field(int N, const double* __restrict__ dln, const TU* __restr
 // The segments are walked in order; every band element whose transition wavelength
 // falls in the current segment (the grain's pattern list) is written to the band
 // storage Bb, so the recursion streams B instead of gathering tables.
-template <int BUILD>
+template <int BUILD, bool PF = false>
 __device__ __forceinline__ void build_task(const GrainDev& gd, const ChunkDev& ch, int task, int lane) {
     const int N = gd.N, Cc = ch.Cc;
     const int2 tk = (ch.btasks ? ch.btasks : ch.tasks)[task];
@@ -175,7 +175,7 @@ __device__ __forceinline__ void build_task(const GrainDev& gd, const ChunkDev& c
             // L1 prefetch of the pattern line 32 entries past this segment (about three segments
             // ahead; the table is padded for it).  Measured on the batched workload, A/B in one
             // run: none 4.10 ms, 8 entries 3.93, 16 3.92, 32 3.87, 64 3.88, 128 3.90, two lines 3.94
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(gd.pat32 + k1 + 32));
+            if (PF) asm volatile("prefetch.global.L1 [%0];" ::"l"(gd.pat32 + k1 + 32));
             // every element's argument is z = q t with t in [0, dln]: when |q| dln <= 1/4 the
             // short series serves the whole segment.  The test is per lane (per cell), so a
             // cell's values do not depend on the cells sharing its warp; lanes normally agree
@@ -246,10 +246,10 @@ __device__ __forceinline__ void build_task(const GrainDev& gd, const ChunkDev& c
 }
 
 // One warp per task, in the build's task order.
-template <int BUILD>
+template <int BUILD, bool PF = false>
 __global__ void __launch_bounds__(128) k_build(GrainDev gd, ChunkDev ch) {
     const int task = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (task < ch.n_tasks) build_task<BUILD>(gd, ch, task, threadIdx.x & 31);
+    if (task < ch.n_tasks) build_task<BUILD, PF>(gd, ch, task, threadIdx.x & 31);
 }
 
 // ---------------------------------------------------------------------------
@@ -601,7 +601,7 @@ cudaError_t launch_build(const GrainDev& g, const ChunkDev& ch, int build, cudaS
     }
     if (ch.n_tasks == 0) return cudaSuccess;
     // one warp per task (measured: a persistent launch with a task counter is no faster)
-    auto kern = build == 0 ? k_build<0> : k_build<1>;
+    auto kern = build == 0 ? k_build<0> : (g.pat_prefetch ? k_build<1, true> : k_build<1, false>);
     kern<<<(unsigned)((ch.n_tasks + 3) / 4), 128, 0, st>>>(g, ch);
     return cudaGetLastError();
 }

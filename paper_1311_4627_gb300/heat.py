@@ -46,12 +46,13 @@ class heat_opts(ctypes.Structure):
                 ("ledger_out", ctypes.c_void_p), ("streams", ctypes.c_int), ("heating", ctypes.c_int),
                 ("prune_eps", ctypes.c_double), ("fused_build", ctypes.c_int),
                 ("recur_blocks_per_sm", ctypes.c_int), ("emis_n_tile", ctypes.c_int),
-                ("cooling", ctypes.c_int)]
+                ("cooling", ctypes.c_int), ("build_prefetch", ctypes.c_int)]
 
 
 class heat_tuning(ctypes.Structure):
     _fields_ = [("streams", ctypes.c_int), ("chunk_cells", ctypes.c_int), ("row_weight", ctypes.c_int),
-                ("recur_blocks_per_sm", ctypes.c_int), ("emis_n_tile", ctypes.c_int), ("fused_build", ctypes.c_int)]
+                ("recur_blocks_per_sm", ctypes.c_int), ("emis_n_tile", ctypes.c_int), ("fused_build", ctypes.c_int),
+                ("build_prefetch", ctypes.c_int)]
 
 
 _lib = None

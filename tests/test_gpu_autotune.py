@@ -57,9 +57,19 @@ def test_recursion_resident_blocks_do_not_change_results(sub, bps):
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
 
+@pytest.mark.parametrize("pf", [1, 2])
+def test_build_prefetch_does_not_change_results(sub, pf):
+    """The FP32 build's pattern prefetch on or off: P and j bit for bit."""
+    _, _, lib = sub
+    a = lib.solve(emis=heat.HEAT_EMIS_BF16X3, **MIXED)
+    b = lib.solve(emis=heat.HEAT_EMIS_BF16X3, build_prefetch=pf, **MIXED)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
 def test_launch_shape_option_checks(sub):
     _, _, lib = sub
-    for kw in (dict(emis_n_tile=64), dict(recur_blocks_per_sm=5), dict(recur_blocks_per_sm=-1)):
+    for kw in (dict(emis_n_tile=64), dict(recur_blocks_per_sm=5), dict(recur_blocks_per_sm=-1),
+               dict(build_prefetch=3), dict(build_prefetch=-1)):
         with pytest.raises(heat.HeatError) as e:
             lib.solve(emis=heat.HEAT_EMIS_BF16X3, **kw, **MIXED)
         assert e.value.status == heat.HEAT_EINVAL

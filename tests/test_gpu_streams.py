@@ -79,11 +79,13 @@ def test_autotune_choice_is_used_and_exact(wl_lib):
     t = heat.heat_get_tuning(lib.ctx)
     assert (t["streams"], t["chunk_cells"]) == (s, c)
     assert t["recur_blocks_per_sm"] in (0, 2, 3) and t["emis_n_tile"] in (0, 128) and t["fused_build"] in (0, 1)
+    assert t["build_prefetch"] in (0, 1, 2)
     got = lib.solve(build=heat.HEAT_BUILD_F32, emis=heat.HEAT_EMIS_BF16X3, j_dtype=heat.HEAT_F32)
     # the tuned solve is the solve with the chosen knobs given explicitly, bit for bit ...
     explicit = lib.solve(build=heat.HEAT_BUILD_F32, emis=heat.HEAT_EMIS_BF16X3, j_dtype=heat.HEAT_F32, streams=s,
                          chunk_cells=c, recur_blocks_per_sm=t["recur_blocks_per_sm"],
-                         emis_n_tile=t["emis_n_tile"] or 256, fused_build=2 - t["fused_build"])
+                         emis_n_tile=t["emis_n_tile"] or 256, fused_build=2 - t["fused_build"],
+                         build_prefetch=t["build_prefetch"] or (1 if wl.n_lambda <= 1024 else 2))
     assert np.array_equal(got[0], explicit[0]) and np.array_equal(got[1], explicit[1])
     # ... and P does not depend on the configuration; j only through the tensor-core tiling
     assert np.array_equal(got[0], ref[0])
