@@ -401,15 +401,16 @@ template <int BUILD, bool PRUNE>
 __global__ void __launch_bounds__(128, 5) k_recur(GrainDev gd, ChunkDev ch) {
     for_each_task(ch, 1, [&](int task, int lane) {
         const int g = ch.tasks[task].x, grp = ch.tasks[task].y;
-        const int wm = gd.wmax[g];  // warp-uniform
+        // window classes 1, 2 and 4 (warp-uniform).  Measured on the batched workload: a class
+        // of 8 for rows wider than 4 spilled at the 96 registers of 5 resident blocks (6.26 ms
+        // against 6.04-6.10 with 4 the widest; widest 3 or 5 the same, 6 6.33, 7 7.25 ms)
+        const int wm = gd.wmax[g];
         if (wm <= 1)
             recur_task<BUILD, 1, PRUNE>(gd, ch, g, grp, lane);
         else if (wm <= 2)
             recur_task<BUILD, 2, PRUNE>(gd, ch, g, grp, lane);
-        else if (wm <= 4)
-            recur_task<BUILD, 4, PRUNE>(gd, ch, g, grp, lane);
         else
-            recur_task<BUILD, 8, PRUNE>(gd, ch, g, grp, lane);
+            recur_task<BUILD, 4, PRUNE>(gd, ch, g, grp, lane);
     });
 }
 
