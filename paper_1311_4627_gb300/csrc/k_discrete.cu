@@ -500,23 +500,40 @@ __global__ void __launch_bounds__(kGthThreads, 1) k_gth(GrainDev gd, ChunkDev ch
         int jp = nb;
         for (int k = p0; k <= hi; ++k) jp = jlo[k] < jp ? jlo[k] : jp;
         __syncthreads();
-        for (int i = warp; i < p0; i += nw) {  // the block below the panel: rows with a rate into it
-            double* qi = qs + (size_t)i * ld;
-            const double lv = lane < nk ? qi[hi - lane] : 0.0;
-            if (__ballot_sync(0xffffffffu, lv != 0.0) != 0u) {
-                double l[kGthB];
+        // the block below the panel, two rows per warp so that each U value loaded serves both
+        // (each element's FMAs in the same order as one row at a time); rows with no rate into
+        // the panel are left as they are
+        for (int i0 = 2 * warp; i0 < p0; i0 += 2 * nw) {
+            const bool has1 = i0 + 1 < p0;
+            double* q0 = qs + (size_t)i0 * ld;
+            double* q1 = qs + (size_t)(has1 ? i0 + 1 : i0) * ld;
+            const double lv0 = lane < nk ? q0[hi - lane] : 0.0;
+            const double lv1 = (has1 && lane < nk) ? q1[hi - lane] : 0.0;
+            const bool a0 = __ballot_sync(0xffffffffu, lv0 != 0.0) != 0u;
+            const bool a1 = __ballot_sync(0xffffffffu, lv1 != 0.0) != 0u;
+            if (a0 || a1) {
+                double l0[kGthB], l1[kGthB];
 #pragma unroll
-                for (int kk = 0; kk < kGthB; ++kk) l[kk] = __shfl_sync(0xffffffffu, lv, kk);
+                for (int kk = 0; kk < kGthB; ++kk) {
+                    l0[kk] = __shfl_sync(0xffffffffu, lv0, kk);
+                    l1[kk] = __shfl_sync(0xffffffffu, lv1, kk);
+                }
                 for (int j = jp + lane; j < p0; j += 32) {
-                    double v = qi[j];
+                    double v0 = q0[j], v1 = q1[j];
 #pragma unroll
-                    for (int kk = 0; kk < kGthB; ++kk) v = fma(l[kk], U[kk * nb + j], v);
-                    qi[j] = v;
+                    for (int kk = 0; kk < kGthB; ++kk) {
+                        const double u = U[kk * nb + j];
+                        v0 = fma(l0[kk], u, v0);
+                        v1 = fma(l1[kk], u, v1);
+                    }
+                    if (a0) q0[j] = v0;
+                    if (a1) q1[j] = v1;
                 }
             }
-            if (i == p0 - 1 && i > 0) {  // the first state of the next panel
+            const int inext = p0 - 1;  // the first state of the next panel
+            if (inext > 0 && (i0 == inext || (has1 && i0 + 1 == inext))) {
                 __syncwarp();
-                row_exit(qi, i, s, rs, jlo, lane);
+                row_exit(qs + (size_t)inext * ld, inext, s, rs, jlo, lane);
             }
         }
         __syncthreads();
