@@ -422,6 +422,7 @@ __device__ __forceinline__ void row_exit(const double* qk, int k, double* s, dou
 // the block below it once for kGthB fused multiply-adds per element.
 // Shared memory: s, 1/s, X [nb] each, U [kGthB][nb], the lowest columns [nb] (ints, padded
 // to doubles), then q (SMQ).
+static_assert(kGthB - 1 < kGthThreads / 32, "k_gth: the last warp must be free of panel rows");
 template <bool SMQ>
 __global__ void __launch_bounds__(kGthThreads, 1) k_gth(GrainDev gd, ChunkDev ch, const int* __restrict__ gorder,
                                                         long long s0, double* q, long long qstride) {
@@ -458,13 +459,18 @@ __global__ void __launch_bounds__(kGthThreads, 1) k_gth(GrainDev gd, ChunkDev ch
             const double* qk = qs + (size_t)k * ld;
             const double r = rs[k];
             const int jk = jlo[k];
-            for (int j = tid; j < k; j += kGthThreads) Uk[j] = j < jk ? 0.0 : qk[j] * r;
-            __syncthreads();
+            // the last warp (never one of the panel's rows below k: at most kGthB - 1 < nw of them)
+            // keeps the normalised row for the rows below the panel, while the panel's rows take
+            // their multiple of row k directly: no barrier between the two
+            if (warp == nw - 1)
+                for (int j = lane; j < k; j += 32) Uk[j] = j < jk ? 0.0 : qk[j] * r;
             for (int i = p0 + warp; i < k; i += nw) {  // the panel's rows below k, columns from jk
                 double* qi = qs + (size_t)i * ld;
                 const double qik = qi[k];
-                if (qik != 0.0)
-                    for (int j = jk + lane; j < k; j += 32) qi[j] = fma(qik, Uk[j], qi[j]);
+                if (qik != 0.0) {
+                    const double c = qik * r;
+                    for (int j = jk + lane; j < k; j += 32) qi[j] = fma(c, qk[j], qi[j]);
+                }
                 if (i == k - 1) {  // the next state to be removed
                     __syncwarp();
                     row_exit(qi, k - 1, s, rs, jlo, lane);
