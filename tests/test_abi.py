@@ -36,8 +36,12 @@ def test_default_opts_and_null_handling(libheat):
     # heat_default_opts, so a poisoned value there must be overwritten
     o.heating = 12345
     o.prune_eps = 0.5
+    o.cooling = 777
+    o.build_prefetch = 3
     libheat.heat_default_opts(ctypes.byref(o))
     assert o.heating == heat.HEAT_HEATING_INTEGRAL and o.prune_eps == 0.0
+    assert o.cooling == heat.HEAT_COOLING_CONTINUOUS and o.build_prefetch == 0
+    assert heat.heat_opts._fields_[-1][0] == "build_prefetch"
     # null contexts are rejected without touching a device
     assert libheat.heat_sync(None) == heat.HEAT_EINVAL
     assert libheat.heat_solve(None, ctypes.byref(o), None, None, None) == heat.HEAT_EINVAL
@@ -54,3 +58,31 @@ def test_create_grid_rejects_bad_grids(libheat):
     neg = np.array([-1.0, 2.0])
     assert libheat.heat_create_grid(ctypes.byref(h), 0, 2, neg.ctypes.data) == heat.HEAT_EINVAL
     assert libheat.heat_create_grid(ctypes.byref(h), 0, 1, neg.ctypes.data) == heat.HEAT_EINVAL
+
+
+def _header_struct_fields(text, name):
+    """Member names of `typedef struct name {...} name;` in declaration order (comments removed)."""
+    import re
+
+    m = re.search(r"typedef struct %s \{(.*?)\} %s;" % (name, name), text, re.S)
+    assert m, name
+    body = re.sub(r"/\*.*?\*/", "", m.group(1), flags=re.S)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if decl:
+            decl = re.sub(r"^(const\s+)?(unsigned\s+)?(long long|int|double|float|void|char)\s*\**\s*", "", decl)
+            fields += [f.strip().lstrip("*") for f in decl.split(",")]
+    return fields
+
+
+def test_binding_structs_mirror_the_header():
+    """Every struct the header defines has a ctypes mirror with the same members in the same order."""
+    import os
+    import re
+
+    text = open(os.path.join(os.path.dirname(__file__), "..", "include", "heat.h")).read()
+    defined = re.findall(r"typedef struct (\w+) \{", text)
+    assert set(defined) == {"heat_opts", "heat_tuning"}
+    for name in defined:
+        assert [f for f, _ in getattr(heat, name)._fields_] == _header_struct_fields(text, name), name
