@@ -740,11 +740,36 @@ def main():
 
         v_async = e2e_run(2)
         v_sync = e2e_run(1)
-        line["e2e"] = {"value": v_async, "unit": UNIT, "h2d_bytes_per_step": int(u_host.numel() * 8),
-                       "d2h_bytes_per_step": int(j_host[0].numel() * 4),
+        # the copies alone, as plain pinned-memory copies on a side stream (3 of each, CUDA events):
+        # with the two directions on their own copy engines, the slower one bounds a step from below
+        j_dev = torch.empty(cells, G, N, dtype=torch.float32, device=dev)
+        u_dev2 = torch.empty_like(u)
+        cs = torch.cuda.Stream(dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        with torch.cuda.stream(cs):
+            j_host[0].copy_(j_dev, non_blocking=True)
+            u_dev2.copy_(u_host, non_blocking=True)
+            ev[0].record(cs)
+            for _ in range(3):
+                j_host[0].copy_(j_dev, non_blocking=True)
+            ev[1].record(cs)
+            for _ in range(3):
+                u_dev2.copy_(u_host, non_blocking=True)
+            ev[2].record(cs)
+        cs.synchronize()
+        d2h_b, h2d_b = j_host[0].numel() * 4, u_host.numel() * 8
+        d2h_gbs = 3 * d2h_b / (ev[0].elapsed_time(ev[1]) * 1e-3) / 1e9
+        h2d_gbs = 3 * h2d_b / (ev[1].elapsed_time(ev[2]) * 1e-3) / 1e9
+        floor_ms = max(d2h_b / d2h_gbs, h2d_b / h2d_gbs) / 1e6
+        del j_dev, u_dev2
+        line["e2e"] = {"value": v_async, "unit": UNIT, "h2d_bytes_per_step": int(h2d_b),
+                       "d2h_bytes_per_step": int(d2h_b),
                        "mode": "heat_solve with host_io = 2 (pinned host buffers, copies in and out every step, "
                                "queued without waiting; timed to the device's completion)",
-                       "synchronous_value": v_sync}
+                       "synchronous_value": v_sync,
+                       "copies_alone": {"d2h_gbs": d2h_gbs, "h2d_gbs": h2d_gbs, "floor_ms_per_step": floor_ms,
+                                        "note": "plain pinned-memory copies of one step's j out and u in; the "
+                                                "slower direction bounds an overlapped step from below"}}
         heat.heat_set_fields(ctx, cells, u, heat.HEAT_F64, 1, sh)
 
     # the other exact-method paths, for the plain-vs-mixed comparison
