@@ -172,9 +172,11 @@ __device__ __forceinline__ void build_task(const GrainDev& gd, const ChunkDev& c
             float ua = us.x, su = us.y;
             float phi = Phi32.val();
             int k = sp[n], k1 = sp[n + 1];
-            // L1 prefetch of the pattern line 32 entries past this segment (about three segments
-            // ahead; the table is padded for it).  Measured on the batched workload, A/B in one
-            // run: none 4.10 ms, 8 entries 3.93, 16 3.92, 32 3.87, 64 3.88, 128 3.90, two lines 3.94
+            // PF: L1 prefetch of the pattern line 32 entries past this segment (about three segments
+            // ahead; the table is padded for it).  Measured on the batched workload (1024
+            // wavelengths), A/B in one run: none 4.10 ms, 8 entries 3.93, 16 3.92, 32 3.87, 64 3.88,
+            // 128 3.90, two lines 3.94; on the 2048-wavelength emissivity-heavy one it is slower
+            // (70.5 -> 87.1 ms), so the host picks the variant per grid (heat_opts.build_prefetch)
             if (PF) asm volatile("prefetch.global.L1 [%0];" ::"l"(gd.pat32 + k1 + 32));
             // every element's argument is z = q t with t in [0, dln]: when |q| dln <= 1/4 the
             // short series serves the whole segment.  The test is per lane (per cell), so a
